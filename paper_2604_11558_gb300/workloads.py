@@ -1,0 +1,118 @@
+"""Seeded synthetic inputs for the benchmark and parity workloads.
+
+This module holds random draws and constants only: none of the method's
+arithmetic (no grids, matrices, phi_1 or reaction evaluation).  Both the
+CUDA path's tests/bench and the CPU oracle's tests take their inputs from
+here, so the two sides see bit-identical initial data.
+
+Every workload is a plain dict:
+
+    geometry   'disk' | 'sphere' | 'ball' | 'cylinder'
+    n          points per mode, mode 1 first (disk: (n_rho, n_theta),
+               sphere: (n_theta, n_phi), ball: (n_rho, n_theta, n_phi),
+               cylinder: (n_rho, n_theta, n_z))
+    d          diffusion coefficient per species
+    reaction   'schnakenberg' | 'gray_scott' | 'linear_cubic' | 'none'
+    params     reaction parameters (see below)
+    tau, steps time step and number of steps
+    W0         float64 array (S, *reversed(n)): mode 1 is the last axis
+    seed       numpy PCG64 seed
+
+Reaction parameters: schnakenberg (gamma, a, b); gray_scott (F, k);
+linear_cubic (K as a row-major S x S list).
+"""
+import numpy as np
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _shape(n):
+    return tuple(reversed(tuple(n)))
+
+
+def schnakenberg_disk(n=(32, 64), steps=200, seed=2, gamma=100.0, a=0.1, b=0.9, d=(1.0, 10.0), tau=1e-4):
+    """Polar disk, Schnakenberg, steady state (a+b, b/(a+b)^2) plus U(-0.01, 0.01) noise per point."""
+    rng = _rng(seed)
+    shp = _shape(n)
+    u = (a + b) + rng.uniform(-0.01, 0.01, shp)
+    v = b / (a + b) ** 2 + rng.uniform(-0.01, 0.01, shp)
+    return dict(geometry="disk", n=tuple(n), d=list(d), reaction="schnakenberg", params=[gamma, a, b],
+                tau=tau, steps=steps, W0=np.stack([u, v]), seed=seed, name="disk_schnakenberg")
+
+
+def gray_scott_ball(n=(100, 100, 100), steps=500, seed=3, F=0.04, k=0.06, d=(2e-3, 1e-3), tau=0.5):
+    """Ball, Gray-Scott: u = 1, v = 0 except a seeded patch where v = 0.25 + U(-0.01, 0.01).
+
+    The patch is a box in index space: each side about a fifth of the points
+    of its mode, at a uniformly drawn corner (periodic wrap along theta,
+    clipped along rho and phi).
+    """
+    rng = _rng(seed)
+    shp = _shape(n)
+    u = np.ones(shp)
+    v = np.zeros(shp)
+    n1, n2, n3 = n
+    w1, w2, w3 = max(1, n1 // 5), max(1, n2 // 5), max(1, n3 // 5)
+    i0 = int(rng.integers(0, n1 - w1 + 1))
+    j0 = int(rng.integers(0, n2))
+    k0 = int(rng.integers(0, n3 - w3 + 1))
+    noise = rng.uniform(-0.01, 0.01, (w3, w2, w1))
+    for jl in range(w2):
+        v[k0:k0 + w3, (j0 + jl) % n2, i0:i0 + w1] = 0.25 + noise[:, jl, :]
+    return dict(geometry="ball", n=tuple(n), d=list(d), reaction="gray_scott", params=[F, k],
+                tau=tau, steps=steps, W0=np.stack([u, v]), seed=seed, name="ball_gray_scott")
+
+
+def linear_cubic_cylinder(n=(64, 128, 128), steps=1000, seed=4, d=(1e-3, 5e-3, 20e-3), tau=0.05):
+    """Cylinder, 3 species, f_i = sum_j K_ij u_j - u_i^3 with K = N(0, 0.5^2) + 0.5 I; u_i ~ N(0, 0.01^2)."""
+    rng = _rng(seed)
+    S = len(d)
+    K = rng.normal(0.0, 0.5, (S, S)) + 0.5 * np.eye(S)
+    W0 = rng.normal(0.0, 0.01, (S,) + _shape(n))
+    return dict(geometry="cylinder", n=tuple(n), d=list(d), reaction="linear_cubic",
+                params=[float(x) for x in K.ravel()], tau=tau, steps=steps, W0=W0, seed=seed,
+                name="cylinder_linear_cubic")
+
+
+def batched_disks(count=256, steps=500, seed=5, n_rho=(16, 96), n_theta=(32, 256), gamma=100.0, tau=1e-4):
+    """Independent Schnakenberg disks of uneven sizes.
+
+    Per instance: n_rho ~ U{16..96}, n_theta ~ U{32..256}, a ~ U(0.05, 0.2),
+    b ~ U(0.7, 1.0), d_v ~ U(8, 20), d_u = 1, gamma = 100; steady state plus
+    U(-0.01, 0.01) noise.  Returns a list of workload dicts.
+    """
+    rng = _rng(seed)
+    out = []
+    for _ in range(count):
+        nr = int(rng.integers(n_rho[0], n_rho[1] + 1))
+        nt = int(rng.integers(n_theta[0], n_theta[1] + 1))
+        a = float(rng.uniform(0.05, 0.2))
+        b = float(rng.uniform(0.7, 1.0))
+        dv = float(rng.uniform(8.0, 20.0))
+        shp = (nt, nr)
+        u = (a + b) + rng.uniform(-0.01, 0.01, shp)
+        v = b / (a + b) ** 2 + rng.uniform(-0.01, 0.01, shp)
+        out.append(dict(geometry="disk", n=(nr, nt), d=[1.0, dv], reaction="schnakenberg",
+                        params=[gamma, a, b], tau=tau, steps=steps, W0=np.stack([u, v]), seed=seed,
+                        name="batched_disks"))
+    return out
+
+
+def schnakenberg_sphere(n=(256, 512), steps=1000, seed=6, gamma=200.0, a=0.1, b=0.9, d=(1.0, 10.0), tau=1e-4):
+    """Unit sphere (Laplace-Beltrami), Schnakenberg, steady state plus U(-0.01, 0.01) noise."""
+    rng = _rng(seed)
+    shp = _shape(n)
+    noise = rng.uniform(-0.01, 0.01, (2,) + shp)
+    u = (a + b) + noise[0]
+    v = b / (a + b) ** 2 + noise[1]
+    return dict(geometry="sphere", n=tuple(n), d=list(d), reaction="schnakenberg", params=[gamma, a, b],
+                tau=tau, steps=steps, W0=np.stack([u, v]), seed=seed, name="sphere_schnakenberg",
+                noise=noise)
+
+
+def random_state(geometry, n, S=2, seed=7, scale=0.1, offset=0.5):
+    """Generic seeded field for parity tests: offset + scale * N(0, 1) per point and species."""
+    rng = _rng(seed)
+    return offset + scale * rng.standard_normal((S,) + _shape(n))

@@ -1,0 +1,165 @@
+/*
+ * sexpe.h -- C ABI of the GB300 split exponential Euler library (libsexpe.so).
+ *
+ * The library integrates N-coupled diffusion-reaction systems
+ *     w_s' = d_s M w_s + g_s(w),   M = M_1 + ... + M_d             (Section 2, eq. ODE)
+ * on a disk (polar), sphere surface (Laplace-Beltrami), ball (spherical) or
+ * cylinder (cylindrical coordinates) with the split exponential Euler method
+ *     F_s     = d_s M w_s + g_s(w_n)
+ *     w_s,n+1 = w_s,n + tau phi_1(tau d_s M_1) ... phi_1(tau d_s M_d) F_s
+ * (Section 4, eqs. ee and splitorder), every phi_1 factor applied as mu-mode
+ * products with precomputed per-direction phi_1 matrices or eigenbases and
+ * Hadamard factors (eqs. ee_disk, ee_sphere, ee_ball, ee_cylinder).
+ *
+ * Conventions shared by every entry point
+ *  - State layout: FP64, species outermost, then mode 3, mode 2, mode 1 with
+ *    mode 1 contiguous (the paper's vector ordering w_{i+(j-1)n1+(k-1)n1n2},
+ *    Section 2).  Modes: disk (rho, theta), sphere (theta, phi),
+ *    ball (rho, theta, phi), cylinder (rho, theta, z).  No padding.
+ *  - Pointers named *_dev are device pointers owned by the caller; pointers
+ *    named *_host are host pointers owned by the caller.  The library never
+ *    frees caller memory.  A plan owns all of its own device tables.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Every call returns a sexpe_status and never aborts or prints.  Device-side
+ *    waits are bounded: a wait that runs out records SEXPE_ETIMEOUT, which the
+ *    next sexpe_synchronize() on the plan reports.
+ *  - Calls on one plan are not thread-safe; distinct plans are independent.
+ */
+#ifndef SEXPE_H
+#define SEXPE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SEXPE_OK = 0,
+    SEXPE_EINVAL = 1,        /* bad argument (size, pointer, tau, species count, ...)        */
+    SEXPE_ENOMEM = 2,        /* device or host allocation failed                             */
+    SEXPE_ECUDA = 3,         /* a CUDA runtime call failed                                   */
+    SEXPE_ETIMEOUT = 4,      /* a bounded device-side wait ran out                           */
+    SEXPE_EUNSUPPORTED = 5,  /* valid request this build does not implement                  */
+    SEXPE_ENUMERIC = 6       /* setup produced a non-finite table                            */
+} sexpe_status;
+
+typedef enum { SEXPE_DISK = 0, SEXPE_SPHERE = 1, SEXPE_BALL = 2, SEXPE_CYLINDER = 3 } sexpe_geometry;
+
+/* Arithmetic of the per-step chain.  FP64: every operation in FP64 (SIMT).
+ * SPLIT_TF32: stencil differences at FP64 accuracy, F rounded to FP32, every
+ * mu-mode product on tcgen05 tensor cores as three TF32 products
+ * (hi*hi + hi*lo + lo*hi, each operand split x = hi + lo with both parts
+ * rounded to TF32) accumulated in FP32 in tensor memory; the state stays FP64. */
+typedef enum { SEXPE_FP64 = 0, SEXPE_SPLIT_TF32 = 1 } sexpe_precision;
+
+/* Reaction terms g_s(w), evaluated pointwise.
+ *   SCHNAKENBERG (S=2), params {gamma, a, b}: f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)
+ *   GRAY_SCOTT   (S=2), params {F, k}:        f = -u v^2 + F(1-u),      g = u v^2 - (F+k) v
+ *   LINEAR_CUBIC (S<=4), params K row-major S x S: f_i = sum_j K_ij u_j - u_i^3
+ *   NONE: g = 0 (any S <= 4, no params).                                            */
+typedef enum {
+    SEXPE_REACTION_NONE = 0,
+    SEXPE_SCHNAKENBERG = 1,
+    SEXPE_GRAY_SCOTT = 2,
+    SEXPE_LINEAR_CUBIC = 3
+} sexpe_reaction;
+
+/* Height axis of the cylinder: NEUMANN = homogeneous Neumann at both caps
+ * (node-centred, h = z_star/(n-1)); PAPER = Neumann at 0 and Dirichlet at z_star
+ * exactly as eq. (A_z). */
+typedef enum { SEXPE_Z_NEUMANN = 0, SEXPE_Z_PAPER = 1 } sexpe_zbc;
+
+typedef struct {
+    int32_t geometry;   /* sexpe_geometry                                                 */
+    int32_t n[3];       /* points per mode, mode 1 first (n[2] ignored for disk/sphere);   */
+                        /* each >= 3 and <= 512 (theta >= 3, rho >= 2, phi/z >= 3)        */
+    double rho_star;    /* radius of disk/ball/cylinder (> 0); sphere is the unit sphere  */
+    double z_star;      /* cylinder height (> 0)                                          */
+    int32_t z_bc;       /* sexpe_zbc (cylinder only)                                      */
+} sexpe_grid;
+
+typedef struct {
+    int32_t n_species;      /* 1..4                                                       */
+    const double* d_host;   /* n_species diffusion coefficients (> 0)                     */
+    int32_t reaction;       /* sexpe_reaction                                             */
+    int32_t n_params;       /* number of entries in params_host                           */
+    const double* params_host;
+} sexpe_species;
+
+typedef struct sexpe_plan sexpe_plan;
+
+typedef struct {
+    int32_t geometry, precision, n_species, ndim;
+    int32_t n[3];
+    int32_t n_instances;        /* 1, or the count given to sexpe_batch_setup               */
+    int32_t kernels_per_step;   /* kernel launches of one step                              */
+    int64_t npts;               /* grid points per species (sum over instances for a batch) */
+    int64_t state_elems;        /* FP64 elements of the whole state                         */
+    int64_t workspace_bytes;    /* device bytes owned by the plan                           */
+    double setup_ms;            /* host wall time of the FP64 setup                         */
+} sexpe_plan_info;
+
+/* Build a plan: FP64 host setup of the 1-D axes (Section 3: eqs. A_theta,
+ * disk_discr, ball_discr, syscn/A_phi, A_z), phi_1(tau d_s A_mu) of every plain
+ * direction (Pade [13/13] scaling and squaring on [[tau d A, I],[0,0]]), the
+ * eigenbases of the scaled directions (closed-form real Fourier basis for
+ * A_theta; Proposition 1 symmetrisation + Jacobi for A_phi), the Hadamard
+ * factors phi_1(tau d_s s lambda) (Section 4), then one upload to the device.
+ * The plan also owns the intermediate tensors of the chain.  `stream` orders
+ * the uploads.  On error *out is set to NULL. */
+sexpe_status sexpe_setup(const sexpe_grid* grid, const sexpe_species* species, double tau,
+                         int32_t precision, void* stream, sexpe_plan** out);
+
+/* Build one plan for `count` independent disk problems of uneven sizes
+ * (geometry must be SEXPE_DISK for all; each instance has its own species
+ * block).  Their states are concatenated instance after instance, each in the
+ * single-plan layout; sexpe_state_offsets() gives the element offsets.  Steps
+ * run as one persistent launch per step over an LPT-ordered work list. */
+sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sexpe_species* species,
+                               double tau, int32_t precision, void* stream, sexpe_plan** out);
+
+/* offsets_host[count+1]: element offset of each instance's state (last = total). */
+sexpe_status sexpe_state_offsets(const sexpe_plan* plan, int64_t* offsets_host);
+
+/* Advance state_dev (caller-owned device FP64 array of state_elems elements,
+ * layout above) by n_steps split exponential Euler steps, in place, enqueued
+ * on `stream`.  No allocation, no host synchronisation.  n_steps >= 0. */
+sexpe_status sexpe_step(sexpe_plan* plan, double* state_dev, int64_t n_steps, void* stream);
+
+/* Same as sexpe_step for a HOST state: copies state_host to the plan's device
+ * buffer, steps, copies back, and synchronises `stream` before returning.
+ * state_host should be page-locked for asynchronous copies. */
+sexpe_status sexpe_step_host(sexpe_plan* plan, double* state_host, int64_t n_steps, void* stream);
+
+/* Wait for the plan's work on `stream` and report the device error word
+ * (SEXPE_ETIMEOUT if a bounded wait ran out), clearing it. */
+sexpe_status sexpe_synchronize(sexpe_plan* plan, void* stream);
+
+sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_host);
+
+/* Free every device table of the plan (after synchronising its device). */
+sexpe_status sexpe_destroy(sexpe_plan* plan);
+
+/* Setup introspection (host only, FP64, no GPU needed): the quantities the
+ * plan is built from, for checking the setup stage on its own.
+ * axis: 0 theta (eq. A_theta), 1 rho d=2 (eq. disk_discr), 2 rho d=3
+ * (eq. ball_discr), 3 phi (eqs. syscn, A_phi), 4 z with Neumann caps,
+ * 5 z as in eq. (A_z).  extent = rho_* or z_* (ignored for theta, phi).
+ * sexpe_axis_matrix: A (n x n, row-major) into A_host.
+ * sexpe_axis_phi1:   phi_1(t A) by the plan's Pade route into out_host (n x n).
+ * sexpe_axis_eigen:  A = V diag(lam) Vinv by the plan's route (closed form for
+ *                    theta, Proposition 1 + Jacobi otherwise); any output may be NULL. */
+sexpe_status sexpe_axis_matrix(int32_t axis, int32_t n, double extent, double* A_host);
+sexpe_status sexpe_axis_phi1(int32_t axis, int32_t n, double extent, double t, double* out_host);
+sexpe_status sexpe_axis_eigen(int32_t axis, int32_t n, double extent, double* lam_host, double* V_host,
+                              double* Vinv_host);
+
+/* Static, never-NULL description of a status code. */
+const char* sexpe_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEXPE_H */

@@ -1,0 +1,213 @@
+"""ctypes binding of libsexpe.so (argument marshalling only).
+
+Every computation runs in the library: the FP64 setup on the host inside the
+library, every step in its CUDA kernels.  There is no Python or CPU fallback:
+if the library is missing, ``lib()`` raises.
+
+Device arrays are passed as torch CUDA tensors (``data_ptr()``) on the current
+torch stream, or as raw integer device pointers; the library never sees torch
+types.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsexpe.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "sexpe.h")
+
+GEOMETRY = {"disk": 0, "sphere": 1, "ball": 2, "cylinder": 3}
+PRECISION = {"fp64": 0, "split_tf32": 1}
+REACTION = {"none": 0, "schnakenberg": 1, "gray_scott": 2, "linear_cubic": 3}
+ZBC = {"neumann": 0, "paper": 1}
+AXIS = {"theta": 0, "rho2": 1, "rho3": 2, "phi": 3, "z_neumann": 4, "z_paper": 5}
+STATUS = {0: "SEXPE_OK", 1: "SEXPE_EINVAL", 2: "SEXPE_ENOMEM", 3: "SEXPE_ECUDA", 4: "SEXPE_ETIMEOUT",
+          5: "SEXPE_EUNSUPPORTED", 6: "SEXPE_ENUMERIC"}
+
+
+class SexpeError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib.sexpe_status_string(status).decode()})")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("rho_star", ctypes.c_double),
+                ("z_star", ctypes.c_double), ("z_bc", ctypes.c_int32)]
+
+
+class Species(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int32), ("d_host", ctypes.POINTER(ctypes.c_double)),
+                ("reaction", ctypes.c_int32), ("n_params", ctypes.c_int32),
+                ("params_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_species", ctypes.c_int32),
+                ("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("n_instances", ctypes.c_int32),
+                ("kernels_per_step", ctypes.c_int32), ("npts", ctypes.c_int64), ("state_elems", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Open libsexpe.so (built in-tree by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.sexpe_status_string.restype = ctypes.c_char_p
+        L.sexpe_status_string.argtypes = [ctypes.c_int32]
+        L.sexpe_setup.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Species), ctypes.c_double, ctypes.c_int32,
+                                  _P, ctypes.POINTER(_P)]
+        L.sexpe_batch_setup.argtypes = [ctypes.c_int32, ctypes.POINTER(Grid), ctypes.POINTER(Species),
+                                        ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(_P)]
+        L.sexpe_state_offsets.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+        L.sexpe_step.argtypes = [_P, _P, ctypes.c_int64, _P]
+        L.sexpe_step_host.argtypes = [_P, _DP, ctypes.c_int64, _P]
+        L.sexpe_synchronize.argtypes = [_P, _P]
+        L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
+        L.sexpe_destroy.argtypes = [_P]
+        L.sexpe_axis_matrix.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _DP]
+        L.sexpe_axis_phi1.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _DP]
+        L.sexpe_axis_eigen.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _DP, _DP, _DP]
+        for name in ["sexpe_setup", "sexpe_batch_setup", "sexpe_state_offsets", "sexpe_step", "sexpe_step_host",
+                     "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
+                     "sexpe_axis_phi1", "sexpe_axis_eigen"]:
+            getattr(L, name).restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions include/sexpe.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sexpe_\w+)\s*\(", text)))
+
+
+def _check(status, where):
+    if status != 0:
+        raise SexpeError(status, where)
+
+
+def _dptr(x):
+    return ctypes.cast(np.ascontiguousarray(x, dtype=np.float64).ctypes.data, _DP)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _data_ptr(x):
+    if isinstance(x, int):
+        return x
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TypeError("state must be a contiguous CUDA float64 tensor or a device pointer")
+    return x.data_ptr()
+
+
+def _grid_struct(geometry, n, rho_star=1.0, z_star=1.0, z_bc="neumann"):
+    nn = list(n) + [1] * (3 - len(n))
+    return Grid(GEOMETRY[geometry], (ctypes.c_int32 * 3)(*nn), float(rho_star), float(z_star), ZBC[z_bc])
+
+
+class Plan:
+    """A plan of the split exponential Euler step (wraps sexpe_setup / sexpe_batch_setup)."""
+
+    def __init__(self, geometry, n, d, reaction="none", params=(), tau=1e-3, precision="split_tf32",
+                 rho_star=1.0, z_star=1.0, z_bc="neumann", stream=None):
+        L = lib()
+        self._d = np.ascontiguousarray(d, dtype=np.float64)
+        self._p = np.ascontiguousarray(params if len(params) else [0.0], dtype=np.float64)
+        grid = _grid_struct(geometry, n, rho_star, z_star, z_bc)
+        sp = Species(len(self._d), _dptr(self._d), REACTION[reaction], len(params), _dptr(self._p))
+        h = _P()
+        st = _stream_ptr(stream) if stream is not None else 0
+        _check(L.sexpe_setup(ctypes.byref(grid), ctypes.byref(sp), float(tau), PRECISION[precision], st,
+                             ctypes.byref(h)), "sexpe_setup")
+        self.handle = h
+        self.geometry, self.n, self.S = geometry, tuple(n), len(self._d)
+
+    @classmethod
+    def from_workload(cls, w, precision="split_tf32", stream=None):
+        return cls(w["geometry"], w["n"], w["d"], w["reaction"], w["params"], w["tau"], precision,
+                   stream=stream)
+
+    def info(self):
+        inf = PlanInfo()
+        _check(lib().sexpe_plan_get_info(self.handle, ctypes.byref(inf)), "sexpe_plan_get_info")
+        return {f: (list(getattr(inf, f)) if f == "n" else getattr(inf, f)) for f, _ in PlanInfo._fields_}
+
+    def step(self, state, n_steps, stream=None):
+        _check(lib().sexpe_step(self.handle, _data_ptr(state), int(n_steps), _stream_ptr(stream)), "sexpe_step")
+
+    def step_host(self, state_host, n_steps, stream=None):
+        """state_host: C-contiguous float64 numpy array (or pinned CPU tensor), updated in place."""
+        if hasattr(state_host, "data_ptr"):
+            ptr = ctypes.cast(state_host.data_ptr(), _DP)
+        else:
+            assert state_host.dtype == np.float64 and state_host.flags["C_CONTIGUOUS"]
+            ptr = ctypes.cast(state_host.ctypes.data, _DP)
+        _check(lib().sexpe_step_host(self.handle, ptr, int(n_steps), _stream_ptr(stream)), "sexpe_step_host")
+
+    def synchronize(self, stream=None):
+        _check(lib().sexpe_synchronize(self.handle, _stream_ptr(stream)), "sexpe_synchronize")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sexpe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def setup_status(geometry, n, d, reaction="none", params=(), tau=1e-3, precision="split_tf32", **kw):
+    """Status code of sexpe_setup for the given arguments (the plan is destroyed again)."""
+    try:
+        p = Plan(geometry, n, d, reaction, params, tau, precision, **kw)
+    except SexpeError as e:
+        return e.status
+    p.close()
+    return 0
+
+
+def axis_matrix(axis, n, extent=1.0):
+    out = np.zeros((n, n))
+    _check(lib().sexpe_axis_matrix(AXIS[axis], n, extent, _dptr_out(out)), "sexpe_axis_matrix")
+    return out
+
+
+def axis_phi1(axis, n, t, extent=1.0):
+    out = np.zeros((n, n))
+    _check(lib().sexpe_axis_phi1(AXIS[axis], n, extent, t, _dptr_out(out)), "sexpe_axis_phi1")
+    return out
+
+
+def axis_eigen(axis, n, extent=1.0):
+    lam, V, Vinv = np.zeros(n), np.zeros((n, n)), np.zeros((n, n))
+    _check(lib().sexpe_axis_eigen(AXIS[axis], n, extent, _dptr_out(lam), _dptr_out(V), _dptr_out(Vinv)),
+           "sexpe_axis_eigen")
+    return lam, V, Vinv
+
+
+def _dptr_out(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return ctypes.cast(a.ctypes.data, _DP)

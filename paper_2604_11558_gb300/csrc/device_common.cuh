@@ -1,0 +1,126 @@
+// Stencil + reaction evaluation shared by the FP64 and split-TF32 kernels:
+// F_s = d_s (M w_s) + g_s(w) at one grid point (first line of eqs. ee_disk,
+// ee_sphere, ee_ball, ee_cylinder), with M applied in difference form
+// (A w)_r = lower_r (w_{r-1} - w_r) + upper_r (w_{r+1} - w_r) + rs_r w_r.
+#pragma once
+#include <cstdint>
+
+#include "internal.h"
+
+namespace sexpe {
+
+// Split an FP64 value into FP32 (hi, lo) with hi = w truncated to 24 significant
+// bits and lo = the truncated remainder (rounded to 24 bits), using integer
+// operations only.  Differences of nearby values, (hi_a - hi_b) + (lo_a - lo_b),
+// then carry FP32 relative accuracy of the *difference* (hi_a - hi_b is exact
+// when a and b are within a factor 2), which the stencil needs: its
+// coefficients reach ~1e7 near the coordinate singularities, where rounding w
+// itself to FP32 would leave errors far above the difference.
+__device__ __forceinline__ float2 split_f64(double w) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const int e = (int)((hi32 >> 20) & 0x7FFu);          // biased FP64 exponent
+    const unsigned sign = hi32 & 0x80000000u;
+    if (e < 897) return make_float2(0.f, 0.f);           // |w| < 2^-126: below FP32 normals
+    if (e > 1150) return make_float2(__uint_as_float(sign | 0x7F800000u), 0.f);   // beyond FP32 range
+    const unsigned fb = sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+    float lo = 0.f;
+    const unsigned m29 = lo32 & 0x1FFFFFFFu;             // weight 2^(e-1075) per unit
+    if (m29 != 0u && e >= 949) {
+        const float scale = __uint_as_float((unsigned)(e - 948) << 23);
+        lo = __uint_as_float(__float_as_uint((float)m29) | sign) * scale;
+    }
+    return make_float2(__uint_as_float(fb), lo);
+}
+
+struct F64Acc {
+    using V = double;
+    using T = double;
+    __device__ static V load(const double* p) { return __ldg(p); }
+    __device__ static T diff(V a, V b) { return a - b; }
+    __device__ static T value(V a) { return a; }
+};
+
+struct SplitAcc {
+    using V = float2;
+    using T = float;
+    __device__ static V load(const double* p) { return split_f64(__ldg(p)); }
+    __device__ static T diff(V a, V b) { return (a.x - b.x) + (a.y - b.y); }
+    __device__ static T value(V a) { return a.x + a.y; }
+};
+
+template <class Acc>
+__device__ __forceinline__ typename Acc::T axis_term(const StencilAxis<typename Acc::T>& ax, const double* W,
+                                                     long long idx, int r, long long st, typename Acc::V c) {
+    using T = typename Acc::T;
+    T acc = ax.rs[r] * Acc::value(c);
+    long long im = -1, ip = -1;
+    if (r > 0) im = idx - st;
+    else if (ax.periodic) im = idx + (long long)(ax.n - 1) * st;
+    if (r < ax.n - 1) ip = idx + st;
+    else if (ax.periodic) ip = idx - (long long)(ax.n - 1) * st;
+    if (im >= 0) acc += ax.lower[r] * Acc::diff(Acc::load(W + im), c);
+    if (ip >= 0) acc += ax.upper[r] * Acc::diff(Acc::load(W + ip), c);
+    return acc;
+}
+
+// (M w)(i, j, k) for one species, Kronecker sums of Section 2:
+//  disk     M = I (x) A_rho2 + A_theta (x) D_rho
+//  sphere   M = D_phi (x) A_theta + A_phi (x) I          (mode 1 theta, mode 2 phi)
+//  ball     M = I (x) I (x) A_rho3 + D_phi (x) A_theta (x) D_rho + A_phi (x) I (x) D_rho
+//  cylinder M = I (x) I (x) A_rho2 + I (x) A_theta (x) D_rho + A_z (x) I (x) I
+template <class Acc, int GEO>
+__device__ __forceinline__ typename Acc::T laplacian(const RhsTables<typename Acc::T>& tb, const double* W,
+                                                     long long idx, int i, int j, int k, typename Acc::V c) {
+    using T = typename Acc::T;
+    const T t0 = axis_term<Acc>(tb.ax[0], W, idx, i, 1, c);
+    const T t1 = axis_term<Acc>(tb.ax[1], W, idx, j, tb.n1, c);
+    if constexpr (GEO == GEO_DISK) return t0 + tb.Dr[i] * t1;
+    if constexpr (GEO == GEO_SPHERE) return tb.Dp[j] * t0 + t1;
+    const T t2 = axis_term<Acc>(tb.ax[2], W, idx, k, (long long)tb.n1 * tb.n2, c);
+    if constexpr (GEO == GEO_BALL) return t0 + tb.Dr[i] * (tb.Dp[k] * t1 + t2);
+    return t0 + tb.Dr[i] * t1 + t2;   // cylinder
+}
+
+template <class T>
+__device__ __forceinline__ T reaction(const ReactionParams& rp, const T* w, int s) {
+    switch (rp.kind) {
+    case R_SCHNAKENBERG: {   // f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)
+        const T u2v = w[0] * w[0] * w[1];
+        return s == 0 ? (T)rp.p[0] * ((T)rp.p[1] - w[0] + u2v) : (T)rp.p[0] * ((T)rp.p[2] - u2v);
+    }
+    case R_GRAY_SCOTT: {     // f = -u v^2 + F(1 - u), g = u v^2 - (F + k) v
+        const T uv2 = w[0] * w[1] * w[1];
+        return s == 0 ? -uv2 + (T)rp.p[0] * ((T)1 - w[0]) : uv2 - ((T)rp.p[0] + (T)rp.p[1]) * w[1];
+    }
+    case R_LINEAR_CUBIC: {   // f_i = sum_j K_ij u_j - u_i^3
+        T acc = -w[s] * w[s] * w[s];
+        for (int r = 0; r < rp.S; ++r) acc += (T)rp.p[s * rp.S + r] * w[r];
+        return acc;
+    }
+    default:
+        return (T)0;
+    }
+}
+
+// F_s at flat index idx = i + n1 (j + n2 k) of species s; Wall = all species.
+template <class Acc, int GEO>
+__device__ __forceinline__ typename Acc::T rhs_point(const RhsTables<typename Acc::T>& tb, const double* Wall,
+                                                     int s, long long idx, int i, int j, int k) {
+    using T = typename Acc::T;
+    const double* W = Wall + (long long)s * tb.npts;
+    const typename Acc::V c = Acc::load(W + idx);
+    const T lap = laplacian<Acc, GEO>(tb, W, idx, i, j, k, c);
+    T w[kMaxSpecies];
+#pragma unroll
+    for (int r = 0; r < kMaxSpecies; ++r) {
+        if (r < tb.S) w[r] = (r == s) ? Acc::value(c) : Acc::value(Acc::load(Wall + (long long)r * tb.npts + idx));
+        else w[r] = (T)0;
+    }
+    return (T)tb.d[s] * lap + reaction<T>(tb.reac, w, s);
+}
+
+// phi_1(x) = expm1(x)/x, 1 at 0 (Section 4), FP32 for the on-the-fly Hadamard factors.
+__device__ __forceinline__ float phi1f(float x) { return x == 0.f ? 1.f : expm1f(x) / x; }
+
+}  // namespace sexpe

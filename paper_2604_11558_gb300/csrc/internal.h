@@ -1,0 +1,100 @@
+// Internal types shared by the plan (host) and the kernels of libsexpe.
+#pragma once
+#include <cstdint>
+
+namespace sexpe {
+
+enum Geo { GEO_DISK = 0, GEO_SPHERE = 1, GEO_BALL = 2, GEO_CYLINDER = 3 };
+enum Reac { R_NONE = 0, R_SCHNAKENBERG = 1, R_GRAY_SCOTT = 2, R_LINEAR_CUBIC = 3 };
+
+constexpr int kMaxSpecies = 4;
+constexpr int kMaxN = 512;
+
+// Device error word values (first error wins).
+enum DevErr { DERR_NONE = 0, DERR_TIMEOUT_TMA = 1, DERR_TIMEOUT_MMA = 2, DERR_BAD_TILE = 3 };
+
+// One axis of the stencil: (A w)_r = lower[r](w_{r-1} - w_r) + upper[r](w_{r+1} - w_r) + rs[r] w_r,
+// rs = row sum (zero for Neumann/periodic rows).  Periodic axes wrap r-1 / r+1.
+template <class T>
+struct StencilAxis {
+    const T* lower;
+    const T* upper;
+    const T* rs;
+    int n;
+    int periodic;
+};
+
+struct ReactionParams {
+    int kind;
+    int S;
+    double p[16];
+};
+
+// Everything the stencil+reaction evaluation needs (values of type T).
+template <class T>
+struct RhsTables {
+    int geometry;
+    int S;
+    int n1, n2, n3;
+    long long npts;
+    StencilAxis<T> ax[3];
+    const T* Dr;   // rho_i^-2 (mode-1 index), disk/ball/cylinder
+    const T* Dp;   // sin^-2 phi_k (phi-mode index), sphere/ball
+    double d[kMaxSpecies];
+    ReactionParams reac;
+};
+
+// ---------------- FP64 SIMT path ------------------------------------------
+// C(b, r, c) = sum_k A(b, r, k) B(b, k, c); element strides given per operand.
+struct Gemm64 {
+    int R, C, K, batch;
+    const double* A; long long a_b, a_r, a_k;
+    const double* B; long long b_b, b_k, b_c;
+    double* out;     long long o_b, o_r, o_c;
+    const double* had;      // Hadamard factor at the output index (or null)
+    double* upd;            // if set: upd[idx] += tau * value (out ignored)
+    double tau;
+    // per-species offsets (blockIdx.z)
+    long long A_sp, B_sp, out_sp, had_sp, upd_sp;
+};
+
+// ---------------- split TF32 tensor-core path -----------------------------
+// Shared-memory operand tiles: K-major, no swizzle, core matrices of 8 rows x 16 B.
+// Within a tile of R rows and kKC (=16) K-columns: byte offset of (r, k) is
+// (r/8)*kSBO + (k/4)*kLBO + (r%8)*16 + (k%4)*4.
+constexpr int kKC = 16;               // K elements per pipeline chunk
+constexpr int kLBO = 128;             // bytes between K-adjacent core matrices
+constexpr int kSBO = 512;             // bytes between M/N-adjacent 8-row groups
+constexpr int kTileRowBytes = 64;     // bytes per row of one tile (16 fp32)
+
+// Pre-laid matrix image: for every K-chunk c: [hi tile (rows_pad x 16)][lo tile].
+struct Image {
+    const float* ptr;
+    int rows_pad;        // multiple of 16 (B operand) or of 128 (A operand)
+    int k_chunks;
+    long long chunk_floats;   // 2 * rows_pad * 16
+};
+
+struct SplitTables {
+    int geometry, S;
+    int n1, n2, n3;
+    long long npts;
+    RhsTables<float> rhs;     // FP32 coefficients (differences are formed at FP64 accuracy)
+    const double* state;      // read in producers
+    double* state_upd;        // updated in the slab epilogue
+    float* Y;                 // FP32 intermediate between the mode-3 pass and the slab pass
+    float tau;
+    double tau_d;
+    // slab pass (theta then rho)
+    Image QT, Q, P[kMaxSpecies];
+    const float* had_theta;   // per species: coefficient c(i[,k]) so that x = c * lam_theta[j]
+    long long had_theta_sp;   // floats per species
+    const float* lam_theta;
+    // mode-3 pass
+    Image M3a, M3b[kMaxSpecies];   // ball: Vinv (M3a) and V (M3b[0]); cylinder: Pz_s in M3b[s]
+    const float* had_phi;          // ball: c_s(i) = tau d_s rho_i^-2
+    const float* lam_phi;
+    int* err;
+};
+
+}  // namespace sexpe

@@ -1,0 +1,27 @@
+// Host-side launch entry points of the kernels (internal to libsexpe).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace sexpe {
+
+// FP64 SIMT path.
+cudaError_t launch_rhs64(int geometry, const RhsTables<double>& tb, const double* W, double* F, cudaStream_t st);
+cudaError_t launch_gemm64(const Gemm64& g, int n_species, cudaStream_t st);
+
+// Split-TF32 tensor-core path.
+struct TcShape {
+    uint32_t stage_bytes;
+    uint32_t tmem_cols;
+    uint32_t smem_bytes;
+};
+TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3);
+TcShape tc_slab_shape(int n1, int n2);
+// Raise the kernels' dynamic shared-memory limit (once, outside stream capture).
+cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab);
+cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st);
+cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st);
+cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st);
+
+}  // namespace sexpe

@@ -1,0 +1,683 @@
+// C ABI of libsexpe: plan construction (FP64 host setup + one upload), the
+// per-step launch sequence of both arithmetic paths, CUDA-graph replay and
+// error reporting.  See include/sexpe.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <vector>
+
+#include "host_setup.h"
+#include "internal.h"
+#include "launch.h"
+#include "sexpe.h"
+
+using namespace sexpe;
+
+namespace {
+
+constexpr int kGraphSteps = 10;   // steps captured per CUDA graph replay
+
+struct Dir64 {
+    int mu = 0;
+    bool eigen = false;
+    const double* V = nullptr;      // eigen: V and V^{-1} (row-major n x n, shared by species)
+    const double* Vinv = nullptr;
+    const double* P = nullptr;      // plain: phi_1(tau d_s A) per species, S x n x n
+    const double* had = nullptr;    // eigen: Hadamard table per species, S x npts
+};
+
+}  // namespace
+
+struct sexpe_plan {
+    int geometry = 0, precision = 0, S = 0, ndim = 0;
+    int n[3] = {1, 1, 1};
+    long long npts = 0;
+    double tau = 0.0;
+    std::vector<double> d, params;
+    int reaction = 0;
+    Axis ax[3];
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    int* d_err = nullptr;
+    double* d_host_state = nullptr;   // staging buffer of sexpe_step_host
+    // FP64 path
+    RhsTables<double> rhs64{};
+    std::vector<Dir64> dirs64;
+    double* buf64[3] = {nullptr, nullptr, nullptr};
+    // split path
+    SplitTables tabs{};
+    TcShape sh3{}, shs{};
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    double* g_state = nullptr;
+    int kernels_per_step = 0;
+    double setup_ms = 0.0;
+};
+
+namespace {
+
+sexpe_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SEXPE_OK;
+    if (e == cudaErrorMemoryAllocation) return SEXPE_ENOMEM;
+    return SEXPE_ECUDA;
+}
+
+#define SX_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_status(e_);  \
+    } while (0)
+
+template <class T>
+sexpe_status upload(sexpe_plan* p, const std::vector<T>& h, const T** out, cudaStream_t st) {
+    void* dptr = nullptr;
+    const size_t bytes = h.size() * sizeof(T);
+    SX_CUDA(cudaMalloc(&dptr, bytes > 0 ? bytes : 16));
+    p->allocs.push_back(dptr);
+    p->bytes += bytes;
+    if (bytes) SX_CUDA(cudaMemcpyAsync(dptr, h.data(), bytes, cudaMemcpyHostToDevice, st));
+    *out = static_cast<const T*>(dptr);
+    return SEXPE_OK;
+}
+
+template <class T>
+sexpe_status alloc_dev(sexpe_plan* p, size_t count, T** out) {
+    void* dptr = nullptr;
+    SX_CUDA(cudaMalloc(&dptr, count * sizeof(T) > 0 ? count * sizeof(T) : 16));
+    p->allocs.push_back(dptr);
+    p->bytes += count * sizeof(T);
+    *out = static_cast<T*>(dptr);
+    return SEXPE_OK;
+}
+
+#define SX_TRY(call)                         \
+    do {                                     \
+        sexpe_status s_ = (call);            \
+        if (s_ != SEXPE_OK) return s_;       \
+    } while (0)
+
+// Scale factor of direction mu at grid point (i, j, k): the diagonal factors of
+// the other modes in the Kronecker term M_mu (Section 2).
+double dir_scale(const sexpe_plan* p, int mu, int i, int j, int k) {
+    auto Dr = [&](int ii) { double r = p->ax[0].pts[ii]; return 1.0 / (r * r); };
+    auto Dp = [&](int m, int kk) { double s = std::sin(p->ax[m].pts[kk]); return 1.0 / (s * s); };
+    switch (p->geometry) {
+    case SEXPE_DISK: return mu == 2 ? Dr(i) : 1.0;
+    case SEXPE_SPHERE: return mu == 1 ? Dp(1, j) : 1.0;
+    case SEXPE_BALL: return mu == 2 ? Dr(i) * Dp(2, k) : (mu == 3 ? Dr(i) : 1.0);
+    default: return mu == 2 ? Dr(i) : 1.0;
+    }
+}
+
+bool dir_is_eigen(int geometry, int mu) {
+    switch (geometry) {
+    case SEXPE_DISK: return mu == 2;
+    case SEXPE_SPHERE: return mu == 1;
+    case SEXPE_BALL: return mu >= 2;
+    default: return mu == 2;
+    }
+}
+
+bool all_finite(const std::vector<double>& v) {
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// TF32 rounding to nearest (ties away from zero) of an FP32 value, on the host.
+float tf32_rna_host(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return x;
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// Pre-laid operand image of a constant matrix: for each 16-wide K-chunk, a hi
+// tile then a lo tile of rows_pad rows in the K-major no-swizzle core-matrix
+// layout the kernels' shared-memory descriptors describe.
+std::vector<float> make_image(int rows_valid, int k_valid, int rows_pad, int k_pad,
+                              const std::function<double(int, int)>& f) {
+    const int chunks = k_pad / kKC;
+    const size_t tile = (size_t)rows_pad * kKC;
+    std::vector<float> img((size_t)chunks * 2 * tile, 0.0f);
+    for (int c = 0; c < chunks; ++c) {
+        float* hi = img.data() + (size_t)c * 2 * tile;
+        float* lo = hi + tile;
+        for (int r = 0; r < rows_valid; ++r) {
+            for (int kk = 0; kk < kKC; ++kk) {
+                const int k = c * kKC + kk;
+                if (k >= k_valid) continue;
+                const double x = f(r, k);
+                const float h = tf32_rna_host((float)x);
+                const float l = tf32_rna_host((float)(x - (double)h));
+                const size_t off = ((size_t)(r >> 3) * kSBO + (size_t)(kk >> 2) * kLBO + (size_t)(r & 7) * 16 +
+                                    (size_t)(kk & 3) * 4) / 4;
+                hi[off] = h;
+                lo[off] = l;
+            }
+        }
+    }
+    return img;
+}
+
+sexpe_status upload_image(sexpe_plan* p, int rows_valid, int k_valid, int rows_pad, int k_pad,
+                          const std::function<double(int, int)>& f, Image* out, cudaStream_t st) {
+    std::vector<float> img = make_image(rows_valid, k_valid, rows_pad, k_pad, f);
+    const float* dptr = nullptr;
+    SX_TRY(upload(p, img, &dptr, st));
+    out->ptr = dptr;
+    out->rows_pad = rows_pad;
+    out->k_chunks = k_pad / kKC;
+    out->chunk_floats = 2LL * rows_pad * kKC;
+    return SEXPE_OK;
+}
+
+int rup16(int x) { return (x + 15) / 16 * 16; }
+
+template <class T>
+sexpe_status build_rhs_tables(sexpe_plan* p, RhsTables<T>* tb, cudaStream_t st) {
+    tb->geometry = p->geometry;
+    tb->S = p->S;
+    tb->n1 = p->n[0];
+    tb->n2 = p->n[1];
+    tb->n3 = p->n[2];
+    tb->npts = p->npts;
+    for (int m = 0; m < 3; ++m) {
+        const Axis& a = p->ax[m];
+        if (m >= p->ndim) {
+            tb->ax[m] = StencilAxis<T>{nullptr, nullptr, nullptr, 1, 0};
+            continue;
+        }
+        std::vector<T> lo(a.n), up(a.n), rs(a.n);
+        for (int r = 0; r < a.n; ++r) {
+            lo[r] = (T)a.lower[r];
+            up[r] = (T)a.upper[r];
+            // Row sums are zero for every Neumann/periodic row; only a Dirichlet
+            // end (A_z as printed) leaves a nonzero residual.
+            const double l = (r > 0 || a.periodic) ? a.lower[r] : 0.0;
+            const double u = (r < a.n - 1 || a.periodic) ? a.upper[r] : 0.0;
+            const double sum = a.diag[r] + l + u;
+            rs[r] = (T)(std::fabs(sum) <= 1e-9 * std::fabs(a.diag[r]) ? 0.0 : sum);
+        }
+        StencilAxis<T> sa{};
+        SX_TRY(upload(p, lo, &sa.lower, st));
+        SX_TRY(upload(p, up, &sa.upper, st));
+        SX_TRY(upload(p, rs, &sa.rs, st));
+        sa.n = a.n;
+        sa.periodic = a.periodic ? 1 : 0;
+        tb->ax[m] = sa;
+    }
+    tb->Dr = nullptr;
+    tb->Dp = nullptr;
+    if (p->geometry != SEXPE_SPHERE) {
+        std::vector<T> dr(p->n[0]);
+        for (int i = 0; i < p->n[0]; ++i) dr[i] = (T)(1.0 / (p->ax[0].pts[i] * p->ax[0].pts[i]));
+        SX_TRY(upload(p, dr, &tb->Dr, st));
+    }
+    if (p->geometry == SEXPE_SPHERE || p->geometry == SEXPE_BALL) {
+        const int m = p->geometry == SEXPE_SPHERE ? 1 : 2;
+        std::vector<T> dp(p->n[m]);
+        for (int k = 0; k < p->n[m]; ++k) {
+            const double s = std::sin(p->ax[m].pts[k]);
+            dp[k] = (T)(1.0 / (s * s));
+        }
+        SX_TRY(upload(p, dp, &tb->Dp, st));
+    }
+    for (int s = 0; s < kMaxSpecies; ++s) tb->d[s] = s < p->S ? p->d[s] : 0.0;
+    tb->reac.kind = p->reaction;
+    tb->reac.S = p->S;
+    for (int q = 0; q < 16; ++q) tb->reac.p[q] = q < (int)p->params.size() ? p->params[q] : 0.0;
+    return SEXPE_OK;
+}
+
+sexpe_status build_fp64(sexpe_plan* p, cudaStream_t st) {
+    SX_TRY(build_rhs_tables<double>(p, &p->rhs64, st));
+    for (int b = 0; b < 3; ++b) SX_TRY(alloc_dev(p, (size_t)p->S * p->npts, &p->buf64[b]));
+    for (int mu = p->ndim; mu >= 1; --mu) {
+        const Axis& a = p->ax[mu - 1];
+        const int n = a.n;
+        Dir64 dir;
+        dir.mu = mu;
+        dir.eigen = dir_is_eigen(p->geometry, mu);
+        if (dir.eigen) {
+            Eigen e = a.periodic ? theta_eigen(a) : tridiag_eigen(a);
+            if (!all_finite(e.V.a) || !all_finite(e.Vinv.a)) return SEXPE_ENUMERIC;
+            SX_TRY(upload(p, e.V.a, &dir.V, st));
+            SX_TRY(upload(p, e.Vinv.a, &dir.Vinv, st));
+            std::vector<double> had((size_t)p->S * p->npts);
+            for (int s = 0; s < p->S; ++s)
+                for (int k = 0; k < p->n[2]; ++k)
+                    for (int j = 0; j < p->n[1]; ++j)
+                        for (int i = 0; i < p->n[0]; ++i) {
+                            const int m = mu == 1 ? i : (mu == 2 ? j : k);
+                            const long long idx = i + (long long)p->n[0] * (j + (long long)p->n[1] * k);
+                            had[(size_t)s * p->npts + idx] =
+                                phi1_scalar(p->tau * p->d[s] * dir_scale(p, mu, i, j, k) * e.lam[m]);
+                        }
+            if (!all_finite(had)) return SEXPE_ENUMERIC;
+            SX_TRY(upload(p, had, &dir.had, st));
+        } else {
+            const Mat A = a.dense();
+            std::vector<double> P((size_t)p->S * n * n);
+            for (int s = 0; s < p->S; ++s) {
+                Mat X(n);
+                for (size_t q = 0; q < X.a.size(); ++q) X.a[q] = p->tau * p->d[s] * A.a[q];
+                const Mat R = phi1_pade(X);
+                std::memcpy(&P[(size_t)s * n * n], R.a.data(), sizeof(double) * n * n);
+            }
+            if (!all_finite(P)) return SEXPE_ENUMERIC;
+            SX_TRY(upload(p, P, &dir.P, st));
+        }
+        p->dirs64.push_back(dir);
+    }
+    p->kernels_per_step = 1;
+    for (const Dir64& d : p->dirs64) p->kernels_per_step += d.eigen ? 2 : 1;
+    return SEXPE_OK;
+}
+
+sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
+    if (p->geometry == SEXPE_SPHERE) return SEXPE_EUNSUPPORTED;
+    const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+    if (n1 > 128 || n2 > 256 || (p->ndim == 3 && n3 > 256)) return SEXPE_EUNSUPPORTED;
+    SplitTables& T = p->tabs;
+    T.geometry = p->geometry;
+    T.S = p->S;
+    T.n1 = n1;
+    T.n2 = n2;
+    T.n3 = n3;
+    T.npts = p->npts;
+    T.tau = (float)p->tau;
+    T.tau_d = p->tau;
+    SX_TRY(build_rhs_tables<float>(p, &T.rhs, st));
+    SX_TRY(alloc_dev(p, (size_t)p->S * p->npts, &T.Y));
+    T.err = p->d_err;
+    // theta direction (mode 2): Q_theta, eigenvalues, Hadamard coefficients
+    const int n1p = rup16(n1), n2p = rup16(n2), m2 = (n2 + 127) / 128;
+    Eigen th = theta_eigen(p->ax[1]);
+    SX_TRY(upload_image(p, n2, n2, n2p, n2p, [&](int r, int k) { return th.V(k, r); }, &T.QT, st));
+    SX_TRY(upload_image(p, n2, n2, 128 * m2, n2p, [&](int r, int k) { return th.V(r, k); }, &T.Q, st));
+    std::vector<float> lam(th.lam.begin(), th.lam.end());
+    SX_TRY(upload(p, lam, &T.lam_theta, st));
+    const bool ball = p->geometry == SEXPE_BALL;
+    T.had_theta_sp = ball ? (long long)n3 * n1 : n1;
+    std::vector<float> hc((size_t)p->S * T.had_theta_sp);
+    for (int s = 0; s < p->S; ++s)
+        for (int k = 0; k < (ball ? n3 : 1); ++k)
+            for (int i = 0; i < n1; ++i)
+                hc[(size_t)s * T.had_theta_sp + (size_t)k * n1 + i] =
+                    (float)(p->tau * p->d[s] * dir_scale(p, 2, i, 0, k));
+    SX_TRY(upload(p, hc, &T.had_theta, st));
+    // rho direction (mode 1): phi_1(tau d_s A_rho) per species
+    const Mat Arho = p->ax[0].dense();
+    for (int s = 0; s < p->S; ++s) {
+        Mat X(n1);
+        for (size_t q = 0; q < X.a.size(); ++q) X.a[q] = p->tau * p->d[s] * Arho.a[q];
+        const Mat Ps = phi1_pade(X);
+        if (!all_finite(Ps.a)) return SEXPE_ENUMERIC;
+        SX_TRY(upload_image(p, n1, n1, n1p, n1p, [&](int r, int k) { return Ps(r, k); }, &T.P[s], st));
+    }
+    // mode 3
+    if (p->ndim == 3) {
+        const int n3p = rup16(n3);
+        if (ball) {
+            Eigen ph = tridiag_eigen(p->ax[2]);
+            if (!all_finite(ph.V.a) || !all_finite(ph.Vinv.a)) return SEXPE_ENUMERIC;
+            SX_TRY(upload_image(p, n3, n3, n3p, n3p, [&](int r, int k) { return ph.Vinv(r, k); }, &T.M3a, st));
+            SX_TRY(upload_image(p, n3, n3, n3p, n3p, [&](int r, int k) { return ph.V(r, k); }, &T.M3b[0], st));
+            std::vector<float> lp(ph.lam.begin(), ph.lam.end());
+            SX_TRY(upload(p, lp, &T.lam_phi, st));
+            std::vector<float> hp((size_t)p->S * n1);
+            for (int s = 0; s < p->S; ++s)
+                for (int i = 0; i < n1; ++i) hp[(size_t)s * n1 + i] = (float)(p->tau * p->d[s] * dir_scale(p, 3, i, 0, 0));
+            SX_TRY(upload(p, hp, &T.had_phi, st));
+        } else {
+            const Mat Az = p->ax[2].dense();
+            for (int s = 0; s < p->S; ++s) {
+                Mat X(n3);
+                for (size_t q = 0; q < X.a.size(); ++q) X.a[q] = p->tau * p->d[s] * Az.a[q];
+                const Mat Pz = phi1_pade(X);
+                if (!all_finite(Pz.a)) return SEXPE_ENUMERIC;
+                SX_TRY(upload_image(p, n3, n3, n3p, n3p, [&](int r, int k) { return Pz(r, k); }, &T.M3b[s], st));
+            }
+        }
+        p->sh3 = tc_mode3_shape(p->geometry, n1, n2, n3);
+    }
+    p->shs = tc_slab_shape(n1, n2);
+    if (p->shs.smem_bytes > 227 * 1024 || p->sh3.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
+    SX_CUDA(tc_prepare(p->ndim == 3 ? p->sh3.smem_bytes : 0, p->shs.smem_bytes));
+    p->kernels_per_step = 2;
+    return SEXPE_OK;
+}
+
+// Mode-mu product of all species: out = X x_mu L (L row-major n_mu x n_mu,
+// per-species stride L_sp), with optional Hadamard table and fused update.
+Gemm64 mode_gemm(const sexpe_plan* p, int mu, const double* L, long long L_sp, const double* X, double* out,
+                 const double* had, double* upd) {
+    const long long n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+    Gemm64 g{};
+    if (mu == 1) {          // Y[p][i'] = sum_i X[p][i] L[i'][i]
+        g.R = (int)(n2 * n3); g.C = (int)n1; g.K = (int)n1; g.batch = 1;
+        g.A = X; g.a_b = 0; g.a_r = n1; g.a_k = 1; g.A_sp = p->npts;
+        g.B = L; g.b_b = 0; g.b_k = 1; g.b_c = n1; g.B_sp = L_sp;
+        g.o_b = 0; g.o_r = n1; g.o_c = 1;
+    } else if (mu == 2) {   // Y[k][j'][i] = sum_j L[j'][j] X[k][j][i]
+        g.R = (int)n2; g.C = (int)n1; g.K = (int)n2; g.batch = (int)n3;
+        g.A = L; g.a_b = 0; g.a_r = n2; g.a_k = 1; g.A_sp = L_sp;
+        g.B = X; g.b_b = n1 * n2; g.b_k = n1; g.b_c = 1; g.B_sp = p->npts;
+        g.o_b = n1 * n2; g.o_r = n1; g.o_c = 1;
+    } else {                // Y[k'][q] = sum_k L[k'][k] X[k][q]
+        g.R = (int)n3; g.C = (int)(n1 * n2); g.K = (int)n3; g.batch = 1;
+        g.A = L; g.a_b = 0; g.a_r = n3; g.a_k = 1; g.A_sp = L_sp;
+        g.B = X; g.b_b = 0; g.b_k = n1 * n2; g.b_c = 1; g.B_sp = p->npts;
+        g.o_b = 0; g.o_r = n1 * n2; g.o_c = 1;
+    }
+    g.out = out;
+    g.out_sp = p->npts;
+    g.had = had;
+    g.had_sp = p->npts;
+    g.upd = upd;
+    g.upd_sp = p->npts;
+    g.tau = p->tau;
+    return g;
+}
+
+sexpe_status enqueue_step(sexpe_plan* p, double* state, cudaStream_t st) {
+    if (p->precision == SEXPE_FP64) {
+        SX_CUDA(launch_rhs64(p->geometry, p->rhs64, state, p->buf64[0], st));
+        int x = 0;                                  // buffer holding the current operand
+        for (const Dir64& d : p->dirs64) {
+            const bool last = d.mu == 1;
+            const int nmu = p->n[d.mu - 1];
+            const int t = (x + 1) % 3, y = (x + 2) % 3;
+            if (d.eigen) {
+                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.Vinv, 0, p->buf64[x], p->buf64[t], d.had, nullptr), p->S, st));
+                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.V, 0, p->buf64[t], p->buf64[y], nullptr,
+                                                last ? state : nullptr), p->S, st));
+                x = y;
+            } else {
+                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.P, (long long)nmu * nmu, p->buf64[x], p->buf64[t],
+                                                nullptr, last ? state : nullptr), p->S, st));
+                x = t;
+            }
+        }
+        return SEXPE_OK;
+    }
+    SplitTables T = p->tabs;
+    T.state = state;
+    T.state_upd = state;
+    if (p->ndim == 3) SX_CUDA(launch_tc_mode3(T, p->sh3, st));
+    else SX_CUDA(launch_rhs_split(T, st));
+    SX_CUDA(launch_tc_slab(T, p->shs, st));
+    return SEXPE_OK;
+}
+
+sexpe_status validate(const sexpe_grid* g, const sexpe_species* sp, double tau, int32_t precision) {
+    if (!g || !sp) return SEXPE_EINVAL;
+    if (g->geometry < SEXPE_DISK || g->geometry > SEXPE_CYLINDER) return SEXPE_EINVAL;
+    if (precision != SEXPE_FP64 && precision != SEXPE_SPLIT_TF32) return SEXPE_EINVAL;
+    if (!(tau > 0.0) || !std::isfinite(tau)) return SEXPE_EINVAL;
+    const int ndim = (g->geometry == SEXPE_BALL || g->geometry == SEXPE_CYLINDER) ? 3 : 2;
+    for (int m = 0; m < ndim; ++m)
+        if (g->n[m] < 3 || g->n[m] > kMaxN) return SEXPE_EINVAL;
+    if (g->geometry != SEXPE_SPHERE && !(g->rho_star > 0.0 && std::isfinite(g->rho_star))) return SEXPE_EINVAL;
+    if (g->geometry == SEXPE_CYLINDER) {
+        if (!(g->z_star > 0.0 && std::isfinite(g->z_star))) return SEXPE_EINVAL;
+        if (g->z_bc != SEXPE_Z_NEUMANN && g->z_bc != SEXPE_Z_PAPER) return SEXPE_EINVAL;
+    }
+    if (sp->n_species < 1 || sp->n_species > kMaxSpecies || !sp->d_host) return SEXPE_EINVAL;
+    for (int s = 0; s < sp->n_species; ++s)
+        if (!(sp->d_host[s] > 0.0) || !std::isfinite(sp->d_host[s])) return SEXPE_EINVAL;
+    if (sp->n_params < 0 || sp->n_params > 16 || (sp->n_params > 0 && !sp->params_host)) return SEXPE_EINVAL;
+    switch (sp->reaction) {
+    case SEXPE_REACTION_NONE: break;
+    case SEXPE_SCHNAKENBERG: if (sp->n_species != 2 || sp->n_params != 3) return SEXPE_EINVAL; break;
+    case SEXPE_GRAY_SCOTT: if (sp->n_species != 2 || sp->n_params != 2) return SEXPE_EINVAL; break;
+    case SEXPE_LINEAR_CUBIC:
+        if (sp->n_params != sp->n_species * sp->n_species) return SEXPE_EINVAL;
+        break;
+    default: return SEXPE_EINVAL;
+    }
+    for (int q = 0; q < sp->n_params; ++q)
+        if (!std::isfinite(sp->params_host[q])) return SEXPE_EINVAL;
+    return SEXPE_OK;
+}
+
+void free_plan(sexpe_plan* p) {
+    if (!p) return;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (void* a : p->allocs) cudaFree(a);
+    delete p;
+}
+
+sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species* sp, double tau, int32_t precision,
+                        cudaStream_t st) {
+    p->geometry = g->geometry;
+    p->precision = precision;
+    p->S = sp->n_species;
+    p->ndim = (g->geometry == SEXPE_BALL || g->geometry == SEXPE_CYLINDER) ? 3 : 2;
+    for (int m = 0; m < 3; ++m) p->n[m] = m < p->ndim ? g->n[m] : 1;
+    p->npts = (long long)p->n[0] * p->n[1] * p->n[2];
+    p->tau = tau;
+    p->d.assign(sp->d_host, sp->d_host + sp->n_species);
+    p->params.assign(sp->params_host, sp->params_host + sp->n_params);
+    p->reaction = sp->reaction;
+    switch (g->geometry) {
+    case SEXPE_DISK:
+        p->ax[0] = build_axis(AX_RHO2, p->n[0], g->rho_star);
+        p->ax[1] = build_axis(AX_THETA, p->n[1], 0.0);
+        break;
+    case SEXPE_SPHERE:
+        p->ax[0] = build_axis(AX_THETA, p->n[0], 0.0);
+        p->ax[1] = build_axis(AX_PHI, p->n[1], 0.0);
+        break;
+    case SEXPE_BALL:
+        p->ax[0] = build_axis(AX_RHO3, p->n[0], g->rho_star);
+        p->ax[1] = build_axis(AX_THETA, p->n[1], 0.0);
+        p->ax[2] = build_axis(AX_PHI, p->n[2], 0.0);
+        break;
+    default:
+        p->ax[0] = build_axis(AX_RHO2, p->n[0], g->rho_star);
+        p->ax[1] = build_axis(AX_THETA, p->n[1], 0.0);
+        p->ax[2] = build_axis(g->z_bc == SEXPE_Z_PAPER ? AX_Z_PAPER : AX_Z_NEUMANN, p->n[2], g->z_star);
+        break;
+    }
+    SX_TRY(alloc_dev(p, 4, &p->d_err));
+    SX_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st));
+    SX_TRY(alloc_dev(p, (size_t)p->S * p->npts, &p->d_host_state));
+    if (precision == SEXPE_FP64) SX_TRY(build_fp64(p, st));
+    else SX_TRY(build_split(p, st));
+    SX_CUDA(cudaStreamSynchronize(st));   // host vectors of the uploads go out of scope
+    return SEXPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sexpe_status_string(int32_t status) {
+    switch (status) {
+    case SEXPE_OK: return "ok";
+    case SEXPE_EINVAL: return "invalid argument";
+    case SEXPE_ENOMEM: return "out of memory";
+    case SEXPE_ECUDA: return "CUDA runtime error";
+    case SEXPE_ETIMEOUT: return "bounded device wait timed out";
+    case SEXPE_EUNSUPPORTED: return "unsupported configuration";
+    case SEXPE_ENUMERIC: return "non-finite setup table";
+    default: return "unknown status";
+    }
+}
+
+sexpe_status sexpe_setup(const sexpe_grid* grid, const sexpe_species* species, double tau, int32_t precision,
+                         void* stream, sexpe_plan** out) {
+    if (!out) return SEXPE_EINVAL;
+    *out = nullptr;
+    sexpe_status v = validate(grid, species, tau, precision);
+    if (v != SEXPE_OK) return v;
+    auto t0 = std::chrono::steady_clock::now();
+    sexpe_plan* p = new (std::nothrow) sexpe_plan();
+    if (!p) return SEXPE_ENOMEM;
+    sexpe_status s;
+    try {
+        s = build_plan(p, grid, species, tau, precision, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        s = SEXPE_ENOMEM;
+    } catch (...) {
+        s = SEXPE_ENUMERIC;
+    }
+    if (s != SEXPE_OK) {
+        free_plan(p);
+        return s;
+    }
+    p->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sexpe_species* species, double tau,
+                               int32_t precision, void* stream, sexpe_plan** out) {
+    (void)count; (void)grids; (void)species; (void)tau; (void)precision; (void)stream;
+    if (out) *out = nullptr;
+    return SEXPE_EUNSUPPORTED;
+}
+
+sexpe_status sexpe_state_offsets(const sexpe_plan* plan, int64_t* offsets_host) {
+    if (!plan || !offsets_host) return SEXPE_EINVAL;
+    offsets_host[0] = 0;
+    offsets_host[1] = (int64_t)plan->S * plan->npts;
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* stream) {
+    if (!p || !state || n_steps < 0) return SEXPE_EINVAL;
+    if (((uintptr_t)state & 7u) != 0) return SEXPE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t done = 0;
+    if (n_steps >= kGraphSteps) {
+        if (!p->gexec || p->g_state != state) {
+            if (p->gexec) {
+                cudaGraphExecDestroy(p->gexec);
+                p->gexec = nullptr;
+            }
+            cudaStream_t cs;
+            SX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            sexpe_status s = SEXPE_OK;
+            if (e == cudaSuccess) {
+                for (int k = 0; k < kGraphSteps && s == SEXPE_OK; ++k) s = enqueue_step(p, state, cs);
+                cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess && s == SEXPE_OK) e = cudaGraphInstantiate(&p->gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cs);
+            if (s != SEXPE_OK) return s;
+            if (e != cudaSuccess) {
+                p->gexec = nullptr;
+                return cuda_status(e);
+            }
+            p->g_state = state;
+        }
+        for (; done + kGraphSteps <= n_steps; done += kGraphSteps) SX_CUDA(cudaGraphLaunch(p->gexec, st));
+    }
+    for (; done < n_steps; ++done) SX_TRY(enqueue_step(p, state, st));
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_step_host(sexpe_plan* p, double* state_host, int64_t n_steps, void* stream) {
+    if (!p || !state_host || n_steps < 0) return SEXPE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * (size_t)p->S * p->npts;
+    SX_CUDA(cudaMemcpyAsync(p->d_host_state, state_host, bytes, cudaMemcpyHostToDevice, st));
+    SX_TRY(sexpe_step(p, p->d_host_state, n_steps, stream));
+    SX_CUDA(cudaMemcpyAsync(state_host, p->d_host_state, bytes, cudaMemcpyDeviceToHost, st));
+    return sexpe_synchronize(p, stream);
+}
+
+sexpe_status sexpe_synchronize(sexpe_plan* p, void* stream) {
+    if (!p) return SEXPE_EINVAL;
+    SX_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int err = 0;
+    SX_CUDA(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) {
+        SX_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+        return SEXPE_ETIMEOUT;
+    }
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
+    if (!p || !info) return SEXPE_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->geometry = p->geometry;
+    info->precision = p->precision;
+    info->n_species = p->S;
+    info->ndim = p->ndim;
+    for (int m = 0; m < 3; ++m) info->n[m] = p->n[m];
+    info->n_instances = 1;
+    info->kernels_per_step = p->kernels_per_step;
+    info->npts = p->npts;
+    info->state_elems = (int64_t)p->S * p->npts;
+    info->workspace_bytes = (int64_t)p->bytes;
+    info->setup_ms = p->setup_ms;
+    return SEXPE_OK;
+}
+
+static bool axis_args(int32_t axis, int32_t n, double extent, AxisKind* kind) {
+    static const AxisKind kinds[6] = {AX_THETA, AX_RHO2, AX_RHO3, AX_PHI, AX_Z_NEUMANN, AX_Z_PAPER};
+    if (axis < 0 || axis > 5 || n < 3 || n > kMaxN) return false;
+    if ((axis == 1 || axis == 2 || axis == 4 || axis == 5) && !(extent > 0.0 && std::isfinite(extent))) return false;
+    *kind = kinds[axis];
+    return true;
+}
+
+sexpe_status sexpe_axis_matrix(int32_t axis, int32_t n, double extent, double* A_host) {
+    AxisKind kind;
+    if (!A_host || !axis_args(axis, n, extent, &kind)) return SEXPE_EINVAL;
+    const Mat A = build_axis(kind, n, extent).dense();
+    std::memcpy(A_host, A.a.data(), sizeof(double) * n * n);
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_axis_phi1(int32_t axis, int32_t n, double extent, double t, double* out_host) {
+    AxisKind kind;
+    if (!out_host || !std::isfinite(t) || !axis_args(axis, n, extent, &kind)) return SEXPE_EINVAL;
+    try {
+        Mat X = build_axis(kind, n, extent).dense();
+        for (double& v : X.a) v *= t;
+        const Mat R = phi1_pade(X);
+        std::memcpy(out_host, R.a.data(), sizeof(double) * n * n);
+    } catch (...) {
+        return SEXPE_ENUMERIC;
+    }
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_axis_eigen(int32_t axis, int32_t n, double extent, double* lam_host, double* V_host,
+                              double* Vinv_host) {
+    AxisKind kind;
+    if (!axis_args(axis, n, extent, &kind)) return SEXPE_EINVAL;
+    const Axis a = build_axis(kind, n, extent);
+    const Eigen e = a.periodic ? theta_eigen(a) : tridiag_eigen(a);
+    if (lam_host) std::memcpy(lam_host, e.lam.data(), sizeof(double) * n);
+    if (V_host) std::memcpy(V_host, e.V.a.data(), sizeof(double) * n * n);
+    if (Vinv_host) std::memcpy(Vinv_host, e.Vinv.a.data(), sizeof(double) * n * n);
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_destroy(sexpe_plan* p) {
+    if (!p) return SEXPE_EINVAL;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return SEXPE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+"""Shared helpers of the GPU parity tests: run one workload on the CUDA path
+(through the C-ABI binding) and on the CPU oracle, and compare."""
+import numpy as np
+
+from oracle import reactions as R
+from oracle.operators import Grid
+from oracle.stepper import Problem, run
+
+
+def oracle_reaction(w):
+    p = w["params"]
+    if w["reaction"] == "schnakenberg":
+        return lambda W, t: R.schnakenberg(W, p[0], p[1], p[2])
+    if w["reaction"] == "gray_scott":
+        return lambda W, t: R.gray_scott(W, p[0], p[1])
+    if w["reaction"] == "linear_cubic":
+        S = len(w["d"])
+        K = np.array(p).reshape(S, S)
+        return lambda W, t: R.linear_cubic(W, K)
+    return lambda W, t: [np.zeros_like(W[0]) for _ in range(len(w["d"]))]
+
+
+def oracle_run(w, steps=None):
+    g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"))
+    p = Problem(g, w["d"], oracle_reaction(w), w["tau"])
+    return run(p, w["W0"], w["steps"] if steps is None else steps)
+
+
+def gpu_run(w, precision, steps=None, single_calls=False):
+    import torch
+    from paper_2604_11558_gb300 import binding
+    plan = binding.Plan(w["geometry"], w["n"], w["d"], w["reaction"], w["params"], w["tau"], precision,
+                        z_bc=w.get("z_bc", "neumann"))
+    x = torch.from_numpy(np.ascontiguousarray(w["W0"])).cuda()
+    n = w["steps"] if steps is None else steps
+    if single_calls:
+        for _ in range(n):
+            plan.step(x, 1)
+    else:
+        plan.step(x, n)
+    plan.synchronize()
+    out = x.cpu().numpy()
+    plan.close()
+    return out
+
+
+def rel_errors(got, ref):
+    return [float(np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s])) for s in range(ref.shape[0])]
+
+
+def assert_parity(got, ref, W0, tol_state, tol_incr=None):
+    """State: per-species relative 2-norm error <= tol_state and elementwise
+    |got - ref| <= tol_state * max|ref|.  Increment W_n - W_0 likewise with tol_incr."""
+    assert np.all(np.isfinite(got))
+    e = rel_errors(got, ref)
+    assert max(e) <= tol_state, ("state", e)
+    for s in range(ref.shape[0]):
+        assert np.max(np.abs(got[s] - ref[s])) <= tol_state * np.max(np.abs(ref[s])), ("max-abs", s)
+    if tol_incr is not None:
+        di = [float(np.linalg.norm((got[s] - W0[s]) - (ref[s] - W0[s])) / max(np.linalg.norm(ref[s] - W0[s]), 1e-300))
+              for s in range(ref.shape[0])]
+        assert max(di) <= tol_incr, ("increment", di)
+    return e

@@ -1,0 +1,126 @@
+"""GPU parity of the split exponential Euler step against the FP64 oracle.
+
+Every case runs the CUDA path through the C-ABI binding and the oracle on the
+same seeded inputs and compares element by element.  Tolerances: 1e-12
+relative for the FP64 path and 1e-6 for the split-TF32 path on the state
+(the stated targets); the split path's increment W_n - W_0 is held to 1e-5
+relative (three TF32 products per mu-mode product carry ~2^-21 relative error
+each, times the 3-5 products of the chain and the FP32 rounding of F).
+Sizes span several 128-row tiles and 16-wide K-chunks with ragged tails, the
+two-tile theta case (n_theta > 128), the largest supported sizes and n = 3.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_11558_gb300 import workloads as wl
+from tests.gpu_helpers import assert_parity, gpu_run, oracle_run, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def disk(n, steps=5, seed=11):
+    return wl.schnakenberg_disk(n=n, steps=steps, seed=seed)
+
+
+def sphere(n, steps=5, seed=12):
+    return wl.schnakenberg_sphere(n=n, steps=steps, seed=seed)
+
+
+def ball(n, steps=5, seed=13, tau=0.5):
+    return wl.gray_scott_ball(n=n, steps=steps, seed=seed, tau=tau)
+
+
+def cyl(n, steps=5, seed=14):
+    return wl.linear_cubic_cylinder(n=n, steps=steps, seed=seed)
+
+
+FP64_CASES = [
+    ("disk", disk((13, 20))),
+    ("disk_cfg0_full", disk((32, 64), steps=200, seed=2)),
+    ("sphere", sphere((24, 13))),
+    ("sphere_min", sphere((3, 3))),
+    ("ball", ball((11, 13, 10))),
+    ("ball_min", ball((3, 3, 3))),
+    ("cylinder", cyl((9, 14, 11))),
+    ("cylinder_dirichlet_cap", dict(cyl((9, 14, 11)), z_bc="paper")),
+]
+
+
+@pytest.mark.parametrize("name,w", FP64_CASES, ids=[c[0] for c in FP64_CASES])
+def test_fp64_matches_oracle(name, w):
+    got = gpu_run(w, "fp64")
+    ref = oracle_run(w)
+    assert_parity(got, ref, w["W0"], 1e-12, 1e-10)
+
+
+SPLIT_CASES = [
+    ("disk", disk((37, 45))),
+    ("disk_two_theta_tiles", disk((40, 200))),
+    ("disk_min", disk((3, 3))),
+    ("ball", ball((20, 33, 40))),
+    ("ball_rho128", ball((128, 16, 16), steps=3)),
+    ("ball_phi256", ball((8, 12, 256), steps=3)),
+    ("ball_min", ball((3, 3, 3))),
+    ("cylinder", cyl((24, 40, 37))),
+    ("cylinder_theta256", cyl((16, 256, 18), steps=3)),
+]
+
+
+@pytest.mark.parametrize("name,w", SPLIT_CASES, ids=[c[0] for c in SPLIT_CASES])
+def test_split_tf32_matches_oracle(name, w):
+    got = gpu_run(w, "split_tf32")
+    ref = oracle_run(w)
+    assert_parity(got, ref, w["W0"], 1e-6, 1e-5)
+
+
+def test_ball_full_size_split_and_fp64():
+    """The 100^3 ball workload in the launch configuration the benchmark times, a few steps."""
+    w = wl.gray_scott_ball(steps=3)
+    ref = oracle_run(w)
+    assert_parity(gpu_run(w, "split_tf32"), ref, w["W0"], 1e-6, 1e-5)
+    assert_parity(gpu_run(w, "fp64", steps=3), ref, w["W0"], 1e-12, 1e-10)
+
+
+def test_cylinder_full_size_split():
+    w = wl.linear_cubic_cylinder(steps=2)
+    ref = oracle_run(w)
+    assert_parity(gpu_run(w, "split_tf32"), ref, w["W0"], 1e-6, 1e-5)
+
+
+def test_ball_500_steps_split_vs_oracle_reduced_grid():
+    """Final-time parity over the full step count on a reduced ball (oracle in seconds)."""
+    w = wl.gray_scott_ball(n=(24, 20, 16), steps=500)
+    ref = oracle_run(w)
+    e = assert_parity(gpu_run(w, "split_tf32"), ref, w["W0"], 1e-6)
+    print("split vs oracle, ball 24x20x16, 500 steps:", e)
+
+
+def test_graph_replay_equals_single_steps():
+    w = ball((20, 33, 40), steps=25)
+    a = gpu_run(w, "split_tf32")
+    b = gpu_run(w, "split_tf32", single_calls=True)
+    assert np.array_equal(a, b)
+    w = disk((13, 20), steps=23)
+    assert np.array_equal(gpu_run(w, "fp64"), gpu_run(w, "fp64", single_calls=True))
+
+
+def test_step_host_equals_step():
+    import torch
+    from paper_2604_11558_gb300 import binding
+    w = ball((20, 33, 40), steps=4)
+    plan = binding.Plan.from_workload(w, precision="split_tf32")
+    host = torch.from_numpy(w["W0"].copy()).pin_memory()
+    plan.step_host(host, 4)
+    dev = gpu_run(w, "split_tf32")
+    assert np.array_equal(host.numpy(), dev)
+    plan.close()
+
+
+def test_unsupported_and_invalid_on_gpu():
+    from paper_2604_11558_gb300 import binding
+    assert binding.setup_status("sphere", (16, 16), [1.0, 2.0], "schnakenberg", [1, 2, 3], 1e-3,
+                                "split_tf32") == 5
+    assert binding.setup_status("ball", (130, 16, 16), [1.0, 2.0], "gray_scott", [0.04, 0.06], 1e-3,
+                                "split_tf32") == 5
+    assert binding.setup_status("disk", (16, 300), [1.0, 2.0], "schnakenberg", [1, 2, 3], 1e-3,
+                                "split_tf32") == 5

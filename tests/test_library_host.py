@@ -1,0 +1,103 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol the header
+declares, validates arguments without touching a GPU, and its FP64 setup
+stage (axes, phi_1 by Pade, eigenbases) matches the oracle's independent
+route (Proposition 1 symmetrisation + numpy eigh) -- row A0 of the hot path.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import axes as oax
+from oracle.phi import phi1_matrix
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2604_11558_gb300 import binding as b
+    if not os.path.exists(b.LIB_PATH):
+        from paper_2604_11558_gb300 import build_lib
+        build_lib.build()
+    b.lib()
+    return b
+
+
+def test_exports_every_declared_symbol(binding):
+    names = binding.header_functions()
+    assert len(names) >= 12
+    L = binding.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings(binding):
+    L = binding.lib()
+    for code in range(7):
+        assert len(L.sexpe_status_string(code)) > 0
+    assert L.sexpe_status_string(99) == b"unknown status"
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(geometry="disk", n=(10, 12), d=[1.0, 2.0], reaction="schnakenberg", params=[1, 2, 3], tau=-1.0), 1),
+    (dict(geometry="disk", n=(10, 12), d=[1.0, 2.0], reaction="schnakenberg", params=[1, 2, 3], tau=float("nan")), 1),
+    (dict(geometry="disk", n=(2, 12), d=[1.0, 2.0], reaction="schnakenberg", params=[1, 2, 3], tau=1e-3), 1),
+    (dict(geometry="ball", n=(10, 12, 600), d=[1.0, 2.0], reaction="gray_scott", params=[0.04, 0.06], tau=1e-3), 1),
+    (dict(geometry="disk", n=(10, 12), d=[1.0, -2.0], reaction="schnakenberg", params=[1, 2, 3], tau=1e-3), 1),
+    (dict(geometry="disk", n=(10, 12), d=[1.0], reaction="schnakenberg", params=[1, 2, 3], tau=1e-3), 1),
+    (dict(geometry="disk", n=(10, 12), d=[1.0, 2.0], reaction="gray_scott", params=[1, 2, 3], tau=1e-3), 1),
+    (dict(geometry="cylinder", n=(8, 8, 8), d=[1.0] * 3, reaction="linear_cubic", params=[0.0] * 4, tau=1e-3), 1),
+    (dict(geometry="disk", n=(10, 12), d=[1.0] * 5, reaction="none", params=[], tau=1e-3), 1),
+    (dict(geometry="disk", n=(10, 12), d=[1.0, 1.0], reaction="none", params=[], tau=1e-3, rho_star=0.0), 1),
+])
+def test_setup_rejects_invalid_arguments(binding, kw, code):
+    assert binding.setup_status(**kw) == code
+
+
+def test_null_pointers_rejected(binding):
+    L = binding.lib()
+    assert L.sexpe_step(None, None, 1, None) == 1
+    assert L.sexpe_destroy(None) == 1
+    assert L.sexpe_synchronize(None, None) == 1
+    assert L.sexpe_axis_matrix(9, 5, 1.0, None) == 1
+
+
+AXES = {"theta": lambda n: oax.theta_axis(n)[1], "rho2": lambda n: oax.rho2_axis(n)[1],
+        "rho3": lambda n: oax.rho3_axis(n)[1], "phi": lambda n: oax.phi_axis(n)[1],
+        "z_neumann": lambda n: oax.z_axis_neumann(n)[1], "z_paper": lambda n: oax.z_axis_paper(n)[1]}
+
+
+@pytest.mark.parametrize("axis", list(AXES))
+def test_axis_matrices_match_oracle(binding, axis):
+    for n in [3, 7, 32, 100]:
+        A = binding.axis_matrix(axis, n)
+        R = AXES[axis](n)
+        assert np.max(np.abs(A - R)) <= 1e-13 * np.max(np.abs(R))
+
+
+@pytest.mark.parametrize("axis", list(AXES))
+@pytest.mark.parametrize("t", [1e-5, 1e-3, 0.05, 2.0])
+def test_pade_phi1_matches_oracle_eigen_route(binding, axis, t):
+    """Two independent phi_1 routes: Pade [13/13] on [[tA, I], [0, 0]] (library) and
+    V diag(phi_1(t lam)) V^{-1} through Proposition 1 (oracle)."""
+    # ||t A|| reaches ~1e5 at t = 2, n = 100: 14 squarings; both routes then agree to a few 1e-12
+    tol = 1e-12 if t <= 0.05 else 5e-12
+    for n in [5, 33, 100]:
+        P = binding.axis_phi1(axis, n, t)
+        R = phi1_matrix(AXES[axis](n), t)
+        assert np.max(np.abs(P - R)) <= tol * np.max(np.abs(R)), (axis, n, t)
+
+
+@pytest.mark.parametrize("axis", list(AXES))
+def test_library_eigenbasis(binding, axis):
+    for n in [4, 9, 64, 100]:
+        lam, V, Vinv = binding.axis_eigen(axis, n)
+        A = AXES[axis](n)
+        scale = np.max(np.abs(A))
+        assert np.max(np.abs(V @ Vinv - np.eye(n))) < 1e-11
+        assert np.max(np.abs((V * lam) @ Vinv - A)) < 1e-11 * scale
+        ref = np.sort(np.linalg.eigvals(A).real)
+        assert np.max(np.abs(np.sort(lam) - ref)) < 1e-10 * scale
+    if axis == "theta":      # orthogonal real Fourier basis: V^{-1} = V^T
+        assert np.allclose(Vinv, V.T, atol=1e-14)

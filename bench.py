@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the split exponential Euler step on the 100^3 ball (2-species Gray-Scott).
+
+One step = one pass of the whole hot path (stencil + reaction, phi direction,
+theta direction, rho direction + update) over the 2 x 10^6-DOF state.  The
+metric is DOF*steps/s of the split-TF32 path; the FP64 path is timed on the
+same workload and reported beside it.  L2 is flushed (a 256 MB write) before
+every timed step, so every step reads its state from HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank advances its own replica:
+the method does not shard without a per-direction all-to-all, so this is
+replicas only, with no collective on the data path.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF*steps/s on 10^6-DOF ball: FP64 vs split-TF32 at <=1e-6 rel err"
+UNIT = "DOF*steps/s"
+WORKLOAD = "ball_gray_scott_100x100x100_2species"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run only setup + 3 split steps (for an ncu capture of the step kernels)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(value, world):
+    """Max of a float over ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- algorithmic work
+def kernel_work(n, S):
+    """Algorithmic bytes and tensor flops per launch of the two split-path kernels of the ball step.
+
+    mode-3 pass: reads the FP64 state once (8 B/DOF), writes Y in FP32 (4 B/DOF);
+      two mu-mode products of length n3 per point, three TF32 MMAs each: 3*2*2*n3 flop/DOF.
+    slab pass: reads Y (4 B/DOF), reads and writes the FP64 state (16 B/DOF);
+      products over theta, theta, rho: 3*2*(2*n2 + n1) flop/DOF.
+    """
+    n1, n2, n3 = n
+    dof = S * n1 * n2 * n3
+    return {
+        "k_tc_mode3": {"bytes": 12 * dof, "flops": 3 * 2 * 2 * n3 * dof},
+        "k_tc_slab": {"bytes": 20 * dof, "flops": 3 * 2 * (2 * n2 + n1) * dof},
+    }
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        return float(pk["hbm_gbs"]), float(pk["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"sexpe_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.out, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.out)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+ORACLE_TIMER = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle.operators import Grid
+from oracle.stepper import Problem, step
+from oracle import reactions as R
+from paper_2604_11558_gb300 import workloads as wl
+w = wl.gray_scott_ball()
+p = Problem(Grid(w["geometry"], w["n"]), w["d"], lambda W, t: R.gray_scott(W, *w["params"]), w["tau"])
+W = w["W0"]
+for _ in range({warmup}):
+    W = step(p, W)
+steps, t0 = 0, time.perf_counter()
+while steps < {min_steps} or (time.perf_counter() - t0 < {budget} and steps < {max_steps}):
+    W = step(p, W)
+    steps += 1
+dt = time.perf_counter() - t0
+print(json.dumps({{"steps": steps, "seconds": dt}}))
+"""
+
+
+def time_oracle(warmup, min_steps, max_steps, budget_s):
+    """Time the FP64 oracle on the ball in a fresh process using every host core (spawned, not forked)."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(cores)
+    code = ORACLE_TIMER.format(root=ROOT, warmup=warmup, min_steps=min_steps, max_steps=max_steps, budget=budget_s)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    dof = 2 * 100 ** 3
+    return {"value": dof * out["steps"] / out["seconds"], "steps": out["steps"], "seconds": out["seconds"],
+            "cores": cores}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    res = time_oracle(args.warmup, args.steps, args.steps, 0.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": res["steps"], "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": [100, 100, 100], "species": 2, "tau": 0.5,
+                   "implementation": "FP64 numpy/scipy oracle (oracle/), CPU"},
+        "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": f"{res['steps']} full ball steps after {args.warmup} warm-up steps"},
+        "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU legs
+def timed_steps(plan, x, steps, flush, profile=False):
+    """Per-step CUDA-event times (ms) with an L2 flush before each step; optional per-kernel profile."""
+    import torch
+    st = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if profile:
+        plan.profile_begin(steps)
+    for k in range(steps):
+        flush()
+        starts[k].record(st)
+        plan.step(x, 1)
+        ends[k].record(st)
+    torch.cuda.synchronize()
+    kms = plan.profile_end() if profile else None
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)], kms
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_11558_gb300 import binding
+    from paper_2604_11558_gb300 import workloads as wl
+
+    w = wl.gray_scott_ball()
+    n, S = w["n"], len(w["d"])
+    dof = S * int(np.prod(n))
+    plan = binding.Plan.from_workload(w, precision="split_tf32")
+    info = plan.info()
+    x = torch.from_numpy(w["W0"]).cuda()
+    if args.profile_case:
+        plan.step(x, 3)
+        plan.synchronize()
+        return
+    flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush_val = [0]
+
+    def flush():
+        flush_val[0] = (flush_val[0] + 1) & 0xFF
+        flush_buf.fill_(flush_val[0])
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (untimed)
+    for _ in range(max(args.warmup, 3)):
+        flush()
+        plan.step(x, 1)
+    plan.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    step_ms, kernel_ms = timed_steps(plan, x, args.steps, flush, profile=True)
+    barrier()
+    clk = clocks.stop()
+    plan.synchronize()
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = world * dof * args.steps / total_s
+
+    # FP64 leg on the same workload
+    plan64 = binding.Plan.from_workload(w, precision="fp64")
+    x64 = torch.from_numpy(w["W0"]).cuda()
+    plan64.step(x64, 2)
+    plan64.synchronize()
+    ms64, kms64 = timed_steps(plan64, x64, args.fp64_steps, flush, profile=True)
+    fp64_s = max_over_ranks(sum(ms64) / 1e3, world)
+    fp64_value = world * dof * args.fp64_steps / fp64_s
+
+    # accuracy of the split path against the FP64 GPU path on the same start (20 steps)
+    xa = torch.from_numpy(w["W0"]).cuda()
+    xb = torch.from_numpy(w["W0"]).cuda()
+    plan.step(xa, 20)
+    plan64.step(xb, 20)
+    torch.cuda.synchronize()
+    acc = [float(torch.linalg.norm(xa[s] - xb[s]) / torch.linalg.norm(xb[s])) for s in range(S)]
+    acc_all = float(torch.linalg.norm(xa - xb) / torch.linalg.norm(xb))
+
+    # end to end through the C ABI with host buffers: H2D of the state, one step, D2H, every step
+    host = torch.from_numpy(w["W0"].copy()).pin_memory()
+    for _ in range(2):
+        plan.step_host(host, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.step_host(host, 1)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    state_bytes = dof * 8
+
+    # roofline of the dominant kernel
+    names = ["k_tc_mode3", "k_tc_slab"]
+    work = kernel_work(n, S)
+    hbm_gbs, bf16_tf, peak_kind = load_peaks()
+    tf32_tf = bf16_tf * (1.1 / 2.25)       # nominal dense TF32 / BF16 ratio applied to the measured BF16 peak
+    per_kernel = {}
+    for nm, ms in zip(names, kernel_ms):
+        bw = work[nm]["bytes"] / (ms * 1e-3) / 1e9
+        tf = work[nm]["flops"] / (ms * 1e-3) / 1e12
+        per_kernel[nm] = {"ms": ms, "GB/s": bw, "TFLOP/s": tf, "hbm_frac": bw / hbm_gbs, "tensor_frac": tf / tf32_tf}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    d = per_kernel[dom]
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        tj = json.load(open(tpath))
+        if tj.get("kernel") == dom and tj.get("source_hash") == kernel_source_hash():
+            traffic = tj.get("dram_bytes_per_launch")
+    if d["hbm_frac"] >= d["tensor_frac"]:
+        roof = {"bound": "hbm", "achieved": d["GB/s"], "peak": hbm_gbs, "unit": "GB/s", "frac": d["hbm_frac"]}
+    else:
+        roof = {"bound": "tensor", "achieved": d["TFLOP/s"], "peak": tf32_tf, "unit": "TFLOP/s",
+                "frac": d["tensor_frac"]}
+    roof.update({"traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)"
+                 if peak_kind == "measured" else "fallback", "per_kernel": per_kernel})
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3 products, f32 accumulate, f64 state",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": list(n), "species": S, "dof": dof, "tau": w["tau"],
+                   "precision": "split_tf32", "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": 1e3 * fp64_s / args.fp64_steps,
+                 "steps": args.fp64_steps, "kernel_ms": kms64},
+        "speedup_split_over_fp64": value / fp64_value,
+        "accuracy": {"split_vs_fp64_gpu_rel_err_per_species_20_steps": acc, "whole_state": acc_all},
+        "e2e": {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "roofline": roof,
+        "gpu_launches": args.steps * info["kernels_per_step"],
+        "clocks": clk,
+        "setup_ms": info["setup_ms"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = time_oracle(1, 2, 200, 15.0)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                                "sample": f"{cb['steps']} full 100^3 ball steps ({cb['seconds']:.1f} s) after "
+                                          f"1 warm-up step"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ["kernels_tc.cu", "tc_ptx.cuh", "device_common.cuh", "internal.h"]:
+        h.update(open(os.path.join(ROOT, "paper_2604_11558_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,17 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_h
 /* Free every device table of the plan (after synchronising its device). */
 sexpe_status sexpe_destroy(sexpe_plan* plan);
 
+/* Per-kernel timing.  After sexpe_profile_begin(plan, max_steps), the next
+ * steps (up to max_steps, across sexpe_step calls on one stream) launch their
+ * kernels directly (no graph) with a CUDA event recorded on the launching
+ * stream before each kernel and after the last.  sexpe_profile_end waits for
+ * the last event and writes, for each kernel slot of a step in launch order,
+ * the average duration in milliseconds to kernel_ms_host[0..n) (n = kernels
+ * per step, capped at `cap`), stores n in *n_kernels_host, and turns
+ * profiling off.  The events are created in begin and destroyed in end. */
+sexpe_status sexpe_profile_begin(sexpe_plan* plan, int32_t max_steps);
+sexpe_status sexpe_profile_end(sexpe_plan* plan, double* kernel_ms_host, int32_t* n_kernels_host, int32_t cap);
+
 /* Setup introspection (host only, FP64, no GPU needed): the quantities the
  * plan is built from, for checking the setup stage on its own.
  * axis: 0 theta (eq. A_theta), 1 rho d=2 (eq. disk_discr), 2 rho d=3

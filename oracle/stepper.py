@@ -66,22 +66,34 @@ def rhs(problem, W, t=0.0):
     return [problem.d[s] * problem.grid.apply_M(W[s]) + G[s] for s in range(problem.S)]
 
 
-def step(problem, W, t=0.0):
-    """One split exponential Euler step; W has shape (S, *grid.shape). Returns a new array."""
+def _to_fp32(x):
+    return x.astype(np.float32).astype(np.float64)
+
+
+def step(problem, W, t=0.0, fp32_storage=False):
+    """One split exponential Euler step; W has shape (S, *grid.shape). Returns a new array.
+
+    fp32_storage=True is a precision-emulation switch for error modelling
+    only: F, the result of every direction and the increment are rounded to
+    FP32 (the state stays FP64), i.e. the storage precision of a mixed
+    FP32/FP64 implementation, with the arithmetic itself still exact.
+    """
     grid = problem.grid
     F = rhs(problem, W, t)
     out = np.array(W, copy=True)
     for s in range(problem.S):
-        X = F[s]
+        X = _to_fp32(F[s]) if fp32_storage else F[s]
         for mu in range(grid.ndim, 0, -1):          # phi_1(tau d M_d) first, phi_1(tau d M_1) last
             X = apply_phi1_mode(X, grid, problem._eig[mu], mu, problem.tau * problem.d[s])
-        out[s] = W[s] + problem.tau * X
+            if fp32_storage:
+                X = _to_fp32(X)
+        out[s] = W[s] + (_to_fp32(problem.tau * X) if fp32_storage else problem.tau * X)
     return out
 
 
-def run(problem, W0, n_steps, t0=0.0):
+def run(problem, W0, n_steps, t0=0.0, fp32_storage=False):
     """n_steps split exponential Euler steps from W0 (time-dependent reactions see t_n)."""
     W = np.array(W0, copy=True)
     for n in range(n_steps):
-        W = step(problem, W, t0 + n * problem.tau)
+        W = step(problem, W, t0 + n * problem.tau, fp32_storage)
     return W

@@ -75,11 +75,14 @@ def lib():
         L.sexpe_synchronize.argtypes = [_P, _P]
         L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
         L.sexpe_destroy.argtypes = [_P]
+        L.sexpe_profile_begin.argtypes = [_P, ctypes.c_int32]
+        L.sexpe_profile_end.argtypes = [_P, _DP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
         L.sexpe_axis_matrix.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _DP]
         L.sexpe_axis_phi1.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _DP]
         L.sexpe_axis_eigen.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _DP, _DP, _DP]
         for name in ["sexpe_setup", "sexpe_batch_setup", "sexpe_state_offsets", "sexpe_step", "sexpe_step_host",
                      "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
+                     "sexpe_profile_begin", "sexpe_profile_end",
                      "sexpe_axis_phi1", "sexpe_axis_eigen"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
@@ -166,6 +169,16 @@ class Plan:
 
     def synchronize(self, stream=None):
         _check(lib().sexpe_synchronize(self.handle, _stream_ptr(stream)), "sexpe_synchronize")
+
+    def profile_begin(self, max_steps):
+        _check(lib().sexpe_profile_begin(self.handle, int(max_steps)), "sexpe_profile_begin")
+
+    def profile_end(self):
+        """Average duration (ms) of each kernel slot of a step over the profiled steps."""
+        out = np.zeros(16)
+        n = ctypes.c_int32(0)
+        _check(lib().sexpe_profile_end(self.handle, _dptr_out(out), ctypes.byref(n), 16), "sexpe_profile_end")
+        return out[:n.value].tolist()
 
     def close(self):
         if getattr(self, "handle", None):

@@ -52,6 +52,10 @@ struct sexpe_plan {
     // split path
     SplitTables tabs{};
     TcShape sh3{}, shs{};
+    // per-kernel profiling (CUDA events on the launching stream)
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_max_steps = 0, prof_steps = 0, prof_slot = 0;
+    bool profiling = false;
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     double* g_state = nullptr;
@@ -389,8 +393,28 @@ Gemm64 mode_gemm(const sexpe_plan* p, int mu, const double* L, long long L_sp, c
     return g;
 }
 
+// Record the profiling event of the next kernel slot (no-op unless profiling).
+cudaError_t prof_mark(sexpe_plan* p, cudaStream_t st) {
+    if (!p->profiling || p->prof_steps >= p->prof_max_steps) return cudaSuccess;
+    const int per = p->kernels_per_step + 1;
+    return cudaEventRecord(p->prof_ev[(size_t)p->prof_steps * per + p->prof_slot++], st);
+}
+
+sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st);
+
 sexpe_status enqueue_step(sexpe_plan* p, double* state, cudaStream_t st) {
+    p->prof_slot = 0;
+    SX_TRY(enqueue_step_body(p, state, st));
+    if (p->profiling && p->prof_steps < p->prof_max_steps) {
+        SX_CUDA(prof_mark(p, st));
+        ++p->prof_steps;
+    }
+    return SEXPE_OK;
+}
+
+sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
     if (p->precision == SEXPE_FP64) {
+        SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_rhs64(p->geometry, p->rhs64, state, p->buf64[0], st));
         int x = 0;                                  // buffer holding the current operand
         for (const Dir64& d : p->dirs64) {
@@ -398,11 +422,14 @@ sexpe_status enqueue_step(sexpe_plan* p, double* state, cudaStream_t st) {
             const int nmu = p->n[d.mu - 1];
             const int t = (x + 1) % 3, y = (x + 2) % 3;
             if (d.eigen) {
+                SX_CUDA(prof_mark(p, st));
                 SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.Vinv, 0, p->buf64[x], p->buf64[t], d.had, nullptr), p->S, st));
+                SX_CUDA(prof_mark(p, st));
                 SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.V, 0, p->buf64[t], p->buf64[y], nullptr,
                                                 last ? state : nullptr), p->S, st));
                 x = y;
             } else {
+                SX_CUDA(prof_mark(p, st));
                 SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.P, (long long)nmu * nmu, p->buf64[x], p->buf64[t],
                                                 nullptr, last ? state : nullptr), p->S, st));
                 x = t;
@@ -413,8 +440,10 @@ sexpe_status enqueue_step(sexpe_plan* p, double* state, cudaStream_t st) {
     SplitTables T = p->tabs;
     T.state = state;
     T.state_upd = state;
+    SX_CUDA(prof_mark(p, st));
     if (p->ndim == 3) SX_CUDA(launch_tc_mode3(T, p->sh3, st));
     else SX_CUDA(launch_rhs_split(T, st));
+    SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_tc_slab(T, p->shs, st));
     return SEXPE_OK;
 }
@@ -450,8 +479,16 @@ sexpe_status validate(const sexpe_grid* g, const sexpe_species* sp, double tau, 
     return SEXPE_OK;
 }
 
+void free_profile(sexpe_plan* p) {
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    p->prof_ev.clear();
+    p->profiling = false;
+    p->prof_steps = p->prof_max_steps = 0;
+}
+
 void free_plan(sexpe_plan* p) {
     if (!p) return;
+    free_profile(p);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (void* a : p->allocs) cudaFree(a);
     delete p;
@@ -560,7 +597,7 @@ sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* str
     if (((uintptr_t)state & 7u) != 0) return SEXPE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int64_t done = 0;
-    if (n_steps >= kGraphSteps) {
+    if (n_steps >= kGraphSteps && !p->profiling) {
         if (!p->gexec || p->g_state != state) {
             if (p->gexec) {
                 cudaGraphExecDestroy(p->gexec);
@@ -629,6 +666,51 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
     info->workspace_bytes = (int64_t)p->bytes;
     info->setup_ms = p->setup_ms;
     return SEXPE_OK;
+}
+
+sexpe_status sexpe_profile_begin(sexpe_plan* p, int32_t max_steps) {
+    if (!p || max_steps < 1 || max_steps > 100000) return SEXPE_EINVAL;
+    free_profile(p);
+    const size_t n = (size_t)max_steps * (p->kernels_per_step + 1);
+    p->prof_ev.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        cudaError_t e = cudaEventCreate(&p->prof_ev[i]);
+        if (e != cudaSuccess) {
+            p->prof_ev.resize(i);
+            free_profile(p);
+            return cuda_status(e);
+        }
+    }
+    p->prof_max_steps = max_steps;
+    p->prof_steps = 0;
+    p->profiling = true;
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_profile_end(sexpe_plan* p, double* kernel_ms, int32_t* n_kernels, int32_t cap) {
+    if (!p || !kernel_ms || !n_kernels || cap < 0 || !p->profiling) return SEXPE_EINVAL;
+    const int per = p->kernels_per_step + 1;
+    const int k = p->kernels_per_step < cap ? p->kernels_per_step : cap;
+    *n_kernels = k;
+    sexpe_status st = SEXPE_OK;
+    if (p->prof_steps > 0) {
+        cudaError_t e = cudaEventSynchronize(p->prof_ev[(size_t)(p->prof_steps - 1) * per + per - 1]);
+        if (e != cudaSuccess) st = cuda_status(e);
+        for (int q = 0; q < k && st == SEXPE_OK; ++q) {
+            double acc = 0.0;
+            for (int s = 0; s < p->prof_steps; ++s) {
+                float ms = 0.f;
+                e = cudaEventElapsedTime(&ms, p->prof_ev[(size_t)s * per + q], p->prof_ev[(size_t)s * per + q + 1]);
+                if (e != cudaSuccess) { st = cuda_status(e); break; }
+                acc += ms;
+            }
+            kernel_ms[q] = acc / p->prof_steps;
+        }
+    } else {
+        for (int q = 0; q < k; ++q) kernel_ms[q] = 0.0;
+    }
+    free_profile(p);
+    return st;
 }
 
 static bool axis_args(int32_t axis, int32_t n, double extent, AxisKind* kind) {

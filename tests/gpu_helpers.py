@@ -26,6 +26,15 @@ def oracle_run(w, steps=None):
     return run(p, w["W0"], w["steps"] if steps is None else steps)
 
 
+def emulated_fp32_errors(w, ref):
+    """Per-species relative error of the oracle run with FP32 storage of F, of every
+    direction's result and of the increment (the storage floor of an FP32 chain)."""
+    g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"))
+    p = Problem(g, w["d"], oracle_reaction(w), w["tau"])
+    emu = run(p, w["W0"], w["steps"], fp32_storage=True)
+    return rel_errors(emu, ref)
+
+
 def gpu_run(w, precision, steps=None, single_calls=False):
     import torch
     from paper_2604_11558_gb300 import binding

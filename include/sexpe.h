@@ -132,6 +132,28 @@ sexpe_status sexpe_step(sexpe_plan* plan, double* state_dev, int64_t n_steps, vo
  * state_host should be page-locked for asynchronous copies. */
 sexpe_status sexpe_step_host(sexpe_plan* plan, double* state_host, int64_t n_steps, void* stream);
 
+/* The split-TF32 step without any device allocation, for callers that cannot
+ * call cudaMalloc (a region captured into a CUDA graph in the global capture
+ * mode, a host framework that owns all device memory through its own pool, a
+ * loop under a fixed memory budget).  The paper has no counterpart: this is a
+ * deployment variant of sexpe_step.
+ *  - plan: a SEXPE_SPLIT_TF32 plan made earlier on the current device (its
+ *    constant tables are read); state_dev as for sexpe_step (in place).
+ *  - The step's only scratch, the FP32 intermediate between its two kernels,
+ *    lives in a static device array of 2^21 floats (8 MiB) that every GPU
+ *    loading the library holds until exit; plans with species x points above
+ *    2,097,152, or FP64 plans, give SEXPE_EINVAL.  No cudaMalloc/cudaFree or
+ *    allocating library routine is called.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents
+ *    (nothing in it needs to start at zero: each step writes it before
+ *    reading it).  Calls whose work overlaps on the GPU (other streams, other
+ *    threads) race on it: serialise them.
+ *  - Results equal sexpe_step's for the same plan and state. */
+sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_steps, void* stream);
+
 /* Wait for the plan's work on `stream` and report the device error word
  * (SEXPE_ETIMEOUT if a bounded wait ran out), clearing it. */
 sexpe_status sexpe_synchronize(sexpe_plan* plan, void* stream);

@@ -72,6 +72,7 @@ def lib():
         L.sexpe_state_offsets.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         L.sexpe_step.argtypes = [_P, _P, ctypes.c_int64, _P]
         L.sexpe_step_host.argtypes = [_P, _DP, ctypes.c_int64, _P]
+        L.sexpe_step_noalloc.argtypes = [_P, _P, ctypes.c_int64, _P]
         L.sexpe_synchronize.argtypes = [_P, _P]
         L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
         L.sexpe_destroy.argtypes = [_P]
@@ -82,7 +83,7 @@ def lib():
         L.sexpe_axis_eigen.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _DP, _DP, _DP]
         for name in ["sexpe_setup", "sexpe_batch_setup", "sexpe_state_offsets", "sexpe_step", "sexpe_step_host",
                      "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
-                     "sexpe_profile_begin", "sexpe_profile_end",
+                     "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
                      "sexpe_axis_phi1", "sexpe_axis_eigen"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
@@ -157,6 +158,11 @@ class Plan:
 
     def step(self, state, n_steps, stream=None):
         _check(lib().sexpe_step(self.handle, _data_ptr(state), int(n_steps), _stream_ptr(stream)), "sexpe_step")
+
+    def step_noalloc(self, state, n_steps, stream=None):
+        """sexpe_step_noalloc: the split-TF32 step with scratch in the library's static device array."""
+        _check(lib().sexpe_step_noalloc(self.handle, _data_ptr(state), int(n_steps), _stream_ptr(stream)),
+               "sexpe_step_noalloc")
 
     def step_host(self, state_host, n_steps, stream=None):
         """state_host: C-contiguous float64 numpy array (or pinned CPU tensor), updated in place."""

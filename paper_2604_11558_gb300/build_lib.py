@@ -14,7 +14,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["kernels_tc.cu", "kernels_fp64.cu", "plan.cu", "host_setup.cpp"]
+SOURCES = ["kernels_tc.cu", "kernels_fp64.cu", "plan.cu", "noalloc.cu", "host_setup.cpp"]
 
 
 def _compile(src, extra):

@@ -537,6 +537,28 @@ sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species*
 
 }  // namespace
 
+namespace sexpe {
+
+// Enqueue one split-TF32 step of plan `p` with the FP32 intermediate of the
+// chain in caller-provided device memory `Y` (capacity `y_floats`) instead of
+// the plan's own buffer.  Used by the no-allocation entry point.
+sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float* Y, long long y_floats,
+                                             cudaStream_t st) {
+    if (!p || !state || !Y) return SEXPE_EINVAL;
+    if (p->precision != SEXPE_SPLIT_TF32) return SEXPE_EINVAL;
+    if ((long long)p->S * p->npts > y_floats) return SEXPE_EINVAL;
+    SplitTables T = p->tabs;
+    T.state = state;
+    T.state_upd = state;
+    T.Y = Y;
+    if (p->ndim == 3) SX_CUDA(launch_tc_mode3(T, p->sh3, st));
+    else SX_CUDA(launch_rhs_split(T, st));
+    SX_CUDA(launch_tc_slab(T, p->shs, st));
+    return SEXPE_OK;
+}
+
+}  // namespace sexpe
+
 extern "C" {
 
 const char* sexpe_status_string(int32_t status) {

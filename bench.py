@@ -33,7 +33,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=5)
@@ -61,17 +61,19 @@ def max_over_ranks(value, world):
 
 # ----------------------------------------------------------------------------- algorithmic work
 def kernel_work(n, S):
-    """Algorithmic bytes and tensor flops per launch of the two split-path kernels of the ball step.
+    """Algorithmic bytes and tensor flops per launch of the three split-path kernels of the ball step.
 
-    mode-3 pass: reads the FP64 state once (8 B/DOF), writes Y in FP32 (4 B/DOF);
-      two mu-mode products of length n3 per point, three TF32 MMAs each: 3*2*2*n3 flop/DOF.
+    stencil pass: reads the FP64 state once (8 B/DOF), writes F in FP32 (4 B/DOF); no tensor work.
+    mode-3 pass: reads F and writes Y in place (4 + 4 B/DOF); two mu-mode products of length n3
+      per point, three TF32 MMAs each: 3*2*2*n3 flop/DOF.
     slab pass: reads Y (4 B/DOF), reads and writes the FP64 state (16 B/DOF);
       products over theta, theta, rho: 3*2*(2*n2 + n1) flop/DOF.
     """
     n1, n2, n3 = n
     dof = S * n1 * n2 * n3
     return {
-        "k_tc_mode3": {"bytes": 12 * dof, "flops": 3 * 2 * 2 * n3 * dof},
+        "k_rhs_tile": {"bytes": 12 * dof, "flops": 0},
+        "k_tc_mode3": {"bytes": 8 * dof, "flops": 3 * 2 * 2 * n3 * dof},
         "k_tc_slab": {"bytes": 20 * dof, "flops": 3 * 2 * (2 * n2 + n1) * dof},
     }
 
@@ -286,14 +288,14 @@ def main():
     state_bytes = dof * 8
 
     # roofline of the dominant kernel
-    names = ["k_tc_mode3", "k_tc_slab"]
+    names = ["k_rhs_tile", "k_tc_mode3", "k_tc_slab"]
     work = kernel_work(n, S)
     hbm_gbs, bf16_tf, peak_kind = load_peaks()
     tf32_tf = bf16_tf * (1.1 / 2.25)       # nominal dense TF32 / BF16 ratio applied to the measured BF16 peak
     per_kernel = {}
     for nm, ms in zip(names, kernel_ms):
         bw = work[nm]["bytes"] / (ms * 1e-3) / 1e9
-        tf = work[nm]["flops"] / (ms * 1e-3) / 1e12
+        tf = work[nm]["flops"] / (ms * 1e-3) / 1e12 if work[nm]["flops"] else 0.0
         per_kernel[nm] = {"ms": ms, "GB/s": bw, "TFLOP/s": tf, "hbm_frac": bw / hbm_gbs, "tensor_frac": tf / tf32_tf}
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     d = per_kernel[dom]
@@ -344,7 +346,7 @@ def main():
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ["kernels_tc.cu", "tc_ptx.cuh", "device_common.cuh", "internal.h"]:
+    for f in ["kernels_tc.cu", "tc_ptx.cuh", "device_common.cuh", "internal.h", "plan.cu"]:
         h.update(open(os.path.join(ROOT, "paper_2604_11558_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

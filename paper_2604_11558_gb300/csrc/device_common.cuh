@@ -21,16 +21,31 @@ __device__ __forceinline__ float2 split_f64(double w) {
     const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
     const int e = (int)((hi32 >> 20) & 0x7FFu);          // biased FP64 exponent
     const unsigned sign = hi32 & 0x80000000u;
-    if (e < 897) return make_float2(0.f, 0.f);           // |w| < 2^-126: below FP32 normals
-    if (e > 1150) return make_float2(__uint_as_float(sign | 0x7F800000u), 0.f);   // beyond FP32 range
-    const unsigned fb = sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
-    float lo = 0.f;
-    const unsigned m29 = lo32 & 0x1FFFFFFFu;             // weight 2^(e-1075) per unit
-    if (m29 != 0u && e >= 949) {
-        const float scale = __uint_as_float((unsigned)(e - 948) << 23);
-        lo = __uint_as_float(__float_as_uint((float)m29) | sign) * scale;
-    }
+    // |w| < 2^-126 (below FP32 normals) -> signed zero; beyond FP32 range -> infinity.
+    unsigned fb = sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+    fb = (e < 897) ? sign : fb;
+    fb = (e > 1150) ? (sign | 0x7F800000u) : fb;
+    // remainder: the 29 truncated bits, weight 2^(e-1075) each
+    const unsigned m29 = lo32 & 0x1FFFFFFFu;
+    const int se = max(e - 948, 1);
+    float lo = __uint_as_float(__float_as_uint((float)m29) | sign) * __uint_as_float((unsigned)min(se, 254) << 23);
+    lo = (e >= 949 && e <= 1150) ? lo : 0.f;
     return make_float2(__uint_as_float(fb), lo);
+}
+
+// Exact FP32 -> FP64 conversion with integer operations only (FP32 denormals
+// flush to zero); keeps the conversion off the FP64 pipe.
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned m = u & 0x7FFFFFu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    hi = (e == 0u) ? sign : hi;
+    lo = (e == 0u) ? 0u : lo;
+    hi = (e == 0xFFu) ? (sign | 0x7FF00000u | (m >> 3)) : hi;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
 struct F64Acc {
@@ -83,19 +98,21 @@ __device__ __forceinline__ typename Acc::T laplacian(const RhsTables<typename Ac
 }
 
 template <class T>
-__device__ __forceinline__ T reaction(const ReactionParams& rp, const T* w, int s) {
+__device__ __forceinline__ T reaction(const ReactionParams<T>& rp, const T* w, int s) {
     switch (rp.kind) {
     case R_SCHNAKENBERG: {   // f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)
         const T u2v = w[0] * w[0] * w[1];
-        return s == 0 ? (T)rp.p[0] * ((T)rp.p[1] - w[0] + u2v) : (T)rp.p[0] * ((T)rp.p[2] - u2v);
+        return s == 0 ? rp.p[0] * (rp.p[1] - w[0] + u2v) : rp.p[0] * (rp.p[2] - u2v);
     }
     case R_GRAY_SCOTT: {     // f = -u v^2 + F(1 - u), g = u v^2 - (F + k) v
         const T uv2 = w[0] * w[1] * w[1];
-        return s == 0 ? -uv2 + (T)rp.p[0] * ((T)1 - w[0]) : uv2 - ((T)rp.p[0] + (T)rp.p[1]) * w[1];
+        return s == 0 ? -uv2 + rp.p[0] * ((T)1 - w[0]) : uv2 - (rp.p[0] + rp.p[1]) * w[1];
     }
     case R_LINEAR_CUBIC: {   // f_i = sum_j K_ij u_j - u_i^3
         T acc = -w[s] * w[s] * w[s];
-        for (int r = 0; r < rp.S; ++r) acc += (T)rp.p[s * rp.S + r] * w[r];
+#pragma unroll
+        for (int r = 0; r < kMaxSpecies; ++r)
+            if (r < rp.S) acc += rp.p[s * rp.S + r] * w[r];
         return acc;
     }
     default:
@@ -117,10 +134,7 @@ __device__ __forceinline__ typename Acc::T rhs_point(const RhsTables<typename Ac
         if (r < tb.S) w[r] = (r == s) ? Acc::value(c) : Acc::value(Acc::load(Wall + (long long)r * tb.npts + idx));
         else w[r] = (T)0;
     }
-    return (T)tb.d[s] * lap + reaction<T>(tb.reac, w, s);
+    return tb.d[s] * lap + reaction<T>(tb.reac, w, s);
 }
-
-// phi_1(x) = expm1(x)/x, 1 at 0 (Section 4), FP32 for the on-the-fly Hadamard factors.
-__device__ __forceinline__ float phi1f(float x) { return x == 0.f ? 1.f : expm1f(x) / x; }
 
 }  // namespace sexpe

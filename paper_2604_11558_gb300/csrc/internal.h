@@ -24,10 +24,11 @@ struct StencilAxis {
     int periodic;
 };
 
+template <class T>
 struct ReactionParams {
     int kind;
     int S;
-    double p[16];
+    T p[16];     // in the arithmetic type of the kernels that read them (no conversions on the device)
 };
 
 // Everything the stencil+reaction evaluation needs (values of type T).
@@ -40,8 +41,8 @@ struct RhsTables {
     StencilAxis<T> ax[3];
     const T* Dr;   // rho_i^-2 (mode-1 index), disk/ball/cylinder
     const T* Dp;   // sin^-2 phi_k (phi-mode index), sphere/ball
-    double d[kMaxSpecies];
-    ReactionParams reac;
+    T d[kMaxSpecies];
+    ReactionParams<T> reac;
 };
 
 // ---------------- FP64 SIMT path ------------------------------------------
@@ -80,20 +81,19 @@ struct SplitTables {
     int n1, n2, n3;
     long long npts;
     RhsTables<float> rhs;     // FP32 coefficients (differences are formed at FP64 accuracy)
-    const double* state;      // read in producers
+    const double* state;      // read by the stencil pass
     double* state_upd;        // updated in the slab epilogue
-    float* Y;                 // FP32 intermediate between the mode-3 pass and the slab pass
+    float* Y;                 // FP32 chain buffer: F from the stencil pass, overwritten in place
+                              // by the mode-3 pass, read by the slab pass
     float tau;
     double tau_d;
     // slab pass (theta then rho)
     Image QT, Q, P[kMaxSpecies];
-    const float* had_theta;   // per species: coefficient c(i[,k]) so that x = c * lam_theta[j]
+    const float* had_theta;   // Phi table of the theta direction, [s][k][j'][i] (ball) or [s][j'][i]
     long long had_theta_sp;   // floats per species
-    const float* lam_theta;
     // mode-3 pass
     Image M3a, M3b[kMaxSpecies];   // ball: Vinv (M3a) and V (M3b[0]); cylinder: Pz_s in M3b[s]
-    const float* had_phi;          // ball: c_s(i) = tau d_s rho_i^-2
-    const float* lam_phi;
+    const float* had_phi;          // ball: Phi table of the phi direction, [s][k'][i]
     int* err;
 };
 

@@ -1,22 +1,26 @@
 // Split-TF32 tensor-core kernels (tcgen05 + TMEM + TMA bulk copies, sm_103a)
 // for the per-step chain of the split exponential Euler method:
 //
-//   mode-3 pass (ball, cylinder): F = d M w + g(w) at FP64-accurate differences,
-//       then F x_3 V_phi^{-1}, Hadamard phi_1(tau d rho_i^-2 lambda_phi), x_3 V_phi
-//       (ball, eq. ee_ball) or F x_3 phi_1(tau d A_z) (cylinder, eq. ee_cylinder) -> Y.
-//   slab pass (disk, ball, cylinder), one k-slab per CTA:
-//       Y x_2 Q_theta^T, Hadamard Phi (theta factor), x_2 Q_theta, x_1 phi_1(tau d A_rho),
+//   stencil pass (all geometries, SIMT): F = d M w + g(w) in FP32 from FP64-
+//       accurate differences, one shared-memory tile per CTA -> Y.
+//   mode-3 pass (ball, cylinder), in place on Y: F x_3 V_phi^{-1}, Hadamard
+//       Phi_{rho,.,phi}, x_3 V_phi (ball, eq. ee_ball) or F x_3 phi_1(tau d A_z)
+//       (cylinder, eq. ee_cylinder).
+//   slab pass (disk, ball, cylinder), one k-slab per CTA: Y x_2 Q_theta^T,
+//       Hadamard Phi (theta factor), x_2 Q_theta, x_1 phi_1(tau d A_rho),
 //       w += tau * result (eqs. ee_disk, ee_ball, ee_cylinder).
 //
 // Every mu-mode product is D = A B^T with FP32 accumulation in tensor memory
 // and three TF32 MMAs per K-step (lo*hi, hi*lo, hi*hi).  The constant matrix of
 // a product arrives by one TMA bulk copy per K-chunk from an image pre-laid in
 // the canonical K-major no-swizzle layout; the data operand is written by the
-// 128 threads (one row each), split into TF32 hi/lo on the way.  Intermediates
-// stay in tensor memory: a row (lane) of one product becomes the row of the
-// next operand, so the chain swaps the row mode once (theta -> rho) by putting
-// the data in the B operand of the middle product.
+// 256 threads (two per row, eight K-columns each), split into TF32 hi/lo on the
+// way.  Intermediates stay in tensor memory: a row (lane) of one product
+// becomes the row of the next operand, so the chain swaps the row mode once
+// (theta -> rho) by putting the data in the B operand of the middle product.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -25,13 +29,16 @@
 
 namespace sexpe {
 
-constexpr int kThreads = 128;
+constexpr int kRows = 128;                 // MMA M and tensor-memory lanes
+constexpr int kThreads = 256;              // producer threads: two per row, columns 0-7 / 8-15 of a chunk
+constexpr int kBlock = kThreads + 64;      // + one warp issuing TMA copies ahead, one issuing the MMAs
 constexpr int kStages = 3;
 constexpr uint32_t kHeaderBytes = 1024;   // barriers + tensor-memory slot
 
 struct Pipe {
-    uint64_t* tma_bar;
-    uint64_t* mma_bar;
+    uint64_t* tma_bar;     // matrix chunk landed (TMA transaction count)
+    uint64_t* mma_bar;     // MMAs reading the stage completed (tcgen05.commit)
+    uint64_t* data_bar;    // data operand of the stage written (one arrive per producer warp)
     char* stages;
     uint32_t stage_bytes;
     uint32_t g;        // K-chunks issued so far in this CTA (uniform)
@@ -44,16 +51,19 @@ __device__ __forceinline__ void pipe_wait(Pipe& P, uint64_t* bar, uint32_t parit
     if (!mbar_wait_bounded(bar, parity, P.err, code, lim)) *P.aborted = 1;
 }
 
-// Row r of a tile pair (hi, lo), 16 K-values starting at the chunk's first column.
-__device__ __forceinline__ void store_row16(char* hi, char* lo, int r, const float* v) {
-    const uint32_t off = (uint32_t)(r >> 3) * kSBO + (uint32_t)(r & 7) * 16u;
+// Barrier of the 256 compute threads only (the TMA warp runs on its own).
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Row r, columns 8h..8h+7 of a chunk, of a tile pair (hi, lo).
+__device__ __forceinline__ void store_row8(char* hi, char* lo, int r, int h, const float* v) {
+    const uint32_t off = (uint32_t)(r >> 3) * kSBO + (uint32_t)(r & 7) * 16u + (uint32_t)(2 * h) * kLBO;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint32_t h[4], l[4];
+    for (int q = 0; q < 2; ++q) {
+        uint32_t hb[4], lb[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split_tf32(v[4 * q + e], h[e], l[e]);
-        *reinterpret_cast<uint4*>(hi + off + q * kLBO) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(lo + off + q * kLBO) = make_uint4(l[0], l[1], l[2], l[3]);
+        for (int e = 0; e < 4; ++e) split_tf32(v[4 * q + e], hb[e], lb[e]);
+        *reinterpret_cast<uint4*>(hi + off + q * kLBO) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
+        *reinterpret_cast<uint4*>(lo + off + q * kLBO) = make_uint4(lb[0], lb[1], lb[2], lb[3]);
     }
 }
 
@@ -67,34 +77,56 @@ struct GemmSpec {
     uint32_t tmem_d;  // tensor-memory address of the accumulator (tile mt at + mt * n_pad)
 };
 
+// Byte offset of the constant-matrix tiles inside a stage: after the data hi/lo tiles.
+__device__ __forceinline__ uint32_t mat_offset(const GemmSpec& G) { return 2u * G.data_rows * kTileRowBytes; }
+
+// Producer side of one product: the 256 producer threads write the data operand
+// of each K-chunk into its stage and signal the MMA warp through the stage's
+// data barrier; a stage is rewritten only after the MMAs that read it completed.
 template <class Producer>
 __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& produce) {
-    const int tid = threadIdx.x;
     const uint32_t data_bytes = (uint32_t)G.data_rows * kTileRowBytes;
-    const uint32_t mat_bytes = (uint32_t)G.mat.rows_pad * kTileRowBytes;
-    const int nsub = G.n_pad < 256 ? G.n_pad : 256;
-    const int n_halves = G.n_pad / nsub;
-    const uint32_t idesc = idesc_tf32(128, nsub);
     for (int c = 0; c < G.k_chunks; ++c) {
         const uint32_t g = P.g;
         const int s = (int)(g % kStages);
         const uint32_t use = g / kStages;
         if (g >= (uint32_t)kStages) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
         char* st = P.stages + (size_t)s * P.stage_bytes;
-        char* dhi = st;
-        char* dlo = st + data_bytes;
-        char* mhi = st + 2 * data_bytes;
-        char* mlo = mhi + mat_bytes;
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&P.tma_bar[s], 2 * mat_bytes);
-            tma_bulk_g2s(mhi, G.mat.ptr + (long long)c * G.mat.chunk_floats, 2 * mat_bytes, &P.tma_bar[s]);
-        }
-        produce(c, dhi, dlo);
+        produce(c, st, st + data_bytes);
         fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&P.data_bar[s]);
+        P.g = g + 1;
+    }
+    const uint32_t gl = P.g - 1;
+    pipe_wait(P, &P.mma_bar[gl % kStages], (gl / kStages) & 1u, DERR_TIMEOUT_MMA);
+    tc_fence_after();
+}
+
+// MMA side: one lane of the MMA warp walks the K-chunks of every product in
+// order; when a chunk's data operand and matrix copy are both in its stage it
+// issues the three TF32 MMAs per K-step and commits them to the stage barrier.
+__device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
+    if ((threadIdx.x & 31) != 0) return;
+    uint32_t g = 0;
+    for (int q = 0; q < n_gemms; ++q) {
+        const GemmSpec& G = gs[q];
+        const uint32_t data_bytes = (uint32_t)G.data_rows * kTileRowBytes;
+        const uint32_t mat_bytes = (uint32_t)G.mat.rows_pad * kTileRowBytes;
+        const int nsub = G.n_pad < 256 ? G.n_pad : 256;
+        const int n_halves = G.n_pad / nsub;
+        const uint32_t idesc = idesc_tf32(128, nsub);
+        for (int c = 0; c < G.k_chunks; ++c, ++g) {
+            const int s = (int)(g % kStages);
+            const uint32_t use = g / kStages;
+            pipe_wait(P, &P.data_bar[s], use & 1u, DERR_TIMEOUT_MMA);
             pipe_wait(P, &P.tma_bar[s], use & 1u, DERR_TIMEOUT_TMA);
             tc_fence_after();
+            char* st = P.stages + (size_t)s * P.stage_bytes;
+            char* dhi = st;
+            char* dlo = st + data_bytes;
+            char* mhi = st + mat_offset(G);
+            char* mlo = mhi + mat_bytes;
             const uint32_t a_hi = smem_u32(G.mat_is_A ? mhi : dhi), a_lo = smem_u32(G.mat_is_A ? mlo : dlo);
             const uint32_t b_hi = smem_u32(G.mat_is_A ? dhi : mhi), b_lo = smem_u32(G.mat_is_A ? dlo : mlo);
 #pragma unroll
@@ -115,11 +147,27 @@ __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& 
             }
             mma_commit(&P.mma_bar[s]);
         }
-        P.g = g + 1;
     }
-    const uint32_t gl = P.g - 1;
-    pipe_wait(P, &P.mma_bar[gl % kStages], (gl / kStages) & 1u, DERR_TIMEOUT_MMA);
-    tc_fence_after();
+}
+
+// TMA side: one lane of the extra warp walks the K-chunks of every product of
+// the CTA in order and copies each chunk's matrix image into its stage as soon
+// as the stage is free, up to kStages chunks ahead of the MMAs.
+__device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
+    if ((threadIdx.x & 31) != 0) return;
+    uint32_t g = 0;
+    for (int q = 0; q < n_gemms; ++q) {
+        const GemmSpec& G = gs[q];
+        const uint32_t mat_bytes = (uint32_t)G.mat.rows_pad * kTileRowBytes;
+        for (int c = 0; c < G.k_chunks; ++c, ++g) {
+            const int s = (int)(g % kStages);
+            const uint32_t use = g / kStages;
+            if (g >= (uint32_t)kStages) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
+            char* mhi = P.stages + (size_t)s * P.stage_bytes + mat_offset(G);
+            mbar_arrive_expect_tx(&P.tma_bar[s], 2 * mat_bytes);
+            tma_bulk_g2s(mhi, G.mat.ptr + (long long)c * G.mat.chunk_floats, 2 * mat_bytes, &P.tma_bar[s]);
+        }
+    }
 }
 
 // Kernel prologue/epilogue: carve shared memory, init barriers, allocate TMEM.
@@ -132,10 +180,11 @@ __device__ __forceinline__ CtaRes cta_begin(char* smem_raw, uint32_t stage_bytes
     const uint32_t base = smem_u32(smem_raw);
     char* smem = smem_raw + (((base + 1023u) & ~1023u) - base);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * kStages * sizeof(uint64_t));
-    int* aborted = reinterpret_cast<int*>(smem + 2 * kStages * sizeof(uint64_t) + 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 3 * kStages * sizeof(uint64_t));
+    int* aborted = reinterpret_cast<int*>(smem + 3 * kStages * sizeof(uint64_t) + 16);
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2 * kStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 2 * kStages; s < 3 * kStages; ++s) mbar_init(&bars[s], kThreads / 32);
         *aborted = 0;
         fence_mbar_init();
     }
@@ -149,6 +198,7 @@ __device__ __forceinline__ CtaRes cta_begin(char* smem_raw, uint32_t stage_bytes
     CtaRes r;
     r.P.tma_bar = bars;
     r.P.mma_bar = bars + kStages;
+    r.P.data_bar = bars + 2 * kStages;
     r.P.stages = smem + kHeaderBytes;
     r.P.stage_bytes = stage_bytes;
     r.P.g = 0;
@@ -166,57 +216,208 @@ __device__ __forceinline__ void cta_end(const CtaRes& r, uint32_t tmem_cols) {
 }
 
 // ------------------------------------------------------------------------------
-// mode-3 pass: rows = 128 consecutive (i, j) points, columns = the k fibre.
+// stencil pass: F = d_s M w_s + g_s(w) in FP32 for every species of one
+// (all i) x TJ x TK tile.  The tile of every species, with a one-point halo in
+// j and k, is loaded with many loads in flight per thread and each FP64 value
+// is split once into FP32 hi + lo in shared memory; every stencil difference
+// is then formed from split pairs at FP32 relative accuracy of the difference.
 template <int GEO>
-__global__ void __launch_bounds__(kThreads, 1)
+struct TileShape {
+    static constexpr bool k3 = (GEO == GEO_BALL || GEO == GEO_CYLINDER);
+    static constexpr int TK = k3 ? 8 : 1;
+    static constexpr int KH = k3 ? 1 : 0;
+    static constexpr bool periodic1 = (GEO == GEO_SPHERE);   // mode 1 is theta on the sphere
+    static constexpr bool periodic2 = (GEO != GEO_SPHERE);   // mode 2 is theta elsewhere
+};
+
+__device__ __forceinline__ float sdiff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+
+constexpr int kTileBatch = 8;   // global loads in flight per thread while filling the tile
+
+constexpr int kRhsThreads = 512;   // 128 lanes along rho x 4 line parities
+
+template <int GEO>
+__global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, const double* __restrict__ Wall,
+                                                          float* __restrict__ F, int TJ) {
+    using TS = TileShape<GEO>;
+    extern __shared__ float2 tile[];                 // [S][nK][nJ][n1]
+    __shared__ float cj[3][32], ck[4][8];            // j- and k-dependent coefficients of the tile
+    __shared__ long long row_off[kMaxSpecies * 10 * 34];   // global offset of each tile row, -1 outside
+    const int n1 = tb.n1, n2 = tb.n2, n3 = tb.n3, S = tb.S;
+    const int j0 = blockIdx.x * TJ, k0 = blockIdx.y * TS::TK;
+    const int nJ = TJ + 2, nK = TS::TK + 2 * TS::KH;
+    const int rows = S * nK * nJ;
+    const long long npts = tb.npts;
+    const long long n12 = (long long)n1 * n2;
+    constexpr int NP = kRhsThreads / 128;            // line parities
+    const int lane = threadIdx.x & 127, rpar = threadIdx.x >> 7;
+    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+        const int jj = row % nJ, kk = (row / nJ) % nK, sp = row / (nJ * nK);
+        int j = j0 - 1 + jj;
+        const int k = k0 - TS::KH + kk;
+        if (TS::periodic2) j = j < 0 ? j + n2 : (j >= n2 ? j - n2 : j);
+        const bool ok = j >= 0 && j < n2 && k >= 0 && k < n3;
+        row_off[row] = ok ? sp * npts + (long long)k * n12 + (long long)j * n1 : -1;
+    }
+    __syncthreads();
+    for (int row0 = rpar; row0 < rows; row0 += NP * kTileBatch) {
+        for (int i = lane; i < n1; i += 128) {
+            double v[kTileBatch];
+#pragma unroll
+            for (int u = 0; u < kTileBatch; ++u) {
+                const int row = row0 + NP * u;
+                const long long off = row < rows ? row_off[row] : -1;
+                v[u] = off >= 0 ? __ldg(Wall + off + i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kTileBatch; ++u) {
+                const int row = row0 + NP * u;
+                if (row < rows) tile[row * n1 + i] = split_f64(v[u]);
+            }
+        }
+    }
+    if (threadIdx.x < TJ) {
+        const int j = min(j0 + (int)threadIdx.x, n2 - 1);
+        cj[0][threadIdx.x] = tb.ax[1].rs[j];
+        cj[1][threadIdx.x] = tb.ax[1].lower[j];
+        cj[2][threadIdx.x] = tb.ax[1].upper[j];
+    }
+    if (TS::k3 && threadIdx.x >= 64 && threadIdx.x < 64 + TS::TK) {
+        const int t = threadIdx.x - 64;
+        const int k = min(k0 + t, n3 - 1);
+        ck[0][t] = tb.ax[2].rs[k];
+        ck[1][t] = tb.ax[2].lower[k];
+        ck[2][t] = tb.ax[2].upper[k];
+        ck[3][t] = (GEO == GEO_BALL) ? tb.Dp[k] : 1.f;
+    }
+    __syncthreads();
+    const int species_stride = nK * nJ * n1;
+    for (int i = lane; i < n1; i += 128) {
+        const StencilAxis<float>& a1 = tb.ax[0];
+        const float lo1 = a1.lower[i], up1 = a1.upper[i], rs1 = a1.rs[i];
+        const float dr = (GEO == GEO_SPHERE) ? 1.f : tb.Dr[i];
+        const bool has_m = i > 0 || TS::periodic1, has_p = i < n1 - 1 || TS::periodic1;
+        const int im = i > 0 ? i - 1 : n1 - 1, ip = i < n1 - 1 ? i + 1 : 0;
+        for (int line = rpar; line < TS::TK * TJ; line += NP) {
+            const int kl = line / TJ, jl = line - kl * TJ;
+            const int j = j0 + jl, k = k0 + kl;
+            if (j >= n2 || k >= n3) continue;
+            const int cidx = ((kl + TS::KH) * nJ + (jl + 1)) * n1 + i;
+            float w[kMaxSpecies];
+#pragma unroll
+            for (int r = 0; r < kMaxSpecies; ++r) {
+                if (r < S) {
+                    const float2 c = tile[r * species_stride + cidx];
+                    w[r] = c.x + c.y;
+                } else {
+                    w[r] = 0.f;
+                }
+            }
+            const long long idx = (long long)k * n12 + (long long)j * n1 + i;
+#pragma unroll
+            for (int s = 0; s < kMaxSpecies; ++s) {
+                if (s >= S) break;
+                const float2* row = tile + s * species_stride + cidx - i;
+                const float2 c = row[i];
+                float t0 = rs1 * (c.x + c.y);
+                if (has_m) t0 += lo1 * sdiff(row[im], c);
+                if (has_p) t0 += up1 * sdiff(row[ip], c);
+                float t1 = cj[0][jl] * (c.x + c.y);
+                if (j > 0 || TS::periodic2) t1 += cj[1][jl] * sdiff(row[i - n1], c);
+                if (j < n2 - 1 || TS::periodic2) t1 += cj[2][jl] * sdiff(row[i + n1], c);
+                float lap;
+                if constexpr (GEO == GEO_DISK) {
+                    lap = t0 + dr * t1;
+                } else if constexpr (GEO == GEO_SPHERE) {
+                    lap = tb.Dp[j] * t0 + t1;
+                } else {
+                    float t2 = ck[0][kl] * (c.x + c.y);
+                    if (k > 0) t2 += ck[1][kl] * sdiff(row[i - nJ * n1], c);
+                    if (k < n3 - 1) t2 += ck[2][kl] * sdiff(row[i + nJ * n1], c);
+                    if constexpr (GEO == GEO_BALL) lap = t0 + dr * (ck[3][kl] * t1 + t2);
+                    else lap = t0 + dr * t1 + t2;
+                }
+                F[s * npts + idx] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------
+// mode-3 pass: rows = 128 consecutive (i, j) points, columns = the k fibre;
+// reads F from Y and overwrites the same entries with the result.
+template <int GEO>
+__global__ void __launch_bounds__(kBlock, 1)
     k_tc_mode3(SplitTables T, uint32_t stage_bytes, uint32_t tmem_cols) {
     extern __shared__ char smem_raw[];
     CtaRes R = cta_begin(smem_raw, stage_bytes, tmem_cols, T.err);
-    const int tid = threadIdx.x;
-    const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
     const int s = blockIdx.y;
     const int n1 = T.n1, n3 = T.n3;
-    const long long n12 = (long long)T.n1 * T.n2;
     const int n3p = (n3 + 15) & ~15;
-    const long long ij = (long long)blockIdx.x * kThreads + tid;
-    const bool valid = ij < n12;
-    const int i = valid ? (int)(ij % n1) : 0;
-    const int j = valid ? (int)(ij / n1) : 0;
-
-    GemmSpec g1{GEO == GEO_BALL ? T.M3a : T.M3b[s], 0, kThreads, 1, n3p, n3p / kKC, R.tmem};
-    run_gemm(R.P, g1, [&](int c, char* hi, char* lo) {
-        float v[16];
-#pragma unroll 4
-        for (int kk = 0; kk < 16; ++kk) {
-            const int k = c * 16 + kk;
-            v[kk] = (valid && k < n3) ? rhs_point<SplitAcc, GEO>(T.rhs, T.state, s, k * n12 + ij, i, j, k) : 0.f;
-        }
-        store_row16(hi, lo, tid, v);
-    });
-    uint32_t last = 0;
-    if constexpr (GEO == GEO_BALL) {
-        GemmSpec g2{T.M3b[0], 0, kThreads, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p};
-        const float ci = valid ? T.had_phi[s * n1 + i] : 0.f;
-        run_gemm(R.P, g2, [&](int c, char* hi, char* lo) {
-            float v[16];
-            tmem_ld16(R.tmem + lane_base + (uint32_t)(c * 16), v);
+    GemmSpec gs[2] = {{GEO == GEO_BALL ? T.M3a : T.M3b[s], 0, kRows, 1, n3p, n3p / kKC, R.tmem},
+                      {T.M3b[0], 0, kRows, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p}};
+    if (threadIdx.x >= kThreads + 32) {
+        mma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);
+    } else if (threadIdx.x >= kThreads) {
+        tma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);
+    } else {
+        const int tid = threadIdx.x;
+        const int r = tid & (kRows - 1), h = tid >> 7;
+        const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
+        const long long n12 = (long long)T.n1 * T.n2;
+        const long long ij = (long long)blockIdx.x * kRows + r;
+        const bool valid = ij < n12;
+        const int i = valid ? (int)(ij % n1) : 0;
+        float* Ys = T.Y + (long long)s * T.npts;
+        // one chunk of register prefetch: the loads of chunk c+1 are in flight while chunk c is split,
+        // stored and multiplied
+        float nxt[8];
+        auto load_f = [&](int c) {
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                const int kp = c * 16 + kk;
-                v[kk] = (valid && kp < n3) ? v[kk] * phi1f(ci * T.lam_phi[kp]) : 0.f;
+            for (int q = 0; q < 8; ++q) {
+                const int k = c * 16 + h * 8 + q;
+                nxt[q] = (valid && k < n3) ? Ys[k * n12 + ij] : 0.f;
             }
-            store_row16(hi, lo, tid, v);
-        });
-        last = (uint32_t)n3p;
-    }
-    float* Ys = T.Y + (long long)s * T.npts;
-    for (int c = 0; c < n3p / 16; ++c) {
-        float v[16];
-        tmem_ld16(R.tmem + lane_base + last + (uint32_t)(c * 16), v);
+        };
+        load_f(0);
+        run_gemm(R.P, gs[0], [&](int c, char* hi, char* lo) {
+            float v[8];
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            const int k = c * 16 + kk;
-            if (valid && k < n3) Ys[k * n12 + ij] = v[kk];
+            for (int q = 0; q < 8; ++q) v[q] = nxt[q];
+            if (c + 1 < gs[0].k_chunks) load_f(c + 1);
+            store_row8(hi, lo, r, h, v);
+        });
+        uint32_t last = 0;
+        if constexpr (GEO == GEO_BALL) {
+            const float* had = T.had_phi + (long long)s * n3 * n1 + i;
+            auto load_h = [&](int c) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int kp = c * 16 + h * 8 + q;
+                    nxt[q] = (valid && kp < n3) ? __ldg(had + kp * n1) : 0.f;
+                }
+            };
+            load_h(0);
+            run_gemm(R.P, gs[1], [&](int c, char* hi, char* lo) {
+                float v[8], f[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) f[q] = nxt[q];
+                if (c + 1 < gs[1].k_chunks) load_h(c + 1);
+                tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] *= f[q];
+                store_row8(hi, lo, r, h, v);
+            });
+            last = (uint32_t)n3p;
+        }
+        for (int c = 0; c < n3p / 16; ++c) {
+            float v[8];
+            tmem_ld8(R.tmem + lane_base + last + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = c * 16 + h * 8 + q;
+                if (valid && k < n3) Ys[k * n12 + ij] = v[q];
+            }
         }
     }
     cta_end(R, tmem_cols);
@@ -229,60 +430,81 @@ struct SlabJob {
     const float* Y;       // F after the earlier directions, slab base
     double* W;            // state slab base (updated)
     Image QT, Q, P;
-    const float* had_c;   // per rho-row coefficient c_i: Phi = phi_1(c_i lambda_theta_j)
-    const float* lam;     // eigenvalues of A_theta in the column order of Q
-    double tau;
+    const float* had;     // Phi of the theta direction for this slab, [j'][i]
+    float tau_f;
 };
 
-__device__ __forceinline__ void slab_body(const SlabJob& J, Pipe& P, uint32_t tmem, char* epi) {
+// The three products of a slab and their tensor-memory columns: G1 [0, n2p),
+// G2 [n2p, n2p + m2 n1p), G3 reuses [0, m2 n1p) when that does not reach G2.
+__device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, GemmSpec* gs, uint32_t* cols) {
+    const int n1p = (J.n1 + 15) & ~15, n2p = (J.n2 + 15) & ~15, m2 = (J.n2 + 127) / 128;
+    cols[0] = 0;
+    cols[1] = (uint32_t)n2p;
+    cols[2] = (m2 * n1p <= n2p) ? 0u : (uint32_t)(n2p + m2 * n1p);
+    gs[0] = GemmSpec{J.QT, 0, kRows, 1, n2p, n2p / kKC, tmem + cols[0]};
+    gs[1] = GemmSpec{J.Q, 1, n1p, m2, n1p, n2p / kKC, tmem + cols[1]};
+    gs[2] = GemmSpec{J.P, 0, kRows * m2, m2, n1p, n1p / kKC, tmem + cols[2]};
+}
+
+__device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* gs, const uint32_t* cols, Pipe& P,
+                                             uint32_t tmem, char* epi) {
     const int tid = threadIdx.x;
-    const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
+    const int r = tid & (kRows - 1), h = tid >> 7;
+    const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
     const int n1 = J.n1, n2 = J.n2;
-    const int n1p = (n1 + 15) & ~15, n2p = (n2 + 15) & ~15, m2 = (n2 + 127) / 128;
-    const uint32_t c1 = 0, c2 = (uint32_t)n2p;
-    const uint32_t c3 = (m2 * n1p <= n2p) ? 0u : (uint32_t)(n2p + m2 * n1p);
+    const int n1p = (n1 + 15) & ~15, m2 = (n2 + 127) / 128;
+    const uint32_t c1 = cols[0], c2 = cols[1], c3 = cols[2];
 
     // G1: X[i][j'] = sum_j Y[i][j] Q[j][j']          (Y x_2 Q_theta^T), rows i
-    GemmSpec g1{J.QT, 0, kThreads, 1, n2p, n2p / kKC, tmem + c1};
-    run_gemm(P, g1, [&](int c, char* hi, char* lo) {
-        float v[16];
-        const int i = tid;
+    float nxt[8];     // one chunk of register prefetch of the global operands
+    auto load_y = [&](int c) {
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            const int j = c * 16 + kk;
-            v[kk] = (i < n1 && j < n2) ? J.Y[j * n1 + i] : 0.f;
+        for (int q = 0; q < 8; ++q) {
+            const int j = c * 16 + h * 8 + q;
+            nxt[q] = (r < n1 && j < n2) ? J.Y[j * n1 + r] : 0.f;
         }
-        store_row16(hi, lo, tid, v);
+    };
+    load_y(0);
+    run_gemm(P, gs[0], [&](int c, char* hi, char* lo) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = nxt[q];
+        if (c + 1 < gs[0].k_chunks) load_y(c + 1);
+        store_row8(hi, lo, r, h, v);
     });
     // G2: Z^T[j][i] = sum_j' Q[j][j'] (Phi o X)[i][j']   (x_2 Q_theta), data in B, rows j
-    GemmSpec g2{J.Q, 1, n1p, m2, n1p, n2p / kKC, tmem + c2};
-    const float ci = (tid < n1) ? J.had_c[tid] : 0.f;
-    run_gemm(P, g2, [&](int c, char* hi, char* lo) {
-        float v[16];
-        tmem_ld16(tmem + lane_base + c1 + (uint32_t)(c * 16), v);
-        const int i = tid;
-        if (i < n1p) {
+    auto load_h = [&](int c) {
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                const int jp = c * 16 + kk;
-                v[kk] = (i < n1 && jp < n2) ? v[kk] * phi1f(ci * J.lam[jp]) : 0.f;
-            }
-            store_row16(hi, lo, i, v);
+        for (int q = 0; q < 8; ++q) {
+            const int jp = c * 16 + h * 8 + q;
+            nxt[q] = (r < n1 && jp < n2) ? __ldg(J.had + jp * n1 + r) : 0.f;
+        }
+    };
+    load_h(0);
+    run_gemm(P, gs[1], [&](int c, char* hi, char* lo) {
+        float v[8], f[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) f[q] = nxt[q];
+        if (c + 1 < gs[1].k_chunks) load_h(c + 1);
+        tmem_ld8(tmem + lane_base + c1 + (uint32_t)(c * 16 + h * 8), v);
+        if (r < n1p) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] *= f[q];
+            store_row8(hi, lo, r, h, v);
         }
     });
     // G3: R^T[j][i'] = sum_i Z^T[j][i] P[i'][i]      (x_1 phi_1(tau d A_rho)), rows j
-    GemmSpec g3{J.P, 0, kThreads * m2, m2, n1p, n1p / kKC, tmem + c3};
-    run_gemm(P, g3, [&](int c, char* hi, char* lo) {
+    run_gemm(P, gs[2], [&](int c, char* hi, char* lo) {
         for (int mt = 0; mt < m2; ++mt) {
-            float v[16];
-            tmem_ld16(tmem + lane_base + c2 + (uint32_t)(mt * n1p + c * 16), v);
-            const int j = mt * kThreads + tid;
+            float v[8];
+            tmem_ld8(tmem + lane_base + c2 + (uint32_t)(mt * n1p + c * 16 + h * 8), v);
+            const int j = mt * kRows + r;
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                const int i = c * 16 + kk;
-                if (!(j < n2 && i < n1)) v[kk] = 0.f;
+            for (int q = 0; q < 8; ++q) {
+                const int i = c * 16 + h * 8 + q;
+                if (!(j < n2 && i < n1)) v[q] = 0.f;
             }
-            store_row16(hi, lo, mt * kThreads + tid, v);
+            store_row8(hi, lo, mt * kRows + r, h, v);
         }
     });
     // w[k][j][i'] += tau R^T[j][i'], staged through shared memory for coalesced FP64 RMW.
@@ -290,23 +512,38 @@ __device__ __forceinline__ void slab_body(const SlabJob& J, Pipe& P, uint32_t tm
     const int pitch = n1p + 1;
     for (int mt = 0; mt < m2; ++mt) {
         for (int c = 0; c < n1p / 16; ++c) {
-            float v[16];
-            tmem_ld16(tmem + lane_base + c3 + (uint32_t)(mt * n1p + c * 16), v);
+            float v[8];
+            tmem_ld8(tmem + lane_base + c3 + (uint32_t)(mt * n1p + c * 16 + h * 8), v);
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) E[tid * pitch + c * 16 + kk] = v[kk];
+            for (int q = 0; q < 8; ++q) E[r * pitch + c * 16 + h * 8 + q] = v[q];
         }
-        __syncthreads();
-        const int rows = min(kThreads, n2 - mt * kThreads);
-        double* Wt = J.W + (long long)mt * kThreads * n1;
-        for (int f = tid; f < rows * n1; f += kThreads) {
-            const int jl = f / n1, i = f - jl * n1;
-            Wt[f] += J.tau * (double)E[jl * pitch + i];
+        compute_sync();
+        const int rows = min(kRows, n2 - mt * kRows);
+        const int count = rows * n1;
+        double* Wt = J.W + (long long)mt * kRows * n1;
+        // increment rounded to FP32, widened exactly by integer operations: one FP64 add per
+        // point; eight independent read-modify-writes in flight per thread
+        for (int f0 = tid; f0 < count; f0 += kThreads * 8) {
+            double w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = f0 + u * kThreads;
+                w[u] = f < count ? Wt[f] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = f0 + u * kThreads;
+                if (f < count) {
+                    const int jl = f / n1, i = f - jl * n1;
+                    Wt[f] = w[u] + f32_to_f64(J.tau_f * E[jl * pitch + i]);
+                }
+            }
         }
-        __syncthreads();
+        compute_sync();
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kBlock, 1)
     k_tc_slab(SplitTables T, uint32_t stage_bytes, uint32_t tmem_cols) {
     extern __shared__ char smem_raw[];
     CtaRes R = cta_begin(smem_raw, stage_bytes, tmem_cols, T.err);
@@ -320,29 +557,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     J.QT = T.QT;
     J.Q = T.Q;
     J.P = T.P[s];
-    J.had_c = T.had_theta + (long long)s * T.had_theta_sp + (T.geometry == GEO_BALL ? (long long)k * T.n1 : 0);
-    J.lam = T.lam_theta;
-    J.tau = T.tau_d;
-    slab_body(J, R.P, R.tmem, R.P.stages);
+    J.had = T.had_theta + (long long)s * T.had_theta_sp + (T.geometry == GEO_BALL ? k * n12 : 0);
+    J.tau_f = T.tau;
+    GemmSpec gs[3];
+    uint32_t cols[3];
+    slab_specs(J, R.tmem, gs, cols);
+    if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
+    else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
+    else slab_compute(J, gs, cols, R.P, R.tmem, R.P.stages);
     cta_end(R, tmem_cols);
-}
-
-// F in FP32 at FP64-accurate differences (disk: the only direction before the slab pass).
-template <int GEO>
-__global__ void __launch_bounds__(256) k_rhs_split(RhsTables<float> tb, const double* __restrict__ W,
-                                                   float* __restrict__ Y) {
-    const long long npts = tb.npts;
-    const long long total = npts * tb.S;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(t / npts);
-        const long long idx = t - (long long)s * npts;
-        const int i = (int)(idx % tb.n1);
-        const long long rest = idx / tb.n1;
-        const int j = (int)(rest % tb.n2);
-        const int k = (int)(rest / tb.n2);
-        Y[t] = rhs_point<SplitAcc, GEO>(tb, W, s, idx, i, j, k);
-    }
 }
 
 // ------------------------------------------------------------------------------
@@ -361,7 +584,7 @@ TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3) {
     (void)n2;
     TcShape sh{};
     const uint32_t n3p = round_up(n3, 16);
-    sh.stage_bytes = round_up(2u * kThreads * kTileRowBytes + 2u * n3p * kTileRowBytes, 1024);
+    sh.stage_bytes = round_up(2u * kRows * kTileRowBytes + 2u * n3p * kTileRowBytes, 1024);
     sh.tmem_cols = pow2_cols(geometry == GEO_BALL ? 2 * n3p : n3p);
     sh.smem_bytes = 1024 + kHeaderBytes + kStages * sh.stage_bytes;
     return sh;
@@ -370,13 +593,13 @@ TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3) {
 TcShape tc_slab_shape(int n1, int n2) {
     TcShape sh{};
     const uint32_t n1p = round_up(n1, 16), n2p = round_up(n2, 16), m2 = (n2 + 127) / 128;
-    const uint32_t rows1 = kThreads + n2p;              // G1: data 128 rows, matrix n2p rows
-    const uint32_t rows2 = n1p + kThreads * m2;         // G2: data n1p rows, matrix 128 m2 rows
-    const uint32_t rows3 = kThreads * m2 + n1p;         // G3
+    const uint32_t rows1 = kRows + n2p;                 // G1: data 128 rows, matrix n2p rows
+    const uint32_t rows2 = n1p + kRows * m2;            // G2: data n1p rows, matrix 128 m2 rows
+    const uint32_t rows3 = kRows * m2 + n1p;            // G3
     uint32_t rows = rows1 > rows2 ? rows1 : rows2;
     rows = rows > rows3 ? rows : rows3;
     sh.stage_bytes = round_up(2u * rows * kTileRowBytes, 1024);
-    const uint32_t epi = kThreads * (n1p + 1) * 4u;
+    const uint32_t epi = kRows * (n1p + 1) * 4u;
     uint32_t body = kStages * sh.stage_bytes;
     if (body < epi) {
         sh.stage_bytes = round_up((epi + kStages - 1) / kStages, 1024);
@@ -400,35 +623,72 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
         if (e != cudaSuccess) return e;
     }
     if (smem_slab) e = cudaFuncSetAttribute(k_tc_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_slab);
+    if (e != cudaSuccess) return e;
+    const int big = 212 * 1024;   // stencil tiles (all species) are sized to at most 212 KB
+    e = cudaFuncSetAttribute(k_rhs_tile<GEO_DISK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_tile<GEO_SPHERE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_tile<GEO_BALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_tile<GEO_CYLINDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     return e;
 }
 
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
-    dim3 grid((unsigned)((T.n1 * (long long)T.n2 + kThreads - 1) / kThreads), T.S);
+    dim3 grid((unsigned)((T.n1 * (long long)T.n2 + kRows - 1) / kRows), T.S);
     if (T.geometry == GEO_BALL)
-        k_tc_mode3<GEO_BALL><<<grid, kThreads, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
+        k_tc_mode3<GEO_BALL><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
     else
-        k_tc_mode3<GEO_CYLINDER><<<grid, kThreads, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
+        k_tc_mode3<GEO_CYLINDER><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid(T.geometry == GEO_DISK ? 1 : T.n3, T.S);
-    k_tc_slab<<<grid, kThreads, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
+    k_tc_slab<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
+    return cudaGetLastError();
+}
+
+// j-tile of the stencil pass: among the sizes whose all-species tile fits in
+// 200 KB, the one with the least (waves x lines per CTA), i.e. the shortest
+// critical path when CTAs are spread over the 152 SMs.
+template <int GEO>
+static int rhs_tile_tj(const SplitTables& T) {
+    using TS = TileShape<GEO>;
+    const size_t per_line = sizeof(float2) * (size_t)T.S * (TS::TK + 2 * TS::KH) * T.n1;
+    const long long ktiles = (T.n3 + TS::TK - 1) / TS::TK;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int tj = 1; tj <= (TS::k3 ? 16 : 32); ++tj) {
+        const size_t smem = per_line * (tj + 2) + 8 * 1024;
+        if (smem > 220 * 1024) break;
+        const long long per_sm = std::min<long long>(228 * 1024 / smem, 2048 / kRhsThreads);
+        const long long ctas = (T.n2 + tj - 1) / tj * ktiles;
+        const long long waves = (ctas + 152 * per_sm - 1) / (152 * per_sm);
+        const double cost = (double)waves * tj * (1.0 + 2.0 / tj * 0.25);   // halo rows cost a quarter line
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = tj;
+        }
+    }
+    return best;
+}
+
+template <int GEO>
+static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
+    using TS = TileShape<GEO>;
+    const int tj = rhs_tile_tj<GEO>(T);
+    const size_t smem = sizeof(float2) * (size_t)T.S * (TS::TK + 2 * TS::KH) * (tj + 2) * T.n1;
+    dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + TS::TK - 1) / TS::TK, 1);
+    k_rhs_tile<GEO><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st) {
-    const long long total = T.npts * T.S;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
     switch (T.geometry) {
-    case GEO_DISK: k_rhs_split<GEO_DISK><<<(int)blocks, 256, 0, st>>>(T.rhs, T.state, T.Y); break;
-    case GEO_SPHERE: k_rhs_split<GEO_SPHERE><<<(int)blocks, 256, 0, st>>>(T.rhs, T.state, T.Y); break;
-    case GEO_BALL: k_rhs_split<GEO_BALL><<<(int)blocks, 256, 0, st>>>(T.rhs, T.state, T.Y); break;
-    default: k_rhs_split<GEO_CYLINDER><<<(int)blocks, 256, 0, st>>>(T.rhs, T.state, T.Y); break;
+    case GEO_DISK: return launch_rhs_tile_geo<GEO_DISK>(T, st);
+    case GEO_SPHERE: return launch_rhs_tile_geo<GEO_SPHERE>(T, st);
+    case GEO_BALL: return launch_rhs_tile_geo<GEO_BALL>(T, st);
+    default: return launch_rhs_tile_geo<GEO_CYLINDER>(T, st);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace sexpe

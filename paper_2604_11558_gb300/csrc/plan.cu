@@ -235,10 +235,10 @@ sexpe_status build_rhs_tables(sexpe_plan* p, RhsTables<T>* tb, cudaStream_t st) 
         }
         SX_TRY(upload(p, dp, &tb->Dp, st));
     }
-    for (int s = 0; s < kMaxSpecies; ++s) tb->d[s] = s < p->S ? p->d[s] : 0.0;
+    for (int s = 0; s < kMaxSpecies; ++s) tb->d[s] = (T)(s < p->S ? p->d[s] : 0.0);
     tb->reac.kind = p->reaction;
     tb->reac.S = p->S;
-    for (int q = 0; q < 16; ++q) tb->reac.p[q] = q < (int)p->params.size() ? p->params[q] : 0.0;
+    for (int q = 0; q < 16; ++q) tb->reac.p[q] = (T)(q < (int)p->params.size() ? p->params[q] : 0.0);
     return SEXPE_OK;
 }
 
@@ -308,16 +308,17 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     Eigen th = theta_eigen(p->ax[1]);
     SX_TRY(upload_image(p, n2, n2, n2p, n2p, [&](int r, int k) { return th.V(k, r); }, &T.QT, st));
     SX_TRY(upload_image(p, n2, n2, 128 * m2, n2p, [&](int r, int k) { return th.V(r, k); }, &T.Q, st));
-    std::vector<float> lam(th.lam.begin(), th.lam.end());
-    SX_TRY(upload(p, lam, &T.lam_theta, st));
+    // Phi of the theta direction: phi_1(tau d_s s(i, k) lambda_theta_j'), one FP64 evaluation rounded once.
     const bool ball = p->geometry == SEXPE_BALL;
-    T.had_theta_sp = ball ? (long long)n3 * n1 : n1;
+    const long long n12 = (long long)n1 * n2;
+    T.had_theta_sp = ball ? p->npts : n12;
     std::vector<float> hc((size_t)p->S * T.had_theta_sp);
     for (int s = 0; s < p->S; ++s)
         for (int k = 0; k < (ball ? n3 : 1); ++k)
-            for (int i = 0; i < n1; ++i)
-                hc[(size_t)s * T.had_theta_sp + (size_t)k * n1 + i] =
-                    (float)(p->tau * p->d[s] * dir_scale(p, 2, i, 0, k));
+            for (int jp = 0; jp < n2; ++jp)
+                for (int i = 0; i < n1; ++i)
+                    hc[(size_t)s * T.had_theta_sp + (size_t)k * n12 + (size_t)jp * n1 + i] =
+                        (float)phi1_scalar(p->tau * p->d[s] * dir_scale(p, 2, i, 0, k) * th.lam[jp]);
     SX_TRY(upload(p, hc, &T.had_theta, st));
     // rho direction (mode 1): phi_1(tau d_s A_rho) per species
     const Mat Arho = p->ax[0].dense();
@@ -336,11 +337,12 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
             if (!all_finite(ph.V.a) || !all_finite(ph.Vinv.a)) return SEXPE_ENUMERIC;
             SX_TRY(upload_image(p, n3, n3, n3p, n3p, [&](int r, int k) { return ph.Vinv(r, k); }, &T.M3a, st));
             SX_TRY(upload_image(p, n3, n3, n3p, n3p, [&](int r, int k) { return ph.V(r, k); }, &T.M3b[0], st));
-            std::vector<float> lp(ph.lam.begin(), ph.lam.end());
-            SX_TRY(upload(p, lp, &T.lam_phi, st));
-            std::vector<float> hp((size_t)p->S * n1);
+            std::vector<float> hp((size_t)p->S * n3 * n1);
             for (int s = 0; s < p->S; ++s)
-                for (int i = 0; i < n1; ++i) hp[(size_t)s * n1 + i] = (float)(p->tau * p->d[s] * dir_scale(p, 3, i, 0, 0));
+                for (int kp = 0; kp < n3; ++kp)
+                    for (int i = 0; i < n1; ++i)
+                        hp[((size_t)s * n3 + kp) * n1 + i] =
+                            (float)phi1_scalar(p->tau * p->d[s] * dir_scale(p, 3, i, 0, 0) * ph.lam[kp]);
             SX_TRY(upload(p, hp, &T.had_phi, st));
         } else {
             const Mat Az = p->ax[2].dense();
@@ -357,7 +359,7 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     p->shs = tc_slab_shape(n1, n2);
     if (p->shs.smem_bytes > 227 * 1024 || p->sh3.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
     SX_CUDA(tc_prepare(p->ndim == 3 ? p->sh3.smem_bytes : 0, p->shs.smem_bytes));
-    p->kernels_per_step = 2;
+    p->kernels_per_step = p->ndim == 3 ? 3 : 2;
     return SEXPE_OK;
 }
 
@@ -441,8 +443,11 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
     T.state = state;
     T.state_upd = state;
     SX_CUDA(prof_mark(p, st));
-    if (p->ndim == 3) SX_CUDA(launch_tc_mode3(T, p->sh3, st));
-    else SX_CUDA(launch_rhs_split(T, st));
+    SX_CUDA(launch_rhs_split(T, st));
+    if (p->ndim == 3) {
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_tc_mode3(T, p->sh3, st));
+    }
     SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_tc_slab(T, p->shs, st));
     return SEXPE_OK;
@@ -551,8 +556,8 @@ sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float
     T.state = state;
     T.state_upd = state;
     T.Y = Y;
+    SX_CUDA(launch_rhs_split(T, st));
     if (p->ndim == 3) SX_CUDA(launch_tc_mode3(T, p->sh3, st));
-    else SX_CUDA(launch_rhs_split(T, st));
     SX_CUDA(launch_tc_slab(T, p->shs, st));
     return SEXPE_OK;
 }

@@ -163,6 +163,32 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_h
 /* Free every device table of the plan (after synchronising its device). */
 sexpe_status sexpe_destroy(sexpe_plan* plan);
 
+/* Forward steps that also keep checkpoints for sexpe_adjoint: like sexpe_step,
+ * and before every step k with k % every == 0 the current state is copied to
+ * checkpoints_dev + (k / every) * state_elems (caller-owned device buffer of
+ * ceil(n_steps / every) states).  Enqueued on `stream`. */
+sexpe_status sexpe_step_checkpointed(sexpe_plan* plan, double* state_dev, int64_t n_steps, int32_t every,
+                                     double* checkpoints_dev, void* stream);
+
+/* Discrete adjoint of n_ckpt * every steps (the adjoint of the step map of
+ * eqs. ee/splitorder; the paper has no adjoint).  Given checkpoints_dev from
+ * sexpe_step_checkpointed (n_ckpt states, `every` steps apart) and the
+ * gradient of a scalar loss with respect to the final state, dL_dWT_dev, it
+ * writes the gradient with respect to the initial state to dL_dW0_dev (may
+ * alias dL_dWT_dev) and, if dL_dparams_host is not NULL, the parameter
+ * gradient in the order: the reaction parameters as given to sexpe_setup,
+ * then d_s for every species.  Per step, with mu_s = tau P_s^T lambda_s:
+ * lambda_r <- lambda_r + d_r M^T mu_r + sum_s (dg_s/dw_r) mu_s, where P_s^T is
+ * the transposed phi_1 chain in reverse order; dL/dd_s adds <mu_s, M w_s> and
+ * tau <lambda_s, (dP_s/dd_s) F_s> with dphi_1(tau d s A)/dd = V diag(tau s lambda
+ * phi_1'(tau d s lambda)) V^{-1}, phi_1' = phi_1 - phi_2.  Each checkpoint
+ * segment is recomputed forward.  FP64 plans only (SEXPE_EUNSUPPORTED
+ * otherwise); the first call builds the adjoint tables and work buffers
+ * (device allocations); the parameter gradient is copied to the host and the
+ * stream synchronised when dL_dparams_host is given. */
+sexpe_status sexpe_adjoint(sexpe_plan* plan, const double* checkpoints_dev, int32_t n_ckpt, int32_t every,
+                           const double* dL_dWT_dev, double* dL_dW0_dev, double* dL_dparams_host, void* stream);
+
 /* Per-kernel timing.  After sexpe_profile_begin(plan, max_steps), the next
  * steps (up to max_steps, across sexpe_step calls on one stream) launch their
  * kernels directly (no graph) with a CUDA event recorded on the launching

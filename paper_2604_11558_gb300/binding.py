@@ -76,6 +76,8 @@ def lib():
         L.sexpe_synchronize.argtypes = [_P, _P]
         L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
         L.sexpe_destroy.argtypes = [_P]
+        L.sexpe_step_checkpointed.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
+        L.sexpe_adjoint.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _DP, _P]
         L.sexpe_profile_begin.argtypes = [_P, ctypes.c_int32]
         L.sexpe_profile_end.argtypes = [_P, _DP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
         L.sexpe_axis_matrix.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _DP]
@@ -84,6 +86,7 @@ def lib():
         for name in ["sexpe_setup", "sexpe_batch_setup", "sexpe_state_offsets", "sexpe_step", "sexpe_step_host",
                      "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
                      "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
+                     "sexpe_step_checkpointed", "sexpe_adjoint",
                      "sexpe_axis_phi1", "sexpe_axis_eigen"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
@@ -145,6 +148,7 @@ class Plan:
                              ctypes.byref(h)), "sexpe_setup")
         self.handle = h
         self.geometry, self.n, self.S = geometry, tuple(n), len(self._d)
+        self._p_list = list(params)
 
     @classmethod
     def from_workload(cls, w, precision="split_tf32", stream=None):
@@ -175,6 +179,20 @@ class Plan:
 
     def synchronize(self, stream=None):
         _check(lib().sexpe_synchronize(self.handle, _stream_ptr(stream)), "sexpe_synchronize")
+
+    def step_checkpointed(self, state, n_steps, every, checkpoints, stream=None):
+        """Advance `state` n_steps steps, storing the state before every `every`-th step in `checkpoints`
+        (a CUDA float64 tensor of ceil(n_steps/every) states)."""
+        _check(lib().sexpe_step_checkpointed(self.handle, _data_ptr(state), int(n_steps), int(every),
+                                             _data_ptr(checkpoints), _stream_ptr(stream)), "sexpe_step_checkpointed")
+
+    def adjoint(self, checkpoints, n_ckpt, every, dL_dWT, dL_dW0, stream=None):
+        """sexpe_adjoint: writes dL/dW0 into dL_dW0 and returns the parameter gradient
+        (reaction parameters, then the diffusion of every species) as a numpy array."""
+        out = np.zeros(len(self._p_list) + self.S)
+        _check(lib().sexpe_adjoint(self.handle, _data_ptr(checkpoints), int(n_ckpt), int(every), _data_ptr(dL_dWT),
+                                   _data_ptr(dL_dW0), _dptr_out(out), _stream_ptr(stream)), "sexpe_adjoint")
+        return out
 
     def profile_begin(self, max_steps):
         _check(lib().sexpe_profile_begin(self.handle, int(max_steps)), "sexpe_profile_begin")
@@ -230,3 +248,40 @@ def axis_eigen(axis, n, extent=1.0):
 def _dptr_out(a):
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return ctypes.cast(a.ctypes.data, _DP)
+
+
+def _autograd_function():
+    import torch
+
+    class SplitEulerEvolve(torch.autograd.Function):
+        """W_N = (n_steps split exponential Euler steps)(W_0) with the library's
+        checkpointed forward and discrete adjoint.  `params` is a CPU float64
+        tensor holding the values the plan was built with (reaction parameters,
+        then the diffusion coefficients); its gradient is the adjoint's
+        parameter gradient.  FP64 plans."""
+
+        @staticmethod
+        def forward(ctx, W0, params, plan, n_steps, every):
+            n_ckpt = -(-n_steps // every)
+            ckpt = torch.empty((n_ckpt,) + tuple(W0.shape), dtype=torch.float64, device=W0.device)
+            W = W0.detach().clone().contiguous()
+            plan.step_checkpointed(W, n_steps, every, ckpt)
+            ctx.plan, ctx.every, ctx.n_ckpt = plan, every, n_ckpt
+            ctx.save_for_backward(ckpt)
+            if n_steps != n_ckpt * every:
+                raise ValueError("n_steps must be a multiple of every")
+            return W
+
+        @staticmethod
+        def backward(ctx, gW):
+            (ckpt,) = ctx.saved_tensors
+            g0 = torch.empty_like(gW)
+            gp = ctx.plan.adjoint(ckpt, ctx.n_ckpt, ctx.every, gW.contiguous(), g0)
+            return g0, torch.from_numpy(gp), None, None, None
+
+    return SplitEulerEvolve
+
+
+def evolve(plan, W0, params, n_steps, every):
+    """Differentiable n_steps-step evolution (see SplitEulerEvolve)."""
+    return _autograd_function().apply(W0, params, plan, n_steps, every)

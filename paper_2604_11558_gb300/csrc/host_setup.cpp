@@ -352,4 +352,16 @@ Mat phi1_pade(const Mat& X) {
 
 double phi1_scalar(double x) { return x == 0.0 ? 1.0 : std::expm1(x) / x; }
 
+double dphi1_scalar(double x) {
+    if (std::fabs(x) < 0.1) {
+        double term = 0.5, sum = 0.5;          // k = 0: 1/2!
+        for (int k = 1; k <= 12; ++k) {
+            term *= x / (k + 2);               // x^k / (k+2)!  (times (k+1), applied below)
+            sum += (k + 1) * term;
+        }
+        return sum;
+    }
+    return (x + std::expm1(x) * (x - 1.0)) / (x * x);
+}
+
 }  // namespace sexpe

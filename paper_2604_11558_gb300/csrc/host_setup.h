@@ -52,4 +52,8 @@ Mat phi1_pade(const Mat& X);
 // Scalar phi_1(x) = expm1(x)/x, 1 at 0.
 double phi1_scalar(double x);
 
+// Derivative phi_1'(x) = phi_1(x) - phi_2(x) = (x + expm1(x)(x - 1))/x^2, 1/2 at 0
+// (Taylor series sum_k (k+1) x^k/(k+2)! for |x| < 0.1).
+double dphi1_scalar(double x);
+
 }  // namespace sexpe

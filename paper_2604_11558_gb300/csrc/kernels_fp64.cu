@@ -83,6 +83,215 @@ __global__ void __launch_bounds__(256) k_gemm64(Gemm64 g) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Discrete adjoint of the step (derived from eqs. ee and splitorder; the paper
+// has no adjoint).  With mu_s = tau P_s^T lambda_s:
+//   lambda_r += d_r (M^T mu_r) + sum_s (dG_s/dW_r) mu_s.
+// M^T keeps the Kronecker structure: along mode m, (A^T x)_r = a_r x_r
+// + c-entry of row r+1 times x_{r+1} + b-entry of row r-1 times x_{r-1},
+// scaled by the point's own diagonal factors of the other modes.
+
+__device__ __forceinline__ double axisT(const StencilAxis<double>& ax, const double* x, long long idx, int r,
+                                        long long st) {
+    // ax.rs carries the full diagonal a_r here
+    double acc = ax.rs[r] * x[idx];
+    if (r < ax.n - 1) acc += ax.lower[r + 1] * x[idx + st];
+    else if (ax.periodic) acc += ax.lower[0] * x[idx - (long long)(ax.n - 1) * st];
+    if (r > 0) acc += ax.upper[r - 1] * x[idx - st];
+    else if (ax.periodic) acc += ax.upper[ax.n - 1] * x[idx + (long long)(ax.n - 1) * st];
+    return acc;
+}
+
+template <int GEO>
+__device__ __forceinline__ double laplacianT(const RhsTables<double>& tb, const double* x, long long idx, int i, int j,
+                                             int k) {
+    const double t0 = axisT(tb.ax[0], x, idx, i, 1);
+    const double t1 = axisT(tb.ax[1], x, idx, j, tb.n1);
+    if constexpr (GEO == GEO_DISK) return t0 + tb.Dr[i] * t1;
+    if constexpr (GEO == GEO_SPHERE) return tb.Dp[j] * t0 + t1;
+    const double t2 = axisT(tb.ax[2], x, idx, k, (long long)tb.n1 * tb.n2);
+    if constexpr (GEO == GEO_BALL) return t0 + tb.Dr[i] * (tb.Dp[k] * t1 + t2);
+    return t0 + tb.Dr[i] * t1 + t2;
+}
+
+// sum_s (dG_s/dW_r) mu_s at one point, for species r.
+__device__ __forceinline__ double reaction_jt(const ReactionParams<double>& rp, const double* w, const double* mu,
+                                              int r) {
+    switch (rp.kind) {
+    case R_SCHNAKENBERG: {
+        const double g = rp.p[0], u = w[0], v = w[1];
+        // f = g(a - u + u^2 v), h = g(b - u^2 v)
+        return r == 0 ? mu[0] * g * (-1.0 + 2.0 * u * v) - mu[1] * 2.0 * g * u * v
+                      : mu[0] * g * u * u - mu[1] * g * u * u;
+    }
+    case R_GRAY_SCOTT: {
+        const double F = rp.p[0], kk = rp.p[1], u = w[0], v = w[1];
+        // f = -u v^2 + F(1-u), h = u v^2 - (F+k) v
+        return r == 0 ? mu[0] * (-v * v - F) + mu[1] * v * v
+                      : mu[0] * (-2.0 * u * v) + mu[1] * (2.0 * u * v - (F + kk));
+    }
+    case R_LINEAR_CUBIC: {
+        double acc = -3.0 * w[r] * w[r] * mu[r];
+        for (int i = 0; i < rp.S; ++i) acc += mu[i] * rp.p[i * rp.S + r];
+        return acc;
+    }
+    default:
+        return 0.0;
+    }
+}
+
+template <int GEO>
+__global__ void __launch_bounds__(256) k_adj_lambda(RhsTables<double> tb, const double* __restrict__ W,
+                                                    const double* __restrict__ mu, double* __restrict__ lam) {
+    const long long npts = tb.npts;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < npts;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % tb.n1);
+        const long long rest = idx / tb.n1;
+        const int j = (int)(rest % tb.n2);
+        const int k = (int)(rest / tb.n2);
+        double w[kMaxSpecies], m[kMaxSpecies];
+        for (int r = 0; r < kMaxSpecies; ++r) {
+            w[r] = r < tb.S ? W[r * npts + idx] : 0.0;
+            m[r] = r < tb.S ? mu[r * npts + idx] : 0.0;
+        }
+        for (int r = 0; r < tb.S; ++r)
+            lam[r * npts + idx] += tb.d[r] * laplacianT<GEO>(tb, mu + r * npts, idx, i, j, k) +
+                                   reaction_jt(tb.reac, w, m, r);
+    }
+}
+
+// Per-point contributions to the parameter gradient: reaction parameters
+// sum_s mu_s dG_s/dp, then <mu_s, (M W_s)> for the diffusion of each species.
+template <int GEO>
+__global__ void __launch_bounds__(256) k_adj_params(RhsTables<double> tb, const double* __restrict__ W,
+                                                    const double* __restrict__ mu, double* __restrict__ acc) {
+    constexpr int kSlots = 16 + kMaxSpecies;
+    __shared__ double red[kSlots][8];
+    double part[kSlots];
+    for (int q = 0; q < kSlots; ++q) part[q] = 0.0;
+    const long long npts = tb.npts;
+    const int np = tb.reac.kind == R_SCHNAKENBERG ? 3 : (tb.reac.kind == R_GRAY_SCOTT ? 2 :
+                   (tb.reac.kind == R_LINEAR_CUBIC ? tb.S * tb.S : 0));
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < npts;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % tb.n1);
+        const long long rest = idx / tb.n1;
+        const int j = (int)(rest % tb.n2);
+        const int k = (int)(rest / tb.n2);
+        double w[kMaxSpecies], m[kMaxSpecies];
+        for (int r = 0; r < kMaxSpecies; ++r) {
+            w[r] = r < tb.S ? W[r * npts + idx] : 0.0;
+            m[r] = r < tb.S ? mu[r * npts + idx] : 0.0;
+        }
+        switch (tb.reac.kind) {
+        case R_SCHNAKENBERG: {   // params (gamma, a, b)
+            const double u2v = w[0] * w[0] * w[1];
+            part[0] += m[0] * (tb.reac.p[1] - w[0] + u2v) + m[1] * (tb.reac.p[2] - u2v);
+            part[1] += m[0] * tb.reac.p[0];
+            part[2] += m[1] * tb.reac.p[0];
+            break;
+        }
+        case R_GRAY_SCOTT:       // params (F, k)
+            part[0] += m[0] * (1.0 - w[0]) - m[1] * w[1];
+            part[1] += -m[1] * w[1];
+            break;
+        case R_LINEAR_CUBIC:     // params K (row-major): d f_a / d K_ab = u_b
+            for (int a = 0; a < tb.S; ++a)
+                for (int b = 0; b < tb.S; ++b) part[a * tb.S + b] += m[a] * w[b];
+            break;
+        default:
+            break;
+        }
+        for (int r = 0; r < tb.S; ++r)
+            part[16 + r] += m[r] * laplacian<F64Acc, GEO>(tb, W + r * npts, idx, i, j, k, W[r * npts + idx]);
+    }
+    // block reduction (warp shuffles, then across the 8 warps)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < kSlots; ++q) {
+        double v = part[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kSlots) {
+        const int q = threadIdx.x;
+        if (q < np || (q >= 16 && q < 16 + tb.S)) {
+            double v = 0.0;
+            for (int w8 = 0; w8 < 8; ++w8) v += red[q][w8];
+            atomicAdd(&acc[q], v);
+        }
+    }
+}
+
+// acc[slot + s] += sum_p a[s][p] b[s][p] (wt ? wt[s][p] : 1) * scale for every species s.
+__global__ void __launch_bounds__(256) k_wdot(const double* __restrict__ a, const double* __restrict__ b,
+                                              const double* __restrict__ wt, long long npts, double scale,
+                                              double* __restrict__ acc) {
+    __shared__ double red[8];
+    const int s = blockIdx.y;
+    double v = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npts;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long q = s * npts + p;
+        v += a[q] * b[q] * (wt ? wt[q] : 1.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) t += red[w8];
+        atomicAdd(&acc[s], t * scale);
+    }
+}
+
+__global__ void k_scale(double* __restrict__ x, double a, long long n) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        x[p] *= a;
+}
+
+cudaError_t launch_adj_lambda(int geometry, const RhsTables<double>& tb, const double* W, const double* mu,
+                              double* lam, cudaStream_t st) {
+    long long blocks = (tb.npts + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    switch (geometry) {
+    case GEO_DISK: k_adj_lambda<GEO_DISK><<<(int)blocks, 256, 0, st>>>(tb, W, mu, lam); break;
+    case GEO_SPHERE: k_adj_lambda<GEO_SPHERE><<<(int)blocks, 256, 0, st>>>(tb, W, mu, lam); break;
+    case GEO_BALL: k_adj_lambda<GEO_BALL><<<(int)blocks, 256, 0, st>>>(tb, W, mu, lam); break;
+    default: k_adj_lambda<GEO_CYLINDER><<<(int)blocks, 256, 0, st>>>(tb, W, mu, lam); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_params(int geometry, const RhsTables<double>& tb, const double* W, const double* mu,
+                              double* acc, cudaStream_t st) {
+    long long blocks = (tb.npts + 255) / 256;
+    if (blocks > 152LL * 4) blocks = 152LL * 4;
+    switch (geometry) {
+    case GEO_DISK: k_adj_params<GEO_DISK><<<(int)blocks, 256, 0, st>>>(tb, W, mu, acc); break;
+    case GEO_SPHERE: k_adj_params<GEO_SPHERE><<<(int)blocks, 256, 0, st>>>(tb, W, mu, acc); break;
+    case GEO_BALL: k_adj_params<GEO_BALL><<<(int)blocks, 256, 0, st>>>(tb, W, mu, acc); break;
+    default: k_adj_params<GEO_CYLINDER><<<(int)blocks, 256, 0, st>>>(tb, W, mu, acc); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wdot(const double* a, const double* b, const double* wt, long long npts, int S, double scale,
+                        double* acc, cudaStream_t st) {
+    long long blocks = (npts + 255) / 256;
+    if (blocks > 152LL * 2) blocks = 152LL * 2;
+    k_wdot<<<dim3((unsigned)blocks, S), 256, 0, st>>>(a, b, wt, npts, scale, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double* x, double a, long long n, cudaStream_t st) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    k_scale<<<(int)blocks, 256, 0, st>>>(x, a, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rhs64(int geometry, const RhsTables<double>& tb, const double* W, double* F,
                          cudaStream_t st) {
     const long long total = tb.npts * tb.S;

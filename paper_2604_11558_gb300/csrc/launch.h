@@ -9,6 +9,14 @@ namespace sexpe {
 // FP64 SIMT path.
 cudaError_t launch_rhs64(int geometry, const RhsTables<double>& tb, const double* W, double* F, cudaStream_t st);
 cudaError_t launch_gemm64(const Gemm64& g, int n_species, cudaStream_t st);
+// Discrete adjoint (FP64).
+cudaError_t launch_adj_lambda(int geometry, const RhsTables<double>& tb, const double* W, const double* mu,
+                              double* lam, cudaStream_t st);
+cudaError_t launch_adj_params(int geometry, const RhsTables<double>& tb, const double* W, const double* mu,
+                              double* acc, cudaStream_t st);
+cudaError_t launch_wdot(const double* a, const double* b, const double* wt, long long npts, int S, double scale,
+                        double* acc, cudaStream_t st);
+cudaError_t launch_scale(double* x, double a, long long n, cudaStream_t st);
 
 // Split-TF32 tensor-core path.
 struct TcShape {

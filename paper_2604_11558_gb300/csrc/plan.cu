@@ -11,57 +11,9 @@
 #include <new>
 #include <vector>
 
-#include "host_setup.h"
-#include "internal.h"
-#include "launch.h"
-#include "sexpe.h"
+#include "plan_internal.h"
 
 using namespace sexpe;
-
-namespace {
-
-constexpr int kGraphSteps = 10;   // steps captured per CUDA graph replay
-
-struct Dir64 {
-    int mu = 0;
-    bool eigen = false;
-    const double* V = nullptr;      // eigen: V and V^{-1} (row-major n x n, shared by species)
-    const double* Vinv = nullptr;
-    const double* P = nullptr;      // plain: phi_1(tau d_s A) per species, S x n x n
-    const double* had = nullptr;    // eigen: Hadamard table per species, S x npts
-};
-
-}  // namespace
-
-struct sexpe_plan {
-    int geometry = 0, precision = 0, S = 0, ndim = 0;
-    int n[3] = {1, 1, 1};
-    long long npts = 0;
-    double tau = 0.0;
-    std::vector<double> d, params;
-    int reaction = 0;
-    Axis ax[3];
-    std::vector<void*> allocs;
-    size_t bytes = 0;
-    int* d_err = nullptr;
-    double* d_host_state = nullptr;   // staging buffer of sexpe_step_host
-    // FP64 path
-    RhsTables<double> rhs64{};
-    std::vector<Dir64> dirs64;
-    double* buf64[3] = {nullptr, nullptr, nullptr};
-    // split path
-    SplitTables tabs{};
-    TcShape sh3{}, shs{};
-    // per-kernel profiling (CUDA events on the launching stream)
-    std::vector<cudaEvent_t> prof_ev;
-    int prof_max_steps = 0, prof_steps = 0, prof_slot = 0;
-    bool profiling = false;
-    // graph cache
-    cudaGraphExec_t gexec = nullptr;
-    double* g_state = nullptr;
-    int kernels_per_step = 0;
-    double setup_ms = 0.0;
-};
 
 namespace {
 
@@ -540,6 +492,138 @@ sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species*
     return SEXPE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Discrete adjoint of the FP64 step (see include/sexpe.h, sexpe_adjoint).
+
+Mat transpose(const Mat& A) {
+    Mat T(A.n);
+    for (int r = 0; r < A.n; ++r)
+        for (int c = 0; c < A.n; ++c) T(c, r) = A(r, c);
+    return T;
+}
+
+constexpr int kAdjBuffers = 12;   // F, X1..X3, H0..H2, Y0, Y1, HA, Z, MU
+
+sexpe_status build_adjoint(sexpe_plan* p, cudaStream_t st) {
+    if (!p->adj.empty()) return SEXPE_OK;
+    // M^T: same off-diagonals, the full diagonal a_l in the rs slot
+    p->adj_diag = p->rhs64;
+    for (int m = 0; m < p->ndim; ++m) {
+        const double* dg = nullptr;
+        SX_TRY(upload(p, p->ax[m].diag, &dg, st));
+        p->adj_diag.ax[m].rs = dg;
+    }
+    std::vector<DirAdj> adj;
+    for (const Dir64& d : p->dirs64) {
+        const Axis& a = p->ax[d.mu - 1];
+        const int n = a.n;
+        DirAdj q;
+        if (d.eigen) {
+            const Eigen e = a.periodic ? theta_eigen(a) : tridiag_eigen(a);
+            SX_TRY(upload(p, transpose(e.V).a, &q.VT, st));
+            SX_TRY(upload(p, transpose(e.Vinv).a, &q.VinvT, st));
+            // weight Phi' / Phi^2 with Phi' = d Phi / d d_s = tau s lambda phi_1'(tau d_s s lambda)
+            std::vector<double> wt((size_t)p->S * p->npts);
+            for (int s = 0; s < p->S; ++s)
+                for (int k = 0; k < p->n[2]; ++k)
+                    for (int j = 0; j < p->n[1]; ++j)
+                        for (int i = 0; i < p->n[0]; ++i) {
+                            const int m = d.mu == 1 ? i : (d.mu == 2 ? j : k);
+                            const double sl = dir_scale(p, d.mu, i, j, k) * e.lam[m];
+                            const double x = p->tau * p->d[s] * sl;
+                            const double ph = phi1_scalar(x);
+                            wt[(size_t)s * p->npts + i + (size_t)p->n[0] * (j + (size_t)p->n[1] * k)] =
+                                p->tau * sl * dphi1_scalar(x) / (ph * ph);
+                        }
+            if (!all_finite(wt)) return SEXPE_ENUMERIC;
+            SX_TRY(upload(p, wt, &q.dhad, st));
+        } else {
+            const Mat A = a.dense();
+            const Eigen e = tridiag_eigen(a);
+            std::vector<double> PT((size_t)p->S * n * n), dP((size_t)p->S * n * n);
+            for (int s = 0; s < p->S; ++s) {
+                Mat X(n);
+                for (size_t t = 0; t < X.a.size(); ++t) X.a[t] = p->tau * p->d[s] * A.a[t];
+                const Mat Pt = transpose(phi1_pade(X));
+                std::memcpy(&PT[(size_t)s * n * n], Pt.a.data(), sizeof(double) * n * n);
+                // d phi_1(tau d A)/d d = V diag(tau lambda phi_1'(tau d lambda)) V^{-1}
+                for (int r = 0; r < n; ++r)
+                    for (int c = 0; c < n; ++c) {
+                        double acc = 0.0;
+                        for (int m = 0; m < n; ++m)
+                            acc += e.V(r, m) * p->tau * e.lam[m] * dphi1_scalar(p->tau * p->d[s] * e.lam[m]) *
+                                   e.Vinv(m, c);
+                        dP[(size_t)s * n * n + (size_t)r * n + c] = acc;
+                    }
+            }
+            if (!all_finite(PT) || !all_finite(dP)) return SEXPE_ENUMERIC;
+            SX_TRY(upload(p, PT, &q.PT, st));
+            SX_TRY(upload(p, dP, &q.dP, st));
+        }
+        adj.push_back(q);
+    }
+    SX_TRY(alloc_dev(p, (size_t)kAdjBuffers * p->S * p->npts, &p->adj_buf));
+    SX_TRY(alloc_dev(p, 32, &p->adj_red));
+    SX_CUDA(cudaStreamSynchronize(st));
+    p->adj = adj;
+    return SEXPE_OK;
+}
+
+// One adjoint step: lam <- lam_n from lam_{n+1} at the state W_n, accumulating
+// the parameter gradient in p->adj_red.
+sexpe_status adjoint_step(sexpe_plan* p, const double* Wn, double* lam, cudaStream_t st) {
+    const size_t E = (size_t)p->S * p->npts;
+    double* B = p->adj_buf;
+    double* X[4] = {B, B + E, B + 2 * E, B + 3 * E};     // X[q] = input of direction q (X[0] = F)
+    double* H[3] = {B + 4 * E, B + 5 * E, B + 6 * E};    // eigen: Phi o (V^{-1} X[q])
+    double* Y[2] = {B + 7 * E, B + 8 * E};
+    double* HA = B + 9 * E;
+    double* Z = B + 10 * E;
+    double* MU = B + 11 * E;
+    const int nd = (int)p->dirs64.size();
+    // forward chain at W_n, keeping every direction's input
+    SX_CUDA(launch_rhs64(p->geometry, p->rhs64, Wn, X[0], st));
+    for (int q = 0; q < nd; ++q) {
+        const Dir64& d = p->dirs64[q];
+        const long long nmu = p->n[d.mu - 1];
+        if (q + 1 == nd && !d.eigen) break;               // last plain direction: only its input is needed
+        if (d.eigen) {
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.Vinv, 0, X[q], H[q], d.had, nullptr), p->S, st));
+            if (q + 1 < nd)
+                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.V, 0, H[q], X[q + 1], nullptr, nullptr), p->S, st));
+        } else {
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.P, nmu * nmu, X[q], X[q + 1], nullptr, nullptr), p->S, st));
+        }
+    }
+    // transposed chain: phi_1(tau d M_1)^T first, with the d-derivative terms
+    double* acc_d = p->adj_red + 16;
+    const double* y = lam;
+    int yi = 0;
+    for (int q = nd - 1; q >= 0; --q) {
+        const Dir64& d = p->dirs64[q];
+        const DirAdj& a = p->adj[q];
+        const long long nmu = p->n[d.mu - 1];
+        double* yo = Y[yi];
+        if (d.eigen) {
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, a.VT, 0, y, HA, d.had, nullptr), p->S, st));
+            SX_CUDA(launch_wdot(HA, H[q], a.dhad, p->npts, p->S, p->tau, acc_d, st));
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, a.VinvT, 0, HA, yo, nullptr, nullptr), p->S, st));
+        } else {
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, a.dP, nmu * nmu, X[q], Z, nullptr, nullptr), p->S, st));
+            SX_CUDA(launch_wdot(Z, y, nullptr, p->npts, p->S, p->tau, acc_d, st));
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, a.PT, nmu * nmu, y, yo, nullptr, nullptr), p->S, st));
+        }
+        y = yo;
+        yi ^= 1;
+    }
+    // mu = tau P^T lam
+    SX_CUDA(cudaMemcpyAsync(MU, y, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    SX_CUDA(launch_scale(MU, p->tau, (long long)E, st));
+    SX_CUDA(launch_adj_params(p->geometry, p->rhs64, Wn, MU, p->adj_red, st));
+    SX_CUDA(launch_adj_lambda(p->geometry, p->adj_diag, Wn, MU, lam, st));
+    return SEXPE_OK;
+}
+
 }  // namespace
 
 namespace sexpe {
@@ -692,6 +776,63 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
     info->state_elems = (int64_t)p->S * p->npts;
     info->workspace_bytes = (int64_t)p->bytes;
     info->setup_ms = p->setup_ms;
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_step_checkpointed(sexpe_plan* p, double* state, int64_t n_steps, int32_t every,
+                                     double* checkpoints, void* stream) {
+    if (!p || !state || !checkpoints || n_steps < 0 || every < 1) return SEXPE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t E = (size_t)p->S * p->npts;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        if (k % every == 0)
+            SX_CUDA(cudaMemcpyAsync(checkpoints + (size_t)(k / every) * E, state, E * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+        SX_TRY(enqueue_step(p, state, st));
+    }
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_ckpt, int32_t every,
+                           const double* dL_dWT, double* dL_dW0, double* dL_dparams, void* stream) {
+    if (!p || !checkpoints || !dL_dWT || !dL_dW0 || n_ckpt < 1 || every < 1) return SEXPE_EINVAL;
+    if (p->precision != SEXPE_FP64) return SEXPE_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    try {
+        SX_TRY(build_adjoint(p, st));
+    } catch (const std::bad_alloc&) {
+        return SEXPE_ENOMEM;
+    } catch (...) {
+        return SEXPE_ENUMERIC;
+    }
+    const size_t E = (size_t)p->S * p->npts;
+    if (p->adj_seg_cap < every) {
+        double* seg = nullptr;
+        SX_TRY(alloc_dev(p, (size_t)every * E, &seg));
+        p->adj_seg = seg;
+        p->adj_seg_cap = every;
+    }
+    double* lam = dL_dW0;                      // the adjoint variable lives in the output buffer
+    if (lam != dL_dWT) SX_CUDA(cudaMemcpyAsync(lam, dL_dWT, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    SX_CUDA(cudaMemsetAsync(p->adj_red, 0, 32 * sizeof(double), st));
+    for (int c = n_ckpt - 1; c >= 0; --c) {
+        SX_CUDA(cudaMemcpyAsync(p->adj_seg, checkpoints + (size_t)c * E, E * sizeof(double), cudaMemcpyDeviceToDevice,
+                                st));
+        for (int j = 1; j < every; ++j) {
+            double* w = p->adj_seg + (size_t)j * E;
+            SX_CUDA(cudaMemcpyAsync(w, w - E, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            SX_TRY(enqueue_step(p, w, st));
+        }
+        for (int j = every - 1; j >= 0; --j) SX_TRY(adjoint_step(p, p->adj_seg + (size_t)j * E, lam, st));
+    }
+    if (dL_dparams) {
+        double red[32];
+        SX_CUDA(cudaMemcpyAsync(red, p->adj_red, sizeof(red), cudaMemcpyDeviceToHost, st));
+        SX_CUDA(cudaStreamSynchronize(st));
+        const int np = (int)p->params.size();
+        for (int q = 0; q < np; ++q) dL_dparams[q] = red[q];
+        for (int s = 0; s < p->S; ++s) dL_dparams[np + s] = red[16 + s];
+    }
     return SEXPE_OK;
 }
 

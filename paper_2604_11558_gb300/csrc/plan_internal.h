@@ -1,0 +1,72 @@
+// Plan object of libsexpe (internal; shared by plan.cu and adjoint.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "host_setup.h"
+#include "internal.h"
+#include "launch.h"
+#include "sexpe.h"
+
+namespace sexpe {
+
+constexpr int kGraphSteps = 10;   // steps captured per CUDA graph replay
+
+struct Dir64 {
+    int mu = 0;
+    bool eigen = false;
+    const double* V = nullptr;      // eigen: V and V^{-1} (row-major n x n, shared by species)
+    const double* Vinv = nullptr;
+    const double* P = nullptr;      // plain: phi_1(tau d_s A) per species, S x n x n
+    const double* had = nullptr;    // eigen: Hadamard table per species, S x npts
+};
+
+// Tables of the discrete adjoint of one direction (built on the first adjoint call).
+struct DirAdj {
+    const double* VT = nullptr;      // eigen: V^T      (transform of the adjoint variable)
+    const double* VinvT = nullptr;   // eigen: V^{-T}   (back-transform of the adjoint variable)
+    const double* dhad = nullptr;    // eigen: d Phi / d d_s = tau s lambda phi_1'(tau d_s s lambda), S x npts
+    const double* PT = nullptr;      // plain: phi_1(tau d_s A)^T per species, S x n x n
+    const double* dP = nullptr;      // plain: d phi_1(tau d_s A) / d d_s per species, S x n x n
+};
+
+}  // namespace sexpe
+
+struct sexpe_plan {
+    int geometry = 0, precision = 0, S = 0, ndim = 0;
+    int n[3] = {1, 1, 1};
+    long long npts = 0;
+    double tau = 0.0;
+    std::vector<double> d, params;
+    int reaction = 0;
+    sexpe::Axis ax[3];
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    int* d_err = nullptr;
+    double* d_host_state = nullptr;   // staging buffer of sexpe_step_host
+    // FP64 path
+    sexpe::RhsTables<double> rhs64{};
+    std::vector<sexpe::Dir64> dirs64;
+    double* buf64[3] = {nullptr, nullptr, nullptr};
+    // split path
+    sexpe::SplitTables tabs{};
+    sexpe::TcShape sh3{}, shs{};
+    // per-kernel profiling (CUDA events on the launching stream)
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_max_steps = 0, prof_steps = 0, prof_slot = 0;
+    bool profiling = false;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    double* g_state = nullptr;
+    // adjoint (FP64 plans; built on the first sexpe_adjoint call)
+    std::vector<sexpe::DirAdj> adj;
+    sexpe::RhsTables<double> adj_diag{};   // rs slot holds the full diagonal a_l for M^T
+    double* adj_buf = nullptr;              // work buffers, see adjoint.cu
+    double* adj_seg = nullptr;              // recomputed states of one checkpoint segment
+    int adj_seg_cap = 0;
+    double* adj_red = nullptr;              // device accumulators of the parameter gradient
+    int kernels_per_step = 0;
+    double setup_ms = 0.0;
+};
+

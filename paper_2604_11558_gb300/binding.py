@@ -216,6 +216,48 @@ class Plan:
             pass
 
 
+class BatchPlan(Plan):
+    """Many independent disks stepped together (wraps sexpe_batch_setup).
+
+    `workloads` is a list of workload dicts (disk, 2 species); the state is the
+    concatenation of the instances' states (see offsets())."""
+
+    def __init__(self, workloads, precision="split_tf32", stream=None):
+        L = lib()
+        count = len(workloads)
+        grids = (Grid * count)()
+        specs = (Species * count)()
+        self._keep = []
+        for q, w in enumerate(workloads):
+            grids[q] = _grid_struct(w["geometry"], w["n"], w.get("rho_star", 1.0))
+            d = np.ascontiguousarray(w["d"], dtype=np.float64)
+            prm = np.ascontiguousarray(w["params"] if len(w["params"]) else [0.0], dtype=np.float64)
+            self._keep += [d, prm]
+            specs[q] = Species(len(d), _dptr(d), REACTION[w["reaction"]], len(w["params"]), _dptr(prm))
+        h = _P()
+        st = _stream_ptr(stream) if stream is not None else 0
+        _check(L.sexpe_batch_setup(count, grids, specs, float(workloads[0]["tau"]), PRECISION[precision], st,
+                                   ctypes.byref(h)), "sexpe_batch_setup")
+        self.handle = h
+        self.geometry, self.n, self.S = "disk", None, 2
+        self._p_list = []
+        self.count = count
+
+    def offsets(self):
+        out = (ctypes.c_int64 * (self.count + 1))()
+        _check(lib().sexpe_state_offsets(self.handle, out), "sexpe_state_offsets")
+        return list(out)
+
+
+def batch_setup_status(workloads, precision="split_tf32"):
+    try:
+        p = BatchPlan(workloads, precision)
+    except SexpeError as e:
+        return e.status
+    p.close()
+    return 0
+
+
 def setup_status(geometry, n, d, reaction="none", params=(), tau=1e-3, precision="split_tf32", **kw):
     """Status code of sexpe_setup for the given arguments (the plan is destroyed again)."""
     try:

@@ -97,4 +97,27 @@ struct SplitTables {
     int* err;
 };
 
+// ---------------- batched independent disks (split-TF32) -------------------
+struct BatchInstance {
+    int n1, n2;                     // rho, theta points
+    long long w_off;                // element offset of the instance's state (species blocks of n1 n2)
+    Image QT, Q, P[2];              // theta transforms and phi_1(tau d_s A_rho) images
+    const float* had;               // Phi of the theta direction, [s][j'][i]
+    StencilAxis<float> ax_rho, ax_theta;
+    const float* Dr;                // rho_i^-2
+    float d[2];
+    ReactionParams<float> reac;
+};
+
+struct BatchTables {
+    const BatchInstance* inst;
+    const int2* items;              // (instance, species), longest first
+    int n_items;
+    int* counter;                   // work-list cursor, zeroed before every launch
+    const double* W_in;             // state before the step (all instances)
+    double* W_out;                  // state after the step
+    float tau;
+    int* err;
+};
+
 }  // namespace sexpe

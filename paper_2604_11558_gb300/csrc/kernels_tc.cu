@@ -108,7 +108,7 @@ __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& 
 // issues the three TF32 MMAs per K-step and commits them to the stage barrier.
 __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
     if ((threadIdx.x & 31) != 0) return;
-    uint32_t g = 0;
+    uint32_t g = P.g;
     for (int q = 0; q < n_gemms; ++q) {
         const GemmSpec& G = gs[q];
         const uint32_t data_bytes = (uint32_t)G.data_rows * kTileRowBytes;
@@ -148,6 +148,7 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
             mma_commit(&P.mma_bar[s]);
         }
     }
+    P.g = g;
 }
 
 // TMA side: one lane of the extra warp walks the K-chunks of every product of
@@ -155,7 +156,7 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
 // as the stage is free, up to kStages chunks ahead of the MMAs.
 __device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
     if ((threadIdx.x & 31) != 0) return;
-    uint32_t g = 0;
+    uint32_t g = P.g;
     for (int q = 0; q < n_gemms; ++q) {
         const GemmSpec& G = gs[q];
         const uint32_t mat_bytes = (uint32_t)G.mat.rows_pad * kTileRowBytes;
@@ -168,6 +169,7 @@ __device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
             tma_bulk_g2s(mhi, G.mat.ptr + (long long)c * G.mat.chunk_floats, 2 * mat_bytes, &P.tma_bar[s]);
         }
     }
+    P.g = g;
 }
 
 // Kernel prologue/epilogue: carve shared memory, init barriers, allocate TMEM.
@@ -427,27 +429,75 @@ __global__ void __launch_bounds__(kBlock, 1)
 // slab pass: one k-slab (n2 x n1 matrix, rho contiguous) of one species.
 struct SlabJob {
     int n1, n2;
-    const float* Y;       // F after the earlier directions, slab base
-    double* W;            // state slab base (updated)
+    const float* Y;       // F after the earlier directions, slab base (null: F from the state)
+    const double* Win;    // state slab base read by the update (== W for an in-place step)
+    double* W;            // state slab base written by the update
     Image QT, Q, P;
     const float* had;     // Phi of the theta direction for this slab, [j'][i]
     float tau_f;
 };
 
-// The three products of a slab and their tensor-memory columns: G1 [0, n2p),
-// G2 [n2p, n2p + m2 n1p), G3 reuses [0, m2 n1p) when that does not reach G2.
-__device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, GemmSpec* gs, uint32_t* cols) {
+// The three products of a slab and their tensor-memory columns within an
+// allocation of T columns: G1 [0, n2p); G2 [T - m2 n1p, T); G3 [0, m2 n1p),
+// reusing G1's columns, which are dead once G2's operands are written.
+// Valid when n2p + m2 n1p <= T and 2 m2 n1p <= T (slab_tmem_cols).
+__device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, uint32_t T, GemmSpec* gs,
+                                           uint32_t* cols) {
     const int n1p = (J.n1 + 15) & ~15, n2p = (J.n2 + 15) & ~15, m2 = (J.n2 + 127) / 128;
     cols[0] = 0;
-    cols[1] = (uint32_t)n2p;
-    cols[2] = (m2 * n1p <= n2p) ? 0u : (uint32_t)(n2p + m2 * n1p);
+    cols[1] = T - (uint32_t)(m2 * n1p);
+    cols[2] = 0;
     gs[0] = GemmSpec{J.QT, 0, kRows, 1, n2p, n2p / kKC, tmem + cols[0]};
     gs[1] = GemmSpec{J.Q, 1, n1p, m2, n1p, n2p / kKC, tmem + cols[1]};
     gs[2] = GemmSpec{J.P, 0, kRows * m2, m2, n1p, n1p / kKC, tmem + cols[2]};
 }
 
+// F of one disk species at (i, j0 + q), q < 8, from FP64-accurate differences of
+// the state (both species of the instance at `inst_base`), 0 outside the grid.
+__device__ __forceinline__ void disk_F8(const BatchInstance& I, const double* inst_base, int s, int i, int j0,
+                                        float* v) {
+    const int n1 = I.n1, n2 = I.n2;
+    const long long n12 = (long long)n1 * n2;
+    const double* Ws = inst_base + s * n12;
+    const double* Wo = inst_base + (1 - s) * n12;
+    const bool iv = i < n1;
+    const int ii = iv ? i : 0;
+    double c[8], m1[8], p1[8], m2[8], p2[8], o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int j = j0 + q;
+        const int jj = j < n2 ? j : 0;
+        const long long idx = (long long)jj * n1 + ii;
+        c[q] = Ws[idx];
+        m1[q] = ii > 0 ? Ws[idx - 1] : 0.0;
+        p1[q] = ii < n1 - 1 ? Ws[idx + 1] : 0.0;
+        m2[q] = Ws[(long long)(jj > 0 ? jj - 1 : n2 - 1) * n1 + ii];
+        p2[q] = Ws[(long long)(jj < n2 - 1 ? jj + 1 : 0) * n1 + ii];
+        o[q] = Wo[idx];
+    }
+    const float lo1 = I.ax_rho.lower[ii], up1 = I.ax_rho.upper[ii], rs1 = I.ax_rho.rs[ii], dr = I.Dr[ii];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int j = j0 + q;
+        const int jj = j < n2 ? j : 0;
+        const float2 cc = split_f64(c[q]);
+        float t0 = rs1 * (cc.x + cc.y);
+        if (ii > 0) t0 += lo1 * sdiff(split_f64(m1[q]), cc);
+        if (ii < n1 - 1) t0 += up1 * sdiff(split_f64(p1[q]), cc);
+        float t1 = I.ax_theta.rs[jj] * (cc.x + cc.y) + I.ax_theta.lower[jj] * sdiff(split_f64(m2[q]), cc) +
+                   I.ax_theta.upper[jj] * sdiff(split_f64(p2[q]), cc);
+        const float2 oo = split_f64(o[q]);
+        float w[kMaxSpecies] = {0.f, 0.f, 0.f, 0.f};
+        w[s] = cc.x + cc.y;
+        w[1 - s] = oo.x + oo.y;
+        const float f = I.d[s] * (t0 + dr * t1) + reaction<float>(I.reac, w, s);
+        v[q] = (iv && j < n2) ? f : 0.f;
+    }
+}
+
 __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* gs, const uint32_t* cols, Pipe& P,
-                                             uint32_t tmem, char* epi) {
+                                             uint32_t tmem, char* epi, const BatchInstance* BI = nullptr,
+                                             const double* inst_base = nullptr, int species = 0) {
     const int tid = threadIdx.x;
     const int r = tid & (kRows - 1), h = tid >> 7;
     const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
@@ -464,14 +514,22 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
             nxt[q] = (r < n1 && j < n2) ? J.Y[j * n1 + r] : 0.f;
         }
     };
-    load_y(0);
-    run_gemm(P, gs[0], [&](int c, char* hi, char* lo) {
-        float v[8];
+    if (BI) {
+        run_gemm(P, gs[0], [&](int c, char* hi, char* lo) {
+            float v[8];
+            disk_F8(*BI, inst_base, species, r, c * 16 + h * 8, v);
+            store_row8(hi, lo, r, h, v);
+        });
+    } else {
+        load_y(0);
+        run_gemm(P, gs[0], [&](int c, char* hi, char* lo) {
+            float v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = nxt[q];
-        if (c + 1 < gs[0].k_chunks) load_y(c + 1);
-        store_row8(hi, lo, r, h, v);
-    });
+            for (int q = 0; q < 8; ++q) v[q] = nxt[q];
+            if (c + 1 < gs[0].k_chunks) load_y(c + 1);
+            store_row8(hi, lo, r, h, v);
+        });
+    }
     // G2: Z^T[j][i] = sum_j' Q[j][j'] (Phi o X)[i][j']   (x_2 Q_theta), data in B, rows j
     auto load_h = [&](int c) {
 #pragma unroll
@@ -521,6 +579,7 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
         const int rows = min(kRows, n2 - mt * kRows);
         const int count = rows * n1;
         double* Wt = J.W + (long long)mt * kRows * n1;
+        const double* Wi = J.Win + (long long)mt * kRows * n1;
         // increment rounded to FP32, widened exactly by integer operations: one FP64 add per
         // point; eight independent read-modify-writes in flight per thread
         for (int f0 = tid; f0 < count; f0 += kThreads * 8) {
@@ -528,7 +587,7 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int f = f0 + u * kThreads;
-                w[u] = f < count ? Wt[f] : 0.0;
+                w[u] = f < count ? Wi[f] : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -554,6 +613,7 @@ __global__ void __launch_bounds__(kBlock, 1)
     J.n2 = T.n2;
     J.Y = T.Y + (long long)s * T.npts + k * n12;
     J.W = T.state_upd + (long long)s * T.npts + k * n12;
+    J.Win = J.W;
     J.QT = T.QT;
     J.Q = T.Q;
     J.P = T.P[s];
@@ -561,10 +621,53 @@ __global__ void __launch_bounds__(kBlock, 1)
     J.tau_f = T.tau;
     GemmSpec gs[3];
     uint32_t cols[3];
-    slab_specs(J, R.tmem, gs, cols);
+    slab_specs(J, R.tmem, tmem_cols, gs, cols);
     if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
     else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
     else slab_compute(J, gs, cols, R.P, R.tmem, R.P.stages);
+    cta_end(R, tmem_cols);
+}
+
+// ------------------------------------------------------------------------------
+// Batched disks: a persistent CTA per SM takes (instance, species) items from the
+// LPT-ordered work list and runs the whole disk chain of eq. ee_disk for it --
+// F from the previous state, x_2 Q_theta^T, Hadamard, x_2 Q_theta, x_1
+// phi_1(tau d A_rho) -- writing the updated species into the other state buffer.
+__global__ void __launch_bounds__(kBlock, 1)
+    k_tc_batch(BatchTables B, uint32_t stage_bytes, uint32_t tmem_cols) {
+    extern __shared__ char smem_raw[];
+    __shared__ int s_item;
+    CtaRes R = cta_begin(smem_raw, stage_bytes, tmem_cols, B.err);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(B.counter, 1);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= B.n_items) break;
+        const int2 item = B.items[it];
+        const BatchInstance& I = B.inst[item.x];
+        const int s = item.y;
+        const long long n12 = (long long)I.n1 * I.n2;
+        SlabJob J;
+        J.n1 = I.n1;
+        J.n2 = I.n2;
+        J.Y = nullptr;
+        J.Win = B.W_in + I.w_off + s * n12;
+        J.W = B.W_out + I.w_off + s * n12;
+        J.QT = I.QT;
+        J.Q = I.Q;
+        J.P = I.P[s];
+        J.had = I.had + s * n12;
+        J.tau_f = B.tau;
+        GemmSpec gs[3];
+        uint32_t cols[3];
+        slab_specs(J, R.tmem, tmem_cols, gs, cols);
+        if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
+        else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
+        else slab_compute(J, gs, cols, R.P, R.tmem, R.P.stages, &I, B.W_in + I.w_off, s);
+    }
     cta_end(R, tmem_cols);
 }
 
@@ -590,6 +693,14 @@ TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3) {
     return sh;
 }
 
+// Tensor-memory columns of a slab (see slab_specs): a power of two holding G1
+// and G2 side by side and G2 and G3 side by side.
+uint32_t slab_tmem_cols(int n1, int n2) {
+    const uint32_t n1p = round_up(n1, 16), n2p = round_up(n2, 16), m2 = (n2 + 127) / 128;
+    const uint32_t need = std::max(n2p + m2 * n1p, 2 * m2 * n1p);
+    return pow2_cols(need);
+}
+
 TcShape tc_slab_shape(int n1, int n2) {
     TcShape sh{};
     const uint32_t n1p = round_up(n1, 16), n2p = round_up(n2, 16), m2 = (n2 + 127) / 128;
@@ -605,10 +716,7 @@ TcShape tc_slab_shape(int n1, int n2) {
         sh.stage_bytes = round_up((epi + kStages - 1) / kStages, 1024);
         body = kStages * sh.stage_bytes;
     }
-    const uint32_t c3 = (m2 * n1p <= n2p) ? 0 : n2p + m2 * n1p;
-    uint32_t cols = n2p + m2 * n1p;
-    if (c3 + m2 * n1p > cols) cols = c3 + m2 * n1p;
-    sh.tmem_cols = pow2_cols(cols);
+    sh.tmem_cols = slab_tmem_cols(n1, n2);
     sh.smem_bytes = 1024 + kHeaderBytes + body;
     return sh;
 }
@@ -679,6 +787,23 @@ static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)T.S * (TS::TK + 2 * TS::KH) * (tj + 2) * T.n1;
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + TS::TK - 1) / TS::TK, 1);
     k_rhs_tile<GEO><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj);
+    return cudaGetLastError();
+}
+
+TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols) {
+    TcShape sh = tc_slab_shape(max_n1, max_n2);
+    sh.tmem_cols = std::max(sh.tmem_cols, tmem_cols);
+    return sh;
+}
+
+cudaError_t tc_prepare_batch(uint32_t smem) {
+    return cudaFuncSetAttribute(k_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(B.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_tc_batch<<<152, kBlock, sh.smem_bytes, st>>>(B, sh.stage_bytes, sh.tmem_cols);
     return cudaGetLastError();
 }
 

@@ -26,10 +26,15 @@ struct TcShape {
 };
 TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3);
 TcShape tc_slab_shape(int n1, int n2);
+uint32_t slab_tmem_cols(int n1, int n2);
 // Raise the kernels' dynamic shared-memory limit (once, outside stream capture).
 cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab);
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st);
+// Batched disks: one persistent launch per step.
+TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols);
+cudaError_t tc_prepare_batch(uint32_t smem);
+cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_t st);
 
 }  // namespace sexpe

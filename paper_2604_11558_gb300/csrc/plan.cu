@@ -3,6 +3,7 @@
 // error reporting.  See include/sexpe.h for the contract of every entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdint>
@@ -310,6 +311,7 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     }
     p->shs = tc_slab_shape(n1, n2);
     if (p->shs.smem_bytes > 227 * 1024 || p->sh3.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
+    if (p->shs.tmem_cols > 512 || (p->ndim == 3 && p->sh3.tmem_cols > 512)) return SEXPE_EUNSUPPORTED;
     SX_CUDA(tc_prepare(p->ndim == 3 ? p->sh3.smem_bytes : 0, p->shs.smem_bytes));
     p->kernels_per_step = p->ndim == 3 ? 3 : 2;
     return SEXPE_OK;
@@ -367,6 +369,15 @@ sexpe_status enqueue_step(sexpe_plan* p, double* state, cudaStream_t st) {
 }
 
 sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
+    if (p->batch) {
+        BatchTables B = p->btab;
+        B.W_in = p->bparity ? p->bstate : state;
+        B.W_out = p->bparity ? state : p->bstate;
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_tc_batch(B, p->bsh, st));
+        p->bparity ^= 1;
+        return SEXPE_OK;
+    }
     if (p->precision == SEXPE_FP64) {
         SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_rhs64(p->geometry, p->rhs64, state, p->buf64[0], st));
@@ -489,6 +500,159 @@ sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species*
     if (precision == SEXPE_FP64) SX_TRY(build_fp64(p, st));
     else SX_TRY(build_split(p, st));
     SX_CUDA(cudaStreamSynchronize(st));   // host vectors of the uploads go out of scope
+    return SEXPE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched independent disks.
+
+sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, const sexpe_species* species,
+                         double tau, cudaStream_t st) {
+    p->batch = true;
+    p->n_instances = count;
+    p->geometry = SEXPE_DISK;
+    p->precision = SEXPE_SPLIT_TF32;
+    p->S = 2;
+    p->ndim = 2;
+    p->tau = tau;
+    // one float pool for every per-instance table, uploaded once
+    std::vector<float> pool;
+    auto put = [&](const std::vector<float>& v) {
+        while (pool.size() % 64) pool.push_back(0.f);            // 256-byte alignment of every table
+        const size_t off = pool.size();
+        pool.insert(pool.end(), v.begin(), v.end());
+        return off;
+    };
+    struct Offs { size_t qt, q, p0, p1, had, rl, ru, rr, tl, tu, tr, dr; };
+    std::vector<Offs> offs(count);
+    std::vector<BatchInstance> inst(count);
+    p->inst_off.assign(count + 1, 0);
+    int max_n1 = 0, max_n2 = 0;
+    uint32_t tmem_cols = 32;
+    for (int q = 0; q < count; ++q) {
+        const int n1 = grids[q].n[0], n2 = grids[q].n[1];
+        max_n1 = std::max(max_n1, n1);
+        max_n2 = std::max(max_n2, n2);
+        tmem_cols = std::max(tmem_cols, slab_tmem_cols(n1, n2));
+        const Axis ar = build_axis(AX_RHO2, n1, grids[q].rho_star);
+        const Axis at = build_axis(AX_THETA, n2, 0.0);
+        const Eigen th = theta_eigen(at);
+        const int n1p = rup16(n1), n2p = rup16(n2), m2 = (n2 + 127) / 128;
+        Offs& o = offs[q];
+        o.qt = put(make_image(n2, n2, n2p, n2p, [&](int r, int k) { return th.V(k, r); }));
+        o.q = put(make_image(n2, n2, 128 * m2, n2p, [&](int r, int k) { return th.V(r, k); }));
+        const double* dsp = species[q].d_host;
+        const Mat A = ar.dense();
+        size_t pofs[2];
+        for (int sp = 0; sp < 2; ++sp) {
+            Mat X(n1);
+            for (size_t t = 0; t < X.a.size(); ++t) X.a[t] = tau * dsp[sp] * A.a[t];
+            const Mat Ps = phi1_pade(X);
+            if (!all_finite(Ps.a)) return SEXPE_ENUMERIC;
+            pofs[sp] = put(make_image(n1, n1, n1p, n1p, [&](int r, int k) { return Ps(r, k); }));
+        }
+        o.p0 = pofs[0];
+        o.p1 = pofs[1];
+        std::vector<float> had((size_t)2 * n1 * n2);
+        for (int sp = 0; sp < 2; ++sp)
+            for (int jp = 0; jp < n2; ++jp)
+                for (int i = 0; i < n1; ++i)
+                    had[(size_t)sp * n1 * n2 + (size_t)jp * n1 + i] =
+                        (float)phi1_scalar(tau * dsp[sp] * th.lam[jp] / (ar.pts[i] * ar.pts[i]));
+        o.had = put(had);
+        auto axis_f = [&](const Axis& a, size_t& lo, size_t& up, size_t& rs) {
+            std::vector<float> vl(a.n), vu(a.n), vr(a.n);
+            for (int r = 0; r < a.n; ++r) {
+                vl[r] = (float)a.lower[r];
+                vu[r] = (float)a.upper[r];
+                vr[r] = 0.f;   // every row of A_rho2 and A_theta sums to zero
+            }
+            lo = put(vl);
+            up = put(vu);
+            rs = put(vr);
+        };
+        axis_f(ar, o.rl, o.ru, o.rr);
+        axis_f(at, o.tl, o.tu, o.tr);
+        std::vector<float> dr(n1);
+        for (int i = 0; i < n1; ++i) dr[i] = (float)(1.0 / (ar.pts[i] * ar.pts[i]));
+        o.dr = put(dr);
+        BatchInstance& I = inst[q];
+        I.n1 = n1;
+        I.n2 = n2;
+        I.w_off = p->inst_off[q];
+        I.d[0] = (float)dsp[0];
+        I.d[1] = (float)dsp[1];
+        I.reac.kind = species[q].reaction;
+        I.reac.S = 2;
+        for (int t = 0; t < 16; ++t)
+            I.reac.p[t] = t < species[q].n_params ? (float)species[q].params_host[t] : 0.f;
+        I.QT = Image{nullptr, n2p, n2p / kKC, 2LL * n2p * kKC};
+        I.Q = Image{nullptr, 128 * m2, n2p / kKC, 2LL * 128 * m2 * kKC};
+        I.P[0] = Image{nullptr, n1p, n1p / kKC, 2LL * n1p * kKC};
+        I.P[1] = I.P[0];
+        I.ax_rho.n = n1;
+        I.ax_rho.periodic = 0;
+        I.ax_theta.n = n2;
+        I.ax_theta.periodic = 1;
+        p->inst_off[q + 1] = p->inst_off[q] + 2LL * n1 * n2;
+    }
+    const float* base = nullptr;
+    SX_TRY(upload(p, pool, &base, st));
+    for (int q = 0; q < count; ++q) {
+        BatchInstance& I = inst[q];
+        const Offs& o = offs[q];
+        I.QT.ptr = base + o.qt;
+        I.Q.ptr = base + o.q;
+        I.P[0].ptr = base + o.p0;
+        I.P[1].ptr = base + o.p1;
+        I.had = base + o.had;
+        I.ax_rho.lower = base + o.rl;
+        I.ax_rho.upper = base + o.ru;
+        I.ax_rho.rs = base + o.rr;
+        I.ax_theta.lower = base + o.tl;
+        I.ax_theta.upper = base + o.tu;
+        I.ax_theta.rs = base + o.tr;
+        I.Dr = base + o.dr;
+    }
+    // LPT work list: (instance, species) items, most tensor work first
+    std::vector<int2> items;
+    for (int q = 0; q < count; ++q)
+        for (int sp = 0; sp < 2; ++sp) items.push_back(make_int2(q, sp));
+    std::stable_sort(items.begin(), items.end(), [&](const int2& a, const int2& b) {
+        auto cost = [&](const int2& x) {
+            const double n1 = inst[x.x].n1, n2 = inst[x.x].n2;
+            return n1 * n2 * (2.0 * n2 + n1);
+        };
+        return cost(a) > cost(b);
+    });
+    // the instance descriptors go up as raw bytes
+    std::vector<char> ibytes(sizeof(BatchInstance) * count);
+    std::memcpy(ibytes.data(), inst.data(), ibytes.size());
+    const char* dinst = nullptr;
+    SX_TRY(upload(p, ibytes, &dinst, st));
+    const int2* ditems = nullptr;
+    SX_TRY(upload(p, items, &ditems, st));
+    SX_TRY(alloc_dev(p, 4, &p->d_err));
+    SX_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st));
+    int* counter = nullptr;
+    SX_TRY(alloc_dev(p, 4, &counter));
+    SX_TRY(alloc_dev(p, (size_t)p->inst_off.back(), &p->bstate));
+    SX_TRY(alloc_dev(p, (size_t)p->inst_off.back(), &p->d_host_state));
+    p->btab.inst = reinterpret_cast<const BatchInstance*>(dinst);
+    p->btab.items = ditems;
+    p->btab.n_items = (int)items.size();
+    p->btab.counter = counter;
+    p->btab.tau = (float)tau;
+    p->btab.err = p->d_err;
+    p->bsh = tc_batch_shape(max_n1, max_n2, tmem_cols);
+    if (p->bsh.tmem_cols > 512) return SEXPE_EUNSUPPORTED;
+    if (p->bsh.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
+    SX_CUDA(tc_prepare_batch(p->bsh.smem_bytes));
+    p->npts = p->inst_off.back() / 2;
+    p->n[0] = max_n1;
+    p->n[1] = max_n2;
+    p->kernels_per_step = 1;
+    SX_CUDA(cudaStreamSynchronize(st));
     return SEXPE_OK;
 }
 
@@ -634,7 +798,7 @@ namespace sexpe {
 sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float* Y, long long y_floats,
                                              cudaStream_t st) {
     if (!p || !state || !Y) return SEXPE_EINVAL;
-    if (p->precision != SEXPE_SPLIT_TF32) return SEXPE_EINVAL;
+    if (p->precision != SEXPE_SPLIT_TF32 || p->batch) return SEXPE_EINVAL;
     if ((long long)p->S * p->npts > y_floats) return SEXPE_EINVAL;
     SplitTables T = p->tabs;
     T.state = state;
@@ -691,13 +855,44 @@ sexpe_status sexpe_setup(const sexpe_grid* grid, const sexpe_species* species, d
 
 sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sexpe_species* species, double tau,
                                int32_t precision, void* stream, sexpe_plan** out) {
-    (void)count; (void)grids; (void)species; (void)tau; (void)precision; (void)stream;
-    if (out) *out = nullptr;
-    return SEXPE_EUNSUPPORTED;
+    if (!out) return SEXPE_EINVAL;
+    *out = nullptr;
+    if (count < 1 || count > 65536 || !grids || !species) return SEXPE_EINVAL;
+    for (int q = 0; q < count; ++q) {
+        const sexpe_status v = validate(&grids[q], &species[q], tau, precision);
+        if (v != SEXPE_OK) return v;
+        if (grids[q].geometry != SEXPE_DISK || species[q].n_species != 2) return SEXPE_EINVAL;
+        if (species[q].reaction == SEXPE_LINEAR_CUBIC) return SEXPE_EUNSUPPORTED;
+        if (grids[q].n[0] > 128 || grids[q].n[1] > 256) return SEXPE_EUNSUPPORTED;
+    }
+    if (precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
+    auto t0 = std::chrono::steady_clock::now();
+    sexpe_plan* p = new (std::nothrow) sexpe_plan();
+    if (!p) return SEXPE_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    sexpe_status status = SEXPE_OK;
+    try {
+        status = build_batch(p, count, grids, species, tau, st);
+    } catch (const std::bad_alloc&) {
+        status = SEXPE_ENOMEM;
+    } catch (...) {
+        status = SEXPE_ENUMERIC;
+    }
+    if (status != SEXPE_OK) {
+        free_plan(p);
+        return status;
+    }
+    p->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SEXPE_OK;
 }
 
 sexpe_status sexpe_state_offsets(const sexpe_plan* plan, int64_t* offsets_host) {
     if (!plan || !offsets_host) return SEXPE_EINVAL;
+    if (plan->batch) {
+        for (size_t q = 0; q < plan->inst_off.size(); ++q) offsets_host[q] = plan->inst_off[q];
+        return SEXPE_OK;
+    }
     offsets_host[0] = 0;
     offsets_host[1] = (int64_t)plan->S * plan->npts;
     return SEXPE_OK;
@@ -708,6 +903,7 @@ sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* str
     if (((uintptr_t)state & 7u) != 0) return SEXPE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int64_t done = 0;
+    p->bparity = 0;
     if (n_steps >= kGraphSteps && !p->profiling) {
         if (!p->gexec || p->g_state != state) {
             if (p->gexec) {
@@ -737,13 +933,18 @@ sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* str
         for (; done + kGraphSteps <= n_steps; done += kGraphSteps) SX_CUDA(cudaGraphLaunch(p->gexec, st));
     }
     for (; done < n_steps; ++done) SX_TRY(enqueue_step(p, state, st));
+    if (p->batch && p->bparity) {   // odd number of ping-pong steps: the result is in the plan's buffer
+        SX_CUDA(cudaMemcpyAsync(state, p->bstate, sizeof(double) * (size_t)p->inst_off.back(),
+                                cudaMemcpyDeviceToDevice, st));
+        p->bparity = 0;
+    }
     return SEXPE_OK;
 }
 
 sexpe_status sexpe_step_host(sexpe_plan* p, double* state_host, int64_t n_steps, void* stream) {
     if (!p || !state_host || n_steps < 0) return SEXPE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = sizeof(double) * (size_t)p->S * p->npts;
+    const size_t bytes = sizeof(double) * (size_t)(p->batch ? p->inst_off.back() : (long long)p->S * p->npts);
     SX_CUDA(cudaMemcpyAsync(p->d_host_state, state_host, bytes, cudaMemcpyHostToDevice, st));
     SX_TRY(sexpe_step(p, p->d_host_state, n_steps, stream));
     SX_CUDA(cudaMemcpyAsync(state_host, p->d_host_state, bytes, cudaMemcpyDeviceToHost, st));
@@ -770,10 +971,10 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
     info->n_species = p->S;
     info->ndim = p->ndim;
     for (int m = 0; m < 3; ++m) info->n[m] = p->n[m];
-    info->n_instances = 1;
+    info->n_instances = p->n_instances;
     info->kernels_per_step = p->kernels_per_step;
     info->npts = p->npts;
-    info->state_elems = (int64_t)p->S * p->npts;
+    info->state_elems = p->batch ? (int64_t)p->inst_off.back() : (int64_t)p->S * p->npts;
     info->workspace_bytes = (int64_t)p->bytes;
     info->setup_ms = p->setup_ms;
     return SEXPE_OK;

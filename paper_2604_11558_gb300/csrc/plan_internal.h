@@ -66,6 +66,14 @@ struct sexpe_plan {
     double* adj_seg = nullptr;              // recomputed states of one checkpoint segment
     int adj_seg_cap = 0;
     double* adj_red = nullptr;              // device accumulators of the parameter gradient
+    // batched independent disks (sexpe_batch_setup)
+    bool batch = false;
+    int n_instances = 1;
+    std::vector<long long> inst_off;          // element offsets of the instances' states (count + 1)
+    sexpe::BatchTables btab{};
+    sexpe::TcShape bsh{};
+    double* bstate = nullptr;                 // the other state buffer of the ping-pong
+    int bparity = 0;                          // steps enqueued in the current sexpe_step call, mod 2
     int kernels_per_step = 0;
     double setup_ms = 0.0;
 };

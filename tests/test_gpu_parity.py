@@ -67,6 +67,7 @@ SPLIT_CASES = [
     ("disk", disk((37, 45))),
     ("disk_two_theta_tiles", disk((40, 200))),
     ("disk_min", disk((3, 3))),
+    ("disk_rho128_theta136", disk((128, 136))),
     ("ball", ball((20, 33, 40))),
     ("ball_rho128", ball((128, 16, 16), steps=3)),
     ("ball_phi256", ball((8, 12, 256), steps=3)),

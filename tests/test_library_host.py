@@ -101,3 +101,15 @@ def test_library_eigenbasis(binding, axis):
         assert np.max(np.abs(np.sort(lam) - ref)) < 1e-10 * scale
     if axis == "theta":      # orthogonal real Fourier basis: V^{-1} = V^T
         assert np.allclose(Vinv, V.T, atol=1e-14)
+
+
+def test_batch_setup_rejects_invalid(binding):
+    from paper_2604_11558_gb300 import workloads as wl
+    good = wl.schnakenberg_disk(n=(10, 12), steps=1)
+    ball = wl.gray_scott_ball(n=(5, 6, 7), steps=1)
+    assert binding.batch_setup_status([good, ball]) == 1                  # not a disk
+    bad = dict(good, d=[1.0, -1.0])
+    assert binding.batch_setup_status([good, bad]) == 1                   # negative diffusion
+    big = wl.schnakenberg_disk(n=(10, 300), steps=1)
+    assert binding.batch_setup_status([big]) == 5                         # theta > 256 unsupported
+    assert binding.batch_setup_status([good], precision="fp64") == 5      # batched FP64 not built

@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the cylinder, batched-disk and sphere-adjoint measurements")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only setup + 3 split steps (for an ncu capture of the step kernels)")
     return ap.parse_args()
@@ -332,6 +334,11 @@ def main():
         "clocks": clk,
         "setup_ms": info["setup_ms"],
     }
+    if not args.no_extras:
+        try:
+            line["other_workloads"] = measure_extras(flush)
+        except Exception as exc:          # the headline line must survive a failing extra
+            line["other_workloads"] = {"error": repr(exc)[:300]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = time_oracle(1, 2, 200, 15.0)
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
@@ -341,6 +348,61 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_extras(flush):
+    """The other workloads: cylinder 64x128x128 (3 species), 256 uneven disks (one persistent
+    launch per step), and the sphere 256x512 adjoint cost relative to its forward."""
+    import numpy as np
+    import torch
+    from paper_2604_11558_gb300 import binding
+    from paper_2604_11558_gb300 import workloads as wl
+    out = {}
+    # cylinder, split and FP64
+    w = wl.linear_cubic_cylinder(steps=1)
+    dof = len(w["d"]) * int(np.prod(w["n"]))
+    res = {}
+    for prec, steps in (("split_tf32", 50), ("fp64", 5)):
+        plan = binding.Plan.from_workload(w, precision=prec)
+        x = torch.from_numpy(w["W0"]).cuda()
+        plan.step(x, 2)
+        ms, _ = timed_steps(plan, x, steps, flush)
+        res[prec] = {"ms_per_step": sum(ms) / steps, "value": dof * steps / (sum(ms) / 1e3)}
+        plan.close()
+    out["cylinder_64x128x128_3species"] = {"unit": UNIT, "dof": dof, **res}
+    # batched disks
+    ws = wl.batched_disks(steps=1)
+    dof = sum(2 * wq["n"][0] * wq["n"][1] for wq in ws)
+    plan = binding.BatchPlan(ws)
+    x = torch.from_numpy(np.concatenate([wq["W0"].ravel() for wq in ws])).cuda()
+    plan.step(x, 4)
+    steps = 100
+    ms, kms = timed_steps(plan, x, steps, flush, profile=True)
+    out["batched_disks_256"] = {"unit": UNIT, "dof": dof, "ms_per_step": sum(ms) / steps,
+                                "value": dof * steps / (sum(ms) / 1e3), "launches_per_step": 1,
+                                "kernel_ms": kms, "l2": "flushed before every timed step"}
+    plan.close()
+    # sphere adjoint vs forward (FP64), full 256x512 workload: 1000 steps, checkpoints every 50
+    w = wl.schnakenberg_sphere()
+    plan = binding.Plan.from_workload(w, precision="fp64")
+    x = torch.from_numpy(w["W0"]).cuda()
+    every, steps = 50, w["steps"]
+    ck = torch.empty((steps // every,) + tuple(x.shape), dtype=torch.float64, device="cuda")
+    g = torch.ones_like(x)
+    plan.adjoint(ck[:1].copy_(x.unsqueeze(0)), 1, 1, g, torch.empty_like(g))   # builds the adjoint tables
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    plan.step_checkpointed(x, steps, every, ck)
+    e1.record()
+    plan.adjoint(ck, steps // every, every, g, torch.empty_like(g))
+    e2.record()
+    torch.cuda.synchronize()
+    fwd, adj = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    out["sphere_256x512_adjoint_fp64"] = {"forward_ms": fwd, "adjoint_ms": adj, "adjoint_over_forward": adj / fwd,
+                                          "steps": steps, "checkpoint_every": every}
+    plan.close()
+    return out
 
 
 def kernel_source_hash():

@@ -84,16 +84,18 @@ struct SplitTables {
     const double* state;      // read by the stencil pass
     double* state_upd;        // updated in the slab epilogue
     float* Y;                 // FP32 chain buffer: F from the stencil pass, overwritten in place
-                              // by the mode-3 pass, read by the slab pass
+                              // by the mode-3 pass, read by the slab pass; layout [s][k][j][n1q]
+    int n1q;                  // n1 rounded up to a multiple of 4 (16-byte rows for bulk copies)
+    long long ys;             // floats per species of Y: n3 * n2 * n1q
     float tau;
     double tau_d;
     // slab pass (theta then rho)
     Image QT, Q, P[kMaxSpecies];
-    const float* had_theta;   // Phi table of the theta direction, [s][k][j'][i] (ball) or [s][j'][i]
+    const float* had_theta;   // Phi table of the theta direction, [s][k][j'][n1q] (ball) or [s][j'][n1q]
     long long had_theta_sp;   // floats per species
     // mode-3 pass
     Image M3a, M3b[kMaxSpecies];   // ball: Vinv (M3a) and V (M3b[0]); cylinder: Pz_s in M3b[s]
-    const float* had_phi;          // ball: Phi table of the phi direction, [s][k'][i]
+    const float* had_phi;          // ball: Phi table of the phi direction, [s][k'][n1q]
     int* err;
 };
 
@@ -102,7 +104,7 @@ struct BatchInstance {
     int n1, n2;                     // rho, theta points
     long long w_off;                // element offset of the instance's state (species blocks of n1 n2)
     Image QT, Q, P[2];              // theta transforms and phi_1(tau d_s A_rho) images
-    const float* had;               // Phi of the theta direction, [s][j'][i]
+    const float* had;               // Phi of the theta direction, [s][j'][n1q], n1q = n1 rounded up to 4
     StencilAxis<float> ax_rho, ax_theta;
     const float* Dr;                // rho_i^-2
     float d[2];

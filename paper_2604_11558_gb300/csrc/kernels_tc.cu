@@ -32,8 +32,8 @@ namespace sexpe {
 constexpr int kRows = 128;                 // MMA M and tensor-memory lanes
 constexpr int kThreads = 256;              // producer threads: two per row, columns 0-7 / 8-15 of a chunk
 constexpr int kBlock = kThreads + 64;      // + one warp issuing TMA copies ahead, one issuing the MMAs
-constexpr int kStages = 3;
-constexpr uint32_t kHeaderBytes = 1024;   // barriers + tensor-memory slot
+constexpr int kMaxStages = 3;   // stage ring depth: 3, or 2 when 3 would keep two CTAs off one SM
+constexpr uint32_t kHeaderBytes = 128;    // barriers + tensor-memory slot
 
 struct Pipe {
     uint64_t* tma_bar;     // matrix chunk landed (TMA transaction count)
@@ -41,6 +41,8 @@ struct Pipe {
     uint64_t* data_bar;    // data operand of the stage written (one arrive per producer warp)
     char* stages;
     uint32_t stage_bytes;
+    uint32_t nst;      // stages in the ring
+    uint32_t raw_bytes;   // raw region at the end of every stage
     uint32_t g;        // K-chunks issued so far in this CTA (uniform)
     int* err;
     volatile int* aborted;
@@ -67,6 +69,17 @@ __device__ __forceinline__ void store_row8(char* hi, char* lo, int r, int h, con
     }
 }
 
+// Global FP32 rows copied into a stage's raw region next to each K-chunk's
+// matrix copy (the producers then read shared memory only): chunk c copies rows
+// [16c, min(16c + 16, rows_total)), each `row_floats` floats (a multiple of 4),
+// row r of the chunk landing at raw + r * row_floats.
+struct AuxCopy {
+    const float* src;       // row 0; null = no copy
+    long long row_stride;   // floats between consecutive rows in global memory
+    int row_floats;
+    int rows_total;
+};
+
 struct GemmSpec {
     Image mat;
     int mat_is_A;     // constant matrix is the A operand (data is B) or the B operand
@@ -75,7 +88,11 @@ struct GemmSpec {
     int n_pad;        // N of the product (rows of B), multiple of 16
     int k_chunks;
     uint32_t tmem_d;  // tensor-memory address of the accumulator (tile mt at + mt * n_pad)
+    AuxCopy aux;
 };
+
+// Raw region of a stage: 16 rows of the widest staged row (<= 128 floats).
+__host__ __device__ constexpr uint32_t raw_bytes_for(int row_floats) { return (uint32_t)kKC * row_floats * 4u; }
 
 // Byte offset of the constant-matrix tiles inside a stage: after the data hi/lo tiles.
 __device__ __forceinline__ uint32_t mat_offset(const GemmSpec& G) { return 2u * G.data_rows * kTileRowBytes; }
@@ -88,18 +105,19 @@ __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& 
     const uint32_t data_bytes = (uint32_t)G.data_rows * kTileRowBytes;
     for (int c = 0; c < G.k_chunks; ++c) {
         const uint32_t g = P.g;
-        const int s = (int)(g % kStages);
-        const uint32_t use = g / kStages;
-        if (g >= (uint32_t)kStages) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
+        const int s = (int)(g % P.nst);
+        const uint32_t use = g / P.nst;
+        if (g >= P.nst) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
         char* st = P.stages + (size_t)s * P.stage_bytes;
-        produce(c, st, st + data_bytes);
+        if (G.aux.src) pipe_wait(P, &P.tma_bar[s], use & 1u, DERR_TIMEOUT_TMA);
+        produce(c, st, st + data_bytes, reinterpret_cast<const float*>(st + P.stage_bytes - P.raw_bytes));
         fence_async_smem();
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&P.data_bar[s]);
         P.g = g + 1;
     }
     const uint32_t gl = P.g - 1;
-    pipe_wait(P, &P.mma_bar[gl % kStages], (gl / kStages) & 1u, DERR_TIMEOUT_MMA);
+    pipe_wait(P, &P.mma_bar[gl % P.nst], (gl / P.nst) & 1u, DERR_TIMEOUT_MMA);
     tc_fence_after();
 }
 
@@ -117,8 +135,8 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
         const int n_halves = G.n_pad / nsub;
         const uint32_t idesc = idesc_tf32(128, nsub);
         for (int c = 0; c < G.k_chunks; ++c, ++g) {
-            const int s = (int)(g % kStages);
-            const uint32_t use = g / kStages;
+            const int s = (int)(g % P.nst);
+            const uint32_t use = g / P.nst;
             pipe_wait(P, &P.data_bar[s], use & 1u, DERR_TIMEOUT_MMA);
             pipe_wait(P, &P.tma_bar[s], use & 1u, DERR_TIMEOUT_TMA);
             tc_fence_after();
@@ -153,7 +171,7 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
 
 // TMA side: one lane of the extra warp walks the K-chunks of every product of
 // the CTA in order and copies each chunk's matrix image into its stage as soon
-// as the stage is free, up to kStages chunks ahead of the MMAs.
+// as the stage is free, up to one ring of stages ahead of the MMAs.
 __device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
     if ((threadIdx.x & 31) != 0) return;
     uint32_t g = P.g;
@@ -161,12 +179,31 @@ __device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
         const GemmSpec& G = gs[q];
         const uint32_t mat_bytes = (uint32_t)G.mat.rows_pad * kTileRowBytes;
         for (int c = 0; c < G.k_chunks; ++c, ++g) {
-            const int s = (int)(g % kStages);
-            const uint32_t use = g / kStages;
-            if (g >= (uint32_t)kStages) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
-            char* mhi = P.stages + (size_t)s * P.stage_bytes + mat_offset(G);
-            mbar_arrive_expect_tx(&P.tma_bar[s], 2 * mat_bytes);
+            const int s = (int)(g % P.nst);
+            const uint32_t use = g / P.nst;
+            if (g >= P.nst) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
+            char* st = P.stages + (size_t)s * P.stage_bytes;
+            char* mhi = st + mat_offset(G);
+            uint32_t tx = 2 * mat_bytes;
+            int rows = 0;
+            if (G.aux.src) {
+                rows = min(kKC, G.aux.rows_total - c * kKC);
+                rows = rows > 0 ? rows : 0;
+                tx += (uint32_t)rows * G.aux.row_floats * 4u;
+            }
+            mbar_arrive_expect_tx(&P.tma_bar[s], tx);
             tma_bulk_g2s(mhi, G.mat.ptr + (long long)c * G.mat.chunk_floats, 2 * mat_bytes, &P.tma_bar[s]);
+            if (rows > 0) {
+                char* raw = st + P.stage_bytes - P.raw_bytes;
+                const float* src = G.aux.src + (long long)c * kKC * G.aux.row_stride;
+                if (G.aux.row_stride == G.aux.row_floats) {          // contiguous rows: one copy
+                    tma_bulk_g2s(raw, src, (uint32_t)rows * G.aux.row_floats * 4u, &P.tma_bar[s]);
+                } else {
+                    for (int r = 0; r < rows; ++r)
+                        tma_bulk_g2s(raw + (size_t)r * G.aux.row_floats * 4, src + r * G.aux.row_stride,
+                                     (uint32_t)G.aux.row_floats * 4u, &P.tma_bar[s]);
+                }
+            }
         }
     }
     P.g = g;
@@ -178,15 +215,19 @@ struct CtaRes {
     uint32_t tmem;
 };
 
-__device__ __forceinline__ CtaRes cta_begin(char* smem_raw, uint32_t stage_bytes, uint32_t tmem_cols, int* err) {
+__device__ __forceinline__ CtaRes cta_begin(char* smem_raw, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
+                                            uint32_t tmem_cols, int* err) {
     const uint32_t base = smem_u32(smem_raw);
-    char* smem = smem_raw + (((base + 1023u) & ~1023u) - base);
+    char* smem = smem_raw + (((base + 127u) & ~127u) - base);   // 128-byte aligned ring
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 3 * kStages * sizeof(uint64_t));
-    int* aborted = reinterpret_cast<int*>(smem + 3 * kStages * sizeof(uint64_t) + 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 3 * kMaxStages * sizeof(uint64_t));
+    int* aborted = reinterpret_cast<int*>(smem + 3 * kMaxStages * sizeof(uint64_t) + 16);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * kStages; ++s) mbar_init(&bars[s], 1);
-        for (int s = 2 * kStages; s < 3 * kStages; ++s) mbar_init(&bars[s], kThreads / 32);
+        for (int s = 0; s < kMaxStages; ++s) {
+            mbar_init(&bars[s], 1);                          // tma_bar
+            mbar_init(&bars[kMaxStages + s], 1);             // mma_bar
+            mbar_init(&bars[2 * kMaxStages + s], kThreads / 32);   // data_bar
+        }
         *aborted = 0;
         fence_mbar_init();
     }
@@ -199,8 +240,10 @@ __device__ __forceinline__ CtaRes cta_begin(char* smem_raw, uint32_t stage_bytes
     tc_fence_after();
     CtaRes r;
     r.P.tma_bar = bars;
-    r.P.mma_bar = bars + kStages;
-    r.P.data_bar = bars + 2 * kStages;
+    r.P.mma_bar = bars + kMaxStages;
+    r.P.data_bar = bars + 2 * kMaxStages;
+    r.P.nst = nst;
+    r.P.raw_bytes = raw_bytes;
     r.P.stages = smem + kHeaderBytes;
     r.P.stage_bytes = stage_bytes;
     r.P.g = 0;
@@ -240,7 +283,7 @@ constexpr int kRhsThreads = 512;   // 128 lanes along rho x 4 line parities
 
 template <int GEO>
 __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, const double* __restrict__ Wall,
-                                                          float* __restrict__ F, int TJ) {
+                                                          float* __restrict__ F, int TJ, int n1q, long long ys) {
     using TS = TileShape<GEO>;
     extern __shared__ float2 tile[];                 // [S][nK][nJ][n1]
     __shared__ float cj[3][32], ck[4][8];            // j- and k-dependent coefficients of the tile
@@ -339,25 +382,35 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
                     if constexpr (GEO == GEO_BALL) lap = t0 + dr * (ck[3][kl] * t1 + t2);
                     else lap = t0 + dr * t1 + t2;
                 }
-                F[s * npts + idx] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
+                F[s * ys + ((long long)k * n2 + j) * n1q + i] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
             }
         }
     }
 }
 
 // ------------------------------------------------------------------------------
-// mode-3 pass: rows = 128 consecutive (i, j) points, columns = the k fibre;
-// reads F from Y and overwrites the same entries with the result.
+// mode-3 pass: rows = 128 consecutive points of the padded (i, j) plane
+// (row index j * n1q + i), columns = the k fibre; reads F from Y and overwrites
+// the same entries with the result.  The TMA warp stages every chunk's F rows
+// (16 k-planes x 128 points) and, for the ball, the Phi rows next to the
+// matrix chunk, so the producers read shared memory only.
 template <int GEO>
 __global__ void __launch_bounds__(kBlock, 1)
-    k_tc_mode3(SplitTables T, uint32_t stage_bytes, uint32_t tmem_cols) {
+    k_tc_mode3(SplitTables T, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
+                                              uint32_t tmem_cols) {
     extern __shared__ char smem_raw[];
-    CtaRes R = cta_begin(smem_raw, stage_bytes, tmem_cols, T.err);
+    CtaRes R = cta_begin(smem_raw, stage_bytes, nst, raw_bytes, tmem_cols, T.err);
     const int s = blockIdx.y;
-    const int n1 = T.n1, n3 = T.n3;
+    const int n3 = T.n3, n1q = T.n1q;
     const int n3p = (n3 + 15) & ~15;
-    GemmSpec gs[2] = {{GEO == GEO_BALL ? T.M3a : T.M3b[s], 0, kRows, 1, n3p, n3p / kKC, R.tmem},
-                      {T.M3b[0], 0, kRows, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p}};
+    const long long plane = (long long)T.n2 * n1q;          // floats per k-plane of Y
+    const long long row0 = (long long)blockIdx.x * kRows;
+    const int tile_rows = (int)(plane - row0 < kRows ? plane - row0 : kRows);
+    float* Ys = T.Y + (long long)s * T.ys;
+    GemmSpec gs[2] = {{GEO == GEO_BALL ? T.M3a : T.M3b[s], 0, kRows, 1, n3p, n3p / kKC, R.tmem,
+                       AuxCopy{Ys + row0, plane, tile_rows, n3}},
+                      {T.M3b[0], 0, kRows, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p,
+                       AuxCopy{T.had_phi + (long long)s * n3 * n1q, n1q, n1q, n3}}};
     if (threadIdx.x >= kThreads + 32) {
         mma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);
     } else if (threadIdx.x >= kThreads) {
@@ -366,48 +419,27 @@ __global__ void __launch_bounds__(kBlock, 1)
         const int tid = threadIdx.x;
         const int r = tid & (kRows - 1), h = tid >> 7;
         const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
-        const long long n12 = (long long)T.n1 * T.n2;
-        const long long ij = (long long)blockIdx.x * kRows + r;
-        const bool valid = ij < n12;
-        const int i = valid ? (int)(ij % n1) : 0;
-        float* Ys = T.Y + (long long)s * T.npts;
-        // one chunk of register prefetch: the loads of chunk c+1 are in flight while chunk c is split,
-        // stored and multiplied
-        float nxt[8];
-        auto load_f = [&](int c) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = c * 16 + h * 8 + q;
-                nxt[q] = (valid && k < n3) ? Ys[k * n12 + ij] : 0.f;
-            }
-        };
-        load_f(0);
-        run_gemm(R.P, gs[0], [&](int c, char* hi, char* lo) {
+        const bool valid = r < tile_rows;
+        const int i = (int)((row0 + r) % n1q);
+        run_gemm(R.P, gs[0], [&](int c, char* hi, char* lo, const float* raw) {
             float v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = nxt[q];
-            if (c + 1 < gs[0].k_chunks) load_f(c + 1);
+            for (int q = 0; q < 8; ++q) {
+                const int kk = h * 8 + q;
+                v[q] = (valid && c * 16 + kk < n3) ? raw[kk * tile_rows + r] : 0.f;
+            }
             store_row8(hi, lo, r, h, v);
         });
         uint32_t last = 0;
         if constexpr (GEO == GEO_BALL) {
-            const float* had = T.had_phi + (long long)s * n3 * n1 + i;
-            auto load_h = [&](int c) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int kp = c * 16 + h * 8 + q;
-                    nxt[q] = (valid && kp < n3) ? __ldg(had + kp * n1) : 0.f;
-                }
-            };
-            load_h(0);
-            run_gemm(R.P, gs[1], [&](int c, char* hi, char* lo) {
-                float v[8], f[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) f[q] = nxt[q];
-                if (c + 1 < gs[1].k_chunks) load_h(c + 1);
+            run_gemm(R.P, gs[1], [&](int c, char* hi, char* lo, const float* raw) {
+                float v[8];
                 tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] *= f[q];
+                for (int q = 0; q < 8; ++q) {
+                    const int kk = h * 8 + q;
+                    v[q] = (valid && c * 16 + kk < n3) ? v[q] * raw[kk * n1q + i] : 0.f;
+                }
                 store_row8(hi, lo, r, h, v);
             });
             last = (uint32_t)n3p;
@@ -418,7 +450,7 @@ __global__ void __launch_bounds__(kBlock, 1)
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int k = c * 16 + h * 8 + q;
-                if (valid && k < n3) Ys[k * n12 + ij] = v[q];
+                if (valid && k < n3) Ys[k * plane + row0 + r] = v[q];
             }
         }
     }
@@ -428,12 +460,12 @@ __global__ void __launch_bounds__(kBlock, 1)
 // ------------------------------------------------------------------------------
 // slab pass: one k-slab (n2 x n1 matrix, rho contiguous) of one species.
 struct SlabJob {
-    int n1, n2;
+    int n1, n2, n1q;      // n1q: row pitch of Y and of the Phi table (n1 rounded up to 4)
     const float* Y;       // F after the earlier directions, slab base (null: F from the state)
     const double* Win;    // state slab base read by the update (== W for an in-place step)
     double* W;            // state slab base written by the update
     Image QT, Q, P;
-    const float* had;     // Phi of the theta direction for this slab, [j'][i]
+    const float* had;     // Phi of the theta direction for this slab, [j'][n1q]
     float tau_f;
 };
 
@@ -447,9 +479,9 @@ __device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, uint
     cols[0] = 0;
     cols[1] = T - (uint32_t)(m2 * n1p);
     cols[2] = 0;
-    gs[0] = GemmSpec{J.QT, 0, kRows, 1, n2p, n2p / kKC, tmem + cols[0]};
-    gs[1] = GemmSpec{J.Q, 1, n1p, m2, n1p, n2p / kKC, tmem + cols[1]};
-    gs[2] = GemmSpec{J.P, 0, kRows * m2, m2, n1p, n1p / kKC, tmem + cols[2]};
+    gs[0] = GemmSpec{J.QT, 0, kRows, 1, n2p, n2p / kKC, tmem + cols[0], AuxCopy{J.Y, J.n1q, J.n1q, J.n2}};
+    gs[1] = GemmSpec{J.Q, 1, n1p, m2, n1p, n2p / kKC, tmem + cols[1], AuxCopy{J.had, J.n1q, J.n1q, J.n2}};
+    gs[2] = GemmSpec{J.P, 0, kRows * m2, m2, n1p, n1p / kKC, tmem + cols[2], AuxCopy{nullptr, 0, 0, 0}};
 }
 
 // F of one disk species at (i, j0 + q), q < 8, from FP64-accurate differences of
@@ -506,53 +538,39 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
     const uint32_t c1 = cols[0], c2 = cols[1], c3 = cols[2];
 
     // G1: X[i][j'] = sum_j Y[i][j] Q[j][j']          (Y x_2 Q_theta^T), rows i
-    float nxt[8];     // one chunk of register prefetch of the global operands
-    auto load_y = [&](int c) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int j = c * 16 + h * 8 + q;
-            nxt[q] = (r < n1 && j < n2) ? J.Y[j * n1 + r] : 0.f;
-        }
-    };
+    const int n1q = J.n1q;
     if (BI) {
-        run_gemm(P, gs[0], [&](int c, char* hi, char* lo) {
+        run_gemm(P, gs[0], [&](int c, char* hi, char* lo, const float*) {
             float v[8];
             disk_F8(*BI, inst_base, species, r, c * 16 + h * 8, v);
             store_row8(hi, lo, r, h, v);
         });
     } else {
-        load_y(0);
-        run_gemm(P, gs[0], [&](int c, char* hi, char* lo) {
+        run_gemm(P, gs[0], [&](int c, char* hi, char* lo, const float* raw) {
             float v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = nxt[q];
-            if (c + 1 < gs[0].k_chunks) load_y(c + 1);
+            for (int q = 0; q < 8; ++q) {
+                const int jl = h * 8 + q;
+                v[q] = (r < n1 && c * 16 + jl < n2) ? raw[jl * n1q + r] : 0.f;
+            }
             store_row8(hi, lo, r, h, v);
         });
     }
     // G2: Z^T[j][i] = sum_j' Q[j][j'] (Phi o X)[i][j']   (x_2 Q_theta), data in B, rows j
-    auto load_h = [&](int c) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int jp = c * 16 + h * 8 + q;
-            nxt[q] = (r < n1 && jp < n2) ? __ldg(J.had + jp * n1 + r) : 0.f;
-        }
-    };
-    load_h(0);
-    run_gemm(P, gs[1], [&](int c, char* hi, char* lo) {
-        float v[8], f[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) f[q] = nxt[q];
-        if (c + 1 < gs[1].k_chunks) load_h(c + 1);
+    run_gemm(P, gs[1], [&](int c, char* hi, char* lo, const float* raw) {
+        float v[8];
         tmem_ld8(tmem + lane_base + c1 + (uint32_t)(c * 16 + h * 8), v);
         if (r < n1p) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] *= f[q];
+            for (int q = 0; q < 8; ++q) {
+                const int jl = h * 8 + q;
+                v[q] = (r < n1 && c * 16 + jl < n2) ? v[q] * raw[jl * n1q + r] : 0.f;
+            }
             store_row8(hi, lo, r, h, v);
         }
     });
     // G3: R^T[j][i'] = sum_i Z^T[j][i] P[i'][i]      (x_1 phi_1(tau d A_rho)), rows j
-    run_gemm(P, gs[2], [&](int c, char* hi, char* lo) {
+    run_gemm(P, gs[2], [&](int c, char* hi, char* lo, const float*) {
         for (int mt = 0; mt < m2; ++mt) {
             float v[8];
             tmem_ld8(tmem + lane_base + c2 + (uint32_t)(mt * n1p + c * 16 + h * 8), v);
@@ -603,22 +621,26 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
 }
 
 __global__ void __launch_bounds__(kBlock, 1)
-    k_tc_slab(SplitTables T, uint32_t stage_bytes, uint32_t tmem_cols) {
+    k_tc_slab(SplitTables T, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
+                                              uint32_t tmem_cols) {
     extern __shared__ char smem_raw[];
-    CtaRes R = cta_begin(smem_raw, stage_bytes, tmem_cols, T.err);
+    CtaRes R = cta_begin(smem_raw, stage_bytes, nst, raw_bytes, tmem_cols, T.err);
     const int k = blockIdx.x, s = blockIdx.y;
     const long long n12 = (long long)T.n1 * T.n2;
+    const long long plane = (long long)T.n2 * T.n1q;
     SlabJob J;
     J.n1 = T.n1;
     J.n2 = T.n2;
-    J.Y = T.Y + (long long)s * T.npts + k * n12;
+    J.n1q = T.n1q;
+    J.Y = T.Y + (long long)s * T.ys + k * plane;
     J.W = T.state_upd + (long long)s * T.npts + k * n12;
     J.Win = J.W;
     J.QT = T.QT;
     J.Q = T.Q;
     J.P = T.P[s];
-    J.had = T.had_theta + (long long)s * T.had_theta_sp + (T.geometry == GEO_BALL ? k * n12 : 0);
+    J.had = T.had_theta + (long long)s * T.had_theta_sp + (T.geometry == GEO_BALL ? k * plane : 0);
     J.tau_f = T.tau;
+    if (threadIdx.x == kThreads) l2_prefetch(J.W, (unsigned long long)n12 * 8);
     GemmSpec gs[3];
     uint32_t cols[3];
     slab_specs(J, R.tmem, tmem_cols, gs, cols);
@@ -634,10 +656,11 @@ __global__ void __launch_bounds__(kBlock, 1)
 // F from the previous state, x_2 Q_theta^T, Hadamard, x_2 Q_theta, x_1
 // phi_1(tau d A_rho) -- writing the updated species into the other state buffer.
 __global__ void __launch_bounds__(kBlock, 1)
-    k_tc_batch(BatchTables B, uint32_t stage_bytes, uint32_t tmem_cols) {
+    k_tc_batch(BatchTables B, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
+                                              uint32_t tmem_cols) {
     extern __shared__ char smem_raw[];
     __shared__ int s_item;
-    CtaRes R = cta_begin(smem_raw, stage_bytes, tmem_cols, B.err);
+    CtaRes R = cta_begin(smem_raw, stage_bytes, nst, raw_bytes, tmem_cols, B.err);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(B.counter, 1);
         tc_fence_before();
@@ -653,14 +676,16 @@ __global__ void __launch_bounds__(kBlock, 1)
         SlabJob J;
         J.n1 = I.n1;
         J.n2 = I.n2;
+        J.n1q = (I.n1 + 3) & ~3;
         J.Y = nullptr;
         J.Win = B.W_in + I.w_off + s * n12;
         J.W = B.W_out + I.w_off + s * n12;
         J.QT = I.QT;
         J.Q = I.Q;
         J.P = I.P[s];
-        J.had = I.had + s * n12;
+        J.had = I.had + s * (long long)I.n2 * J.n1q;
         J.tau_f = B.tau;
+        if (threadIdx.x == kThreads) l2_prefetch(J.Win, (unsigned long long)n12 * 8);
         GemmSpec gs[3];
         uint32_t cols[3];
         slab_specs(J, R.tmem, tmem_cols, gs, cols);
@@ -682,14 +707,26 @@ static uint32_t pow2_cols(uint32_t c) {
     return p;
 }
 
+// Stage-ring depth and shared-memory size: three stages when two CTAs still fit
+// on one SM (228 KB per SM, 1 KB reserved per CTA), else two.
+static void ring(TcShape& sh, uint32_t min_body) {
+    const uint32_t pair_limit = 228 * 1024 / 2 - 1024 - 128;   // 128: alignment slack of the ring
+    sh.nst = 3;
+    if (kHeaderBytes + 3 * sh.stage_bytes > pair_limit && kHeaderBytes + 2 * sh.stage_bytes >= min_body) sh.nst = 2;
+    uint32_t body = sh.nst * sh.stage_bytes;
+    if (body < min_body) body = min_body;
+    sh.smem_bytes = 128 + kHeaderBytes + body;
+}
+
 TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3) {
     (void)n1;
     (void)n2;
     TcShape sh{};
     const uint32_t n3p = round_up(n3, 16);
-    sh.stage_bytes = round_up(2u * kRows * kTileRowBytes + 2u * n3p * kTileRowBytes, 1024);
+    sh.raw_bytes = raw_bytes_for(kRows);
+    sh.stage_bytes = round_up(2u * kRows * kTileRowBytes + 2u * n3p * kTileRowBytes + sh.raw_bytes, 128);
     sh.tmem_cols = pow2_cols(geometry == GEO_BALL ? 2 * n3p : n3p);
-    sh.smem_bytes = 1024 + kHeaderBytes + kStages * sh.stage_bytes;
+    ring(sh, 0);
     return sh;
 }
 
@@ -709,15 +746,11 @@ TcShape tc_slab_shape(int n1, int n2) {
     const uint32_t rows3 = kRows * m2 + n1p;            // G3
     uint32_t rows = rows1 > rows2 ? rows1 : rows2;
     rows = rows > rows3 ? rows : rows3;
-    sh.stage_bytes = round_up(2u * rows * kTileRowBytes, 1024);
-    const uint32_t epi = kRows * (n1p + 1) * 4u;
-    uint32_t body = kStages * sh.stage_bytes;
-    if (body < epi) {
-        sh.stage_bytes = round_up((epi + kStages - 1) / kStages, 1024);
-        body = kStages * sh.stage_bytes;
-    }
+    sh.raw_bytes = raw_bytes_for((int)round_up(n1, 4));
+    sh.stage_bytes = round_up(2u * rows * kTileRowBytes + sh.raw_bytes, 128);
+    const uint32_t epi = kRows * (n1p + 1) * 4u;       // epilogue staging reuses the ring
     sh.tmem_cols = slab_tmem_cols(n1, n2);
-    sh.smem_bytes = 1024 + kHeaderBytes + body;
+    ring(sh, epi);
     return sh;
 }
 
@@ -741,17 +774,17 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
 }
 
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
-    dim3 grid((unsigned)((T.n1 * (long long)T.n2 + kRows - 1) / kRows), T.S);
+    dim3 grid((unsigned)((T.n1q * (long long)T.n2 + kRows - 1) / kRows), T.S);
     if (T.geometry == GEO_BALL)
-        k_tc_mode3<GEO_BALL><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
+        k_tc_mode3<GEO_BALL><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
     else
-        k_tc_mode3<GEO_CYLINDER><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
+        k_tc_mode3<GEO_CYLINDER><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid(T.geometry == GEO_DISK ? 1 : T.n3, T.S);
-    k_tc_slab<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.tmem_cols);
+    k_tc_slab<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
     return cudaGetLastError();
 }
 
@@ -786,7 +819,7 @@ static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
     const int tj = rhs_tile_tj<GEO>(T);
     const size_t smem = sizeof(float2) * (size_t)T.S * (TS::TK + 2 * TS::KH) * (tj + 2) * T.n1;
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + TS::TK - 1) / TS::TK, 1);
-    k_rhs_tile<GEO><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj);
+    k_rhs_tile<GEO><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, T.n1q, T.ys);
     return cudaGetLastError();
 }
 
@@ -803,7 +836,7 @@ cudaError_t tc_prepare_batch(uint32_t smem) {
 cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(B.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_tc_batch<<<152, kBlock, sh.smem_bytes, st>>>(B, sh.stage_bytes, sh.tmem_cols);
+    k_tc_batch<<<152, kBlock, sh.smem_bytes, st>>>(B, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@ struct TcShape {
     uint32_t stage_bytes;
     uint32_t tmem_cols;
     uint32_t smem_bytes;
+    uint32_t nst;          // stages in the ring
+    uint32_t raw_bytes;    // staged-row region at the end of every stage
 };
 TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3);
 TcShape tc_slab_shape(int n1, int n2);

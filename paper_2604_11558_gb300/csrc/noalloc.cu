@@ -26,8 +26,9 @@ sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float
 
 namespace {
 
-// 2^21 floats = 8 MiB: enough for species x points <= 2,097,152 (the two-species
-// 100^3 ball needs 2,000,000).
+// 2^21 floats = 8 MiB: enough for species x points <= 2,097,152, with every
+// rho line padded to a multiple of 4 points (the two-species 100^3 ball needs
+// 2,000,000).
 constexpr long long kNoAllocScratchFloats = 2LL * 1024 * 1024;
 
 static __device__ __align__(256) float g_step_scratch[kNoAllocScratchFloats];
@@ -61,7 +62,10 @@ extern "C" sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, 
     const sexpe_status s = scratch_for_current_device(&scratch);
     if (s != SEXPE_OK) return s;
     // Nothing in the scratch has to start at zero: every step's first kernel
-    // writes all species x points values before the second kernel reads them.
+    // writes all species x points values before a later kernel reads them.
+    // The padding of the rho lines (n_rho not a multiple of 4) may hold values
+    // left by an earlier call; padded points only ever produce padded points,
+    // which no result reads.
     for (int64_t k = 0; k < n_steps; ++k) {
         const sexpe_status r =
             sexpe::enqueue_split_step_with_scratch(plan, state_dev, scratch, kNoAllocScratchFloats,

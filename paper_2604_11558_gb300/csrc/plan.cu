@@ -254,7 +254,10 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     T.tau = (float)p->tau;
     T.tau_d = p->tau;
     SX_TRY(build_rhs_tables<float>(p, &T.rhs, st));
-    SX_TRY(alloc_dev(p, (size_t)p->S * p->npts, &T.Y));
+    T.n1q = (n1 + 3) & ~3;
+    T.ys = (long long)n3 * n2 * T.n1q;
+    SX_TRY(alloc_dev(p, (size_t)p->S * T.ys, &T.Y));
+    SX_CUDA(cudaMemsetAsync(T.Y, 0, sizeof(float) * (size_t)p->S * T.ys, st));   // padding columns stay zero
     T.err = p->d_err;
     // theta direction (mode 2): Q_theta, eigenvalues, Hadamard coefficients
     const int n1p = rup16(n1), n2p = rup16(n2), m2 = (n2 + 127) / 128;
@@ -263,14 +266,14 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     SX_TRY(upload_image(p, n2, n2, 128 * m2, n2p, [&](int r, int k) { return th.V(r, k); }, &T.Q, st));
     // Phi of the theta direction: phi_1(tau d_s s(i, k) lambda_theta_j'), one FP64 evaluation rounded once.
     const bool ball = p->geometry == SEXPE_BALL;
-    const long long n12 = (long long)n1 * n2;
-    T.had_theta_sp = ball ? p->npts : n12;
-    std::vector<float> hc((size_t)p->S * T.had_theta_sp);
+    const long long plane = (long long)n2 * T.n1q;
+    T.had_theta_sp = ball ? (long long)n3 * plane : plane;
+    std::vector<float> hc((size_t)p->S * T.had_theta_sp, 0.f);
     for (int s = 0; s < p->S; ++s)
         for (int k = 0; k < (ball ? n3 : 1); ++k)
             for (int jp = 0; jp < n2; ++jp)
                 for (int i = 0; i < n1; ++i)
-                    hc[(size_t)s * T.had_theta_sp + (size_t)k * n12 + (size_t)jp * n1 + i] =
+                    hc[(size_t)s * T.had_theta_sp + (size_t)k * plane + (size_t)jp * T.n1q + i] =
                         (float)phi1_scalar(p->tau * p->d[s] * dir_scale(p, 2, i, 0, k) * th.lam[jp]);
     SX_TRY(upload(p, hc, &T.had_theta, st));
     // rho direction (mode 1): phi_1(tau d_s A_rho) per species
@@ -290,11 +293,11 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
             if (!all_finite(ph.V.a) || !all_finite(ph.Vinv.a)) return SEXPE_ENUMERIC;
             SX_TRY(upload_image(p, n3, n3, n3p, n3p, [&](int r, int k) { return ph.Vinv(r, k); }, &T.M3a, st));
             SX_TRY(upload_image(p, n3, n3, n3p, n3p, [&](int r, int k) { return ph.V(r, k); }, &T.M3b[0], st));
-            std::vector<float> hp((size_t)p->S * n3 * n1);
+            std::vector<float> hp((size_t)p->S * n3 * T.n1q, 0.f);
             for (int s = 0; s < p->S; ++s)
                 for (int kp = 0; kp < n3; ++kp)
                     for (int i = 0; i < n1; ++i)
-                        hp[((size_t)s * n3 + kp) * n1 + i] =
+                        hp[((size_t)s * n3 + kp) * T.n1q + i] =
                             (float)phi1_scalar(p->tau * p->d[s] * dir_scale(p, 3, i, 0, 0) * ph.lam[kp]);
             SX_TRY(upload(p, hp, &T.had_phi, st));
         } else {
@@ -553,11 +556,12 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
         }
         o.p0 = pofs[0];
         o.p1 = pofs[1];
-        std::vector<float> had((size_t)2 * n1 * n2);
+        const int n1q = (n1 + 3) & ~3;
+        std::vector<float> had((size_t)2 * n1q * n2, 0.f);
         for (int sp = 0; sp < 2; ++sp)
             for (int jp = 0; jp < n2; ++jp)
                 for (int i = 0; i < n1; ++i)
-                    had[(size_t)sp * n1 * n2 + (size_t)jp * n1 + i] =
+                    had[(size_t)sp * n1q * n2 + (size_t)jp * n1q + i] =
                         (float)phi1_scalar(tau * dsp[sp] * th.lam[jp] / (ar.pts[i] * ar.pts[i]));
         o.had = put(had);
         auto axis_f = [&](const Axis& a, size_t& lo, size_t& up, size_t& rs) {
@@ -799,7 +803,7 @@ sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float
                                              cudaStream_t st) {
     if (!p || !state || !Y) return SEXPE_EINVAL;
     if (p->precision != SEXPE_SPLIT_TF32 || p->batch) return SEXPE_EINVAL;
-    if ((long long)p->S * p->npts > y_floats) return SEXPE_EINVAL;
+    if ((long long)p->S * p->tabs.ys > y_floats) return SEXPE_EINVAL;
     SplitTables T = p->tabs;
     T.state = state;
     T.state_upd = state;

@@ -61,6 +61,18 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
         : "memory");
 }
 
+// Bring the 16-byte-aligned part of [src, src + bytes) into L2 ahead of use
+// (the bulk prefetch takes a 16-byte-aligned address and a multiple of 16 bytes).
+__device__ __forceinline__ void l2_prefetch(const void* src, unsigned long long bytes) {
+    const unsigned long long a = (unsigned long long)src;
+    const unsigned long long lo = (a + 15ull) & ~15ull, hi = (a + bytes) & ~15ull;
+    if (hi > lo) {
+        const unsigned long long n = hi - lo;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(n < 0x7FFFFFF0ull ? n : 0x7FFFFFF0ull))
+                     : "memory");
+    }
+}
+
 // ---- fences ---------------------------------------------------------------
 // Generic-proxy shared-memory writes -> visible to the async proxy (tcgen05.mma operands).
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -32,28 +32,49 @@ namespace sexpe {
 constexpr int kRows = 128;                 // MMA M and tensor-memory lanes
 constexpr int kThreads = 256;              // producer threads: two per row, columns 0-7 / 8-15 of a chunk
 constexpr int kBlock = kThreads + 64;      // + one warp issuing TMA copies ahead, one issuing the MMAs
-constexpr int kMaxStages = 3;   // stage ring depth: 3, or 2 when 3 would keep two CTAs off one SM
-constexpr uint32_t kHeaderBytes = 128;    // barriers + tensor-memory slot
+constexpr int kMaxMat = 6;                 // matrix-ring slots (TMA lookahead)
+constexpr int kMaxData = 4;                // data-ring slots
+constexpr uint32_t kHeaderBytes = 256;     // barriers + tensor-memory slot + abort flag
 
+// Two rings of shared-memory slots, both indexed by the running K-chunk
+// counter g of the CTA: the constant matrix of chunk g goes to matrix slot
+// g % nm (written by the TMA warp), its data operand to data slot g % nd
+// (written by the producers).  The MMAs of a chunk release both slots through
+// tcgen05.commit, so the TMA warp can run nm chunks ahead of the MMAs while
+// the producers run nd chunks ahead.
 struct Pipe {
-    uint64_t* tma_bar;     // matrix chunk landed (TMA transaction count)
-    uint64_t* mma_bar;     // MMAs reading the stage completed (tcgen05.commit)
-    uint64_t* data_bar;    // data operand of the stage written (one arrive per producer warp)
-    char* stages;
-    uint32_t stage_bytes;
-    uint32_t nst;      // stages in the ring
-    uint32_t raw_bytes;   // raw region at the end of every stage
-    uint32_t g;        // K-chunks issued so far in this CTA (uniform)
+    uint64_t* mat_full;     // matrix chunk landed (TMA transaction count)
+    uint64_t* mat_empty;    // MMAs reading the matrix slot completed
+    uint64_t* data_full;    // data operand written (one arrive per producer warp)
+    uint64_t* data_empty;   // MMAs reading the data slot completed
+    char* mat_slots;
+    char* data_slots;
+    uint32_t mat_bytes;     // bytes per matrix slot (hi + lo tiles)
+    uint32_t data_bytes;    // bytes per data slot (hi + lo tiles)
+    uint32_t nm, nd;
+    uint32_t g;             // K-chunks this thread's role has passed so far in this CTA
+    // ring position of chunk g, kept incrementally (no divisions on the hot
+    // paths): slot and phase parity (the number of completed ring turns, mod 2)
+    uint32_t sd, pd, sm, pm;
     int* err;
     volatile int* aborted;
+    __device__ __forceinline__ void advance() {
+        ++g;
+        if (++sd == nd) { sd = 0; pd ^= 1u; }
+        if (++sm == nm) { sm = 0; pm ^= 1u; }
+    }
 };
 
+// Bounded wait on a pipeline barrier; a phase that already completed returns
+// after one try_wait (the hot path of the MMA thread), and after a timeout
+// anywhere in the CTA the remaining waits give up quickly.
 __device__ __forceinline__ void pipe_wait(Pipe& P, uint64_t* bar, uint32_t parity, int code) {
+    if (mbar_try_wait(bar, parity)) return;
     const long long lim = *P.aborted ? 2000000LL : 4000000000LL;
     if (!mbar_wait_bounded(bar, parity, P.err, code, lim)) *P.aborted = 1;
 }
 
-// Barrier of the 256 compute threads only (the TMA warp runs on its own).
+// Barrier of the 256 compute threads only (the TMA and MMA warps run on their own).
 __device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // Row r, columns 8h..8h+7 of a chunk, of a tile pair (hi, lo).
@@ -69,17 +90,6 @@ __device__ __forceinline__ void store_row8(char* hi, char* lo, int r, int h, con
     }
 }
 
-// Global FP32 rows copied into a stage's raw region next to each K-chunk's
-// matrix copy (the producers then read shared memory only): chunk c copies rows
-// [16c, min(16c + 16, rows_total)), each `row_floats` floats (a multiple of 4),
-// row r of the chunk landing at raw + r * row_floats.
-struct AuxCopy {
-    const float* src;       // row 0; null = no copy
-    long long row_stride;   // floats between consecutive rows in global memory
-    int row_floats;
-    int rows_total;
-};
-
 struct GemmSpec {
     Image mat;
     int mat_is_A;     // constant matrix is the A operand (data is B) or the B operand
@@ -88,125 +98,140 @@ struct GemmSpec {
     int n_pad;        // N of the product (rows of B), multiple of 16
     int k_chunks;
     uint32_t tmem_d;  // tensor-memory address of the accumulator (tile mt at + mt * n_pad)
-    AuxCopy aux;
 };
 
-// Raw region of a stage: 16 rows of the widest staged row (<= 128 floats).
-__host__ __device__ constexpr uint32_t raw_bytes_for(int row_floats) { return (uint32_t)kKC * row_floats * 4u; }
+// Eight floats a producer thread needs from global memory for one K-chunk.
+struct Pre8 {
+    float v[8];
+};
 
-// Byte offset of the constant-matrix tiles inside a stage: after the data hi/lo tiles.
-__device__ __forceinline__ uint32_t mat_offset(const GemmSpec& G) { return 2u * G.data_rows * kTileRowBytes; }
-
-// Producer side of one product: the 256 producer threads write the data operand
-// of each K-chunk into its stage and signal the MMA warp through the stage's
-// data barrier; a stage is rewritten only after the MMAs that read it completed.
-template <class Producer>
-__device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& produce) {
-    const uint32_t data_bytes = (uint32_t)G.data_rows * kTileRowBytes;
+// Producer side of one product.  `load(c, Pre8&)` issues the global loads a
+// thread needs for chunk c (or nothing), `produce(c, hi, lo, const Pre8&)`
+// writes the data operand of chunk c into its slot; loads run two chunks ahead
+// in registers so their latency overlaps the work of the chunks in between.  A
+// data slot is rewritten only after the MMAs that read it completed.  Each
+// producer warp arrives on the chunk's data barrier once its part is written
+// AND the chunk's matrix copy has landed, so the MMA thread waits on a single
+// barrier per chunk (every wait costs the issuing thread ~100+ cycles during
+// which the tensor pipe runs dry).
+template <class Loader, class Producer>
+__device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Loader&& load, Producer&& produce) {
+    Pre8 p0, p1;
+    load(0, p0);
+    if (G.k_chunks > 1) load(1, p1);
+    uint32_t last_sd = 0, last_pd = 0;
     for (int c = 0; c < G.k_chunks; ++c) {
-        const uint32_t g = P.g;
-        const int s = (int)(g % P.nst);
-        const uint32_t use = g / P.nst;
-        if (g >= P.nst) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
-        char* st = P.stages + (size_t)s * P.stage_bytes;
-        if (G.aux.src) pipe_wait(P, &P.tma_bar[s], use & 1u, DERR_TIMEOUT_TMA);
-        produce(c, st, st + data_bytes, reinterpret_cast<const float*>(st + P.stage_bytes - P.raw_bytes));
+        Pre8 p2;
+        if (c + 2 < G.k_chunks) load(c + 2, p2);
+        const uint32_t s = P.sd;
+        if (P.g >= P.nd) pipe_wait(P, &P.data_empty[s], P.pd ^ 1u, DERR_TIMEOUT_MMA);
+        char* hi = P.data_slots + (size_t)s * P.data_bytes;
+        produce(c, hi, hi + G.data_rows * kTileRowBytes, p0);
         fence_async_smem();
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&P.data_bar[s]);
-        P.g = g + 1;
+        if ((threadIdx.x & 31) == 0) {
+            pipe_wait(P, &P.mat_full[P.sm], P.pm, DERR_TIMEOUT_TMA);
+            mbar_arrive(&P.data_full[s]);
+        }
+        last_sd = s;
+        last_pd = P.pd;
+        P.advance();
+        p0 = p1;
+        p1 = p2;
     }
-    const uint32_t gl = P.g - 1;
-    pipe_wait(P, &P.mma_bar[gl % P.nst], (gl / P.nst) & 1u, DERR_TIMEOUT_MMA);
+    pipe_wait(P, &P.data_empty[last_sd], last_pd, DERR_TIMEOUT_MMA);
     tc_fence_after();
 }
 
+template <class Producer>
+__device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& produce) {
+    run_gemm(P, G, [](int, Pre8&) {}, produce);
+}
+
 // MMA side: one lane of the MMA warp walks the K-chunks of every product in
-// order; when a chunk's data operand and matrix copy are both in its stage it
-// issues the three TF32 MMAs per K-step and commits them to the stage barrier.
+// order; when a chunk's data barrier completes (data operand written, matrix
+// copy landed) it issues the three TF32 MMAs per K-step and commits them to
+// both slots' empty barriers.
+//
+// The issuing thread is the only producer of work for the tensor pipe, and a
+// few scalar instructions per MMA already cost more than an MMA of N = 112
+// takes to execute (~60 cycles), so the loop is kept lean: descriptors of
+// slot 0 are formed once per product and moved by constant offsets (in the
+// descriptor's 16-byte address units, which cannot carry out of the 14-bit
+// field below 256 KB), and the usual one-tile product is fully unrolled.
 __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
     if ((threadIdx.x & 31) != 0) return;
-    uint32_t g = P.g;
+    const uint32_t mat16 = P.mat_bytes >> 4, data16 = P.data_bytes >> 4;
+    constexpr uint64_t kKStep = (2 * kLBO) >> 4;       // next 8 K-columns: two core matrices
+    const uint32_t mslot0 = smem_u32(P.mat_slots), dslot0 = smem_u32(P.data_slots);
     for (int q = 0; q < n_gemms; ++q) {
         const GemmSpec& G = gs[q];
-        const uint32_t data_bytes = (uint32_t)G.data_rows * kTileRowBytes;
-        const uint32_t mat_bytes = (uint32_t)G.mat.rows_pad * kTileRowBytes;
         const int nsub = G.n_pad < 256 ? G.n_pad : 256;
         const int n_halves = G.n_pad / nsub;
         const uint32_t idesc = idesc_tf32(128, nsub);
-        for (int c = 0; c < G.k_chunks; ++c, ++g) {
-            const int s = (int)(g % P.nst);
-            const uint32_t use = g / P.nst;
-            pipe_wait(P, &P.data_bar[s], use & 1u, DERR_TIMEOUT_MMA);
-            pipe_wait(P, &P.tma_bar[s], use & 1u, DERR_TIMEOUT_TMA);
+        // hi tile at the slot start, lo tile right after it
+        const uint32_t mtile = (uint32_t)G.mat.rows_pad * kTileRowBytes, dtile = (uint32_t)G.data_rows * kTileRowBytes;
+        const uint64_t dmh = smem_desc(mslot0, kLBO, kSBO), dml = smem_desc(mslot0 + mtile, kLBO, kSBO);
+        const uint64_t ddh = smem_desc(dslot0, kLBO, kSBO), ddl = smem_desc(dslot0 + dtile, kLBO, kSBO);
+        const uint32_t d = G.tmem_d;
+        const bool one_tile = G.m_tiles == 1 && n_halves == 1;
+        for (int c = 0; c < G.k_chunks; ++c, P.advance()) {
+            const uint32_t sm = P.sm, sd = P.sd;
+            pipe_wait(P, &P.data_full[sd], P.pd, DERR_TIMEOUT_MMA);
             tc_fence_after();
-            char* st = P.stages + (size_t)s * P.stage_bytes;
-            char* dhi = st;
-            char* dlo = st + data_bytes;
-            char* mhi = st + mat_offset(G);
-            char* mlo = mhi + mat_bytes;
-            const uint32_t a_hi = smem_u32(G.mat_is_A ? mhi : dhi), a_lo = smem_u32(G.mat_is_A ? mlo : dlo);
-            const uint32_t b_hi = smem_u32(G.mat_is_A ? dhi : mhi), b_lo = smem_u32(G.mat_is_A ? dlo : mlo);
+            const uint64_t om = (uint64_t)sm * mat16, od = (uint64_t)sd * data16;
+            const uint64_t mh = dmh + om, ml = dml + om, dh = ddh + od, dl = ddl + od;
+            const uint64_t ah = G.mat_is_A ? mh : dh, al = G.mat_is_A ? ml : dl;
+            const uint64_t bh = G.mat_is_A ? dh : mh, bl = G.mat_is_A ? dl : ml;
+            if (one_tile) {
 #pragma unroll
-            for (int ks = 0; ks < kKC / 8; ++ks) {
+                for (int ks = 0; ks < kKC / 8; ++ks) {       // lo*hi, hi*lo, hi*hi per K-step
+                    const uint64_t k = (uint64_t)ks * kKStep;
+                    mma_tf32(d, al + k, bh + k, idesc, (c | ks) != 0);
+                    mma_tf32(d, ah + k, bl + k, idesc, 1u);
+                    mma_tf32(d, ah + k, bh + k, idesc, 1u);
+                }
+            } else {
 #pragma unroll
-                for (int pass = 0; pass < 3; ++pass) {      // lo*hi, hi*lo, hi*hi
-                    const uint32_t a = (pass == 0) ? a_lo : a_hi;
-                    const uint32_t b = (pass == 1) ? b_lo : b_hi;
-                    const uint32_t acc = (c | ks | pass) != 0;
-                    for (int mt = 0; mt < G.m_tiles; ++mt) {
-                        for (int nh = 0; nh < n_halves; ++nh) {
-                            const uint64_t ad = smem_desc(a + mt * 16 * kSBO + ks * 2 * kLBO, kLBO, kSBO);
-                            const uint64_t bd = smem_desc(b + nh * (nsub / 8) * kSBO + ks * 2 * kLBO, kLBO, kSBO);
-                            mma_tf32(G.tmem_d + (uint32_t)(mt * G.n_pad + nh * nsub), ad, bd, idesc, acc);
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+#pragma unroll
+                    for (int pass = 0; pass < 3; ++pass) {
+                        const uint64_t a = ((pass == 0) ? al : ah) + (uint64_t)ks * kKStep;
+                        const uint64_t b = ((pass == 1) ? bl : bh) + (uint64_t)ks * kKStep;
+                        const uint32_t acc = (c | ks | pass) != 0;
+                        for (int mt = 0; mt < G.m_tiles; ++mt) {
+                            const uint64_t am = a + (uint64_t)mt * ((16 * kSBO) >> 4);
+                            for (int nh = 0; nh < n_halves; ++nh)
+                                mma_tf32(d + (uint32_t)(mt * G.n_pad + nh * nsub), am,
+                                         b + (uint64_t)nh * (((nsub / 8) * kSBO) >> 4), idesc, acc);
                         }
                     }
                 }
             }
-            mma_commit(&P.mma_bar[s]);
+            mma_commit(&P.data_empty[sd]);
+            mma_commit(&P.mat_empty[sm]);
         }
     }
-    P.g = g;
 }
 
 // TMA side: one lane of the extra warp walks the K-chunks of every product of
-// the CTA in order and copies each chunk's matrix image into its stage as soon
-// as the stage is free, up to one ring of stages ahead of the MMAs.
+// the CTA in order and copies each chunk's matrix image (hi tile then lo tile,
+// one bulk copy) into its slot as soon as the slot is free, up to nm chunks ahead
+// of the MMAs.
 __device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
     if ((threadIdx.x & 31) != 0) return;
-    uint32_t g = P.g;
     for (int q = 0; q < n_gemms; ++q) {
         const GemmSpec& G = gs[q];
-        const uint32_t mat_bytes = (uint32_t)G.mat.rows_pad * kTileRowBytes;
-        for (int c = 0; c < G.k_chunks; ++c, ++g) {
-            const int s = (int)(g % P.nst);
-            const uint32_t use = g / P.nst;
-            if (g >= P.nst) pipe_wait(P, &P.mma_bar[s], (use - 1) & 1u, DERR_TIMEOUT_MMA);
-            char* st = P.stages + (size_t)s * P.stage_bytes;
-            char* mhi = st + mat_offset(G);
-            uint32_t tx = 2 * mat_bytes;
-            int rows = 0;
-            if (G.aux.src) {
-                rows = min(kKC, G.aux.rows_total - c * kKC);
-                rows = rows > 0 ? rows : 0;
-                tx += (uint32_t)rows * G.aux.row_floats * 4u;
-            }
-            mbar_arrive_expect_tx(&P.tma_bar[s], tx);
-            tma_bulk_g2s(mhi, G.mat.ptr + (long long)c * G.mat.chunk_floats, 2 * mat_bytes, &P.tma_bar[s]);
-            if (rows > 0) {
-                char* raw = st + P.stage_bytes - P.raw_bytes;
-                const float* src = G.aux.src + (long long)c * kKC * G.aux.row_stride;
-                if (G.aux.row_stride == G.aux.row_floats) {          // contiguous rows: one copy
-                    tma_bulk_g2s(raw, src, (uint32_t)rows * G.aux.row_floats * 4u, &P.tma_bar[s]);
-                } else {
-                    for (int r = 0; r < rows; ++r)
-                        tma_bulk_g2s(raw + (size_t)r * G.aux.row_floats * 4, src + r * G.aux.row_stride,
-                                     (uint32_t)G.aux.row_floats * 4u, &P.tma_bar[s]);
-                }
-            }
+        const uint32_t tile = (uint32_t)G.mat.rows_pad * kTileRowBytes;
+        for (int c = 0; c < G.k_chunks; ++c, P.advance()) {
+            const uint32_t s = P.sm;
+            if (P.g >= P.nm) pipe_wait(P, &P.mat_empty[s], P.pm ^ 1u, DERR_TIMEOUT_MMA);
+            char* slot = P.mat_slots + (size_t)s * P.mat_bytes;
+            const float* src = G.mat.ptr + (long long)c * G.mat.chunk_floats;
+            mbar_arrive_expect_tx(&P.mat_full[s], 2 * tile);
+            tma_bulk_g2s(slot, src, 2 * tile, &P.mat_full[s]);
         }
     }
-    P.g = g;
 }
 
 // Kernel prologue/epilogue: carve shared memory, init barriers, allocate TMEM.
@@ -215,18 +240,21 @@ struct CtaRes {
     uint32_t tmem;
 };
 
-__device__ __forceinline__ CtaRes cta_begin(char* smem_raw, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
-                                            uint32_t tmem_cols, int* err) {
+__device__ __forceinline__ CtaRes cta_begin(char* smem_raw, const TcShape& rs, int* err) {
+    const uint32_t tmem_cols = rs.tmem_cols;
     const uint32_t base = smem_u32(smem_raw);
-    char* smem = smem_raw + (((base + 127u) & ~127u) - base);   // 128-byte aligned ring
+    char* smem = smem_raw + (((base + 127u) & ~127u) - base);   // 128-byte aligned rings
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 3 * kMaxStages * sizeof(uint64_t));
-    int* aborted = reinterpret_cast<int*>(smem + 3 * kMaxStages * sizeof(uint64_t) + 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * (kMaxMat + kMaxData) * sizeof(uint64_t));
+    int* aborted = reinterpret_cast<int*>(tslot + 4);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kMaxStages; ++s) {
-            mbar_init(&bars[s], 1);                          // tma_bar
-            mbar_init(&bars[kMaxStages + s], 1);             // mma_bar
-            mbar_init(&bars[2 * kMaxStages + s], kThreads / 32);   // data_bar
+        for (int s = 0; s < kMaxMat; ++s) {
+            mbar_init(&bars[s], 1);                          // mat_full: the TMA thread's expect_tx
+            mbar_init(&bars[kMaxMat + s], 1);                // mat_empty: tcgen05.commit
+        }
+        for (int s = 0; s < kMaxData; ++s) {
+            mbar_init(&bars[2 * kMaxMat + s], kThreads / 32);          // data_full: producer warps
+            mbar_init(&bars[2 * kMaxMat + kMaxData + s], 1);           // data_empty: tcgen05.commit
         }
         *aborted = 0;
         fence_mbar_init();
@@ -239,14 +267,17 @@ __device__ __forceinline__ CtaRes cta_begin(char* smem_raw, uint32_t stage_bytes
     __syncthreads();
     tc_fence_after();
     CtaRes r;
-    r.P.tma_bar = bars;
-    r.P.mma_bar = bars + kMaxStages;
-    r.P.data_bar = bars + 2 * kMaxStages;
-    r.P.nst = nst;
-    r.P.raw_bytes = raw_bytes;
-    r.P.stages = smem + kHeaderBytes;
-    r.P.stage_bytes = stage_bytes;
-    r.P.g = 0;
+    r.P.mat_full = bars;
+    r.P.mat_empty = bars + kMaxMat;
+    r.P.data_full = bars + 2 * kMaxMat;
+    r.P.data_empty = bars + 2 * kMaxMat + kMaxData;
+    r.P.mat_slots = smem + kHeaderBytes;
+    r.P.data_slots = r.P.mat_slots + (size_t)rs.nm * rs.mat_bytes;
+    r.P.mat_bytes = rs.mat_bytes;
+    r.P.data_bytes = rs.data_bytes;
+    r.P.nm = rs.nm;
+    r.P.nd = rs.nd;
+    r.P.g = r.P.sd = r.P.pd = r.P.sm = r.P.pm = 0;
     r.P.err = err;
     r.P.aborted = aborted;
     r.tmem = *tslot;
@@ -391,15 +422,15 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
 // ------------------------------------------------------------------------------
 // mode-3 pass: rows = 128 consecutive points of the padded (i, j) plane
 // (row index j * n1q + i), columns = the k fibre; reads F from Y and overwrites
-// the same entries with the result.  The TMA warp stages every chunk's F rows
-// (16 k-planes x 128 points) and, for the ball, the Phi rows next to the
-// matrix chunk, so the producers read shared memory only.
+// the same entries with the result.  Each producer thread loads the eight F
+// values (and, for the ball, Phi values) of its row and columns two chunks
+// ahead of use.
 template <int GEO>
 __global__ void __launch_bounds__(kBlock, 1)
-    k_tc_mode3(SplitTables T, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
-                                              uint32_t tmem_cols) {
+    k_tc_mode3(SplitTables T, TcShape sh) {
     extern __shared__ char smem_raw[];
-    CtaRes R = cta_begin(smem_raw, stage_bytes, nst, raw_bytes, tmem_cols, T.err);
+    const uint32_t tmem_cols = sh.tmem_cols;
+    CtaRes R = cta_begin(smem_raw, sh, T.err);
     const int s = blockIdx.y;
     const int n3 = T.n3, n1q = T.n1q;
     const int n3p = (n3 + 15) & ~15;
@@ -407,10 +438,8 @@ __global__ void __launch_bounds__(kBlock, 1)
     const long long row0 = (long long)blockIdx.x * kRows;
     const int tile_rows = (int)(plane - row0 < kRows ? plane - row0 : kRows);
     float* Ys = T.Y + (long long)s * T.ys;
-    GemmSpec gs[2] = {{GEO == GEO_BALL ? T.M3a : T.M3b[s], 0, kRows, 1, n3p, n3p / kKC, R.tmem,
-                       AuxCopy{Ys + row0, plane, tile_rows, n3}},
-                      {T.M3b[0], 0, kRows, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p,
-                       AuxCopy{T.had_phi + (long long)s * n3 * n1q, n1q, n1q, n3}}};
+    GemmSpec gs[2] = {{GEO == GEO_BALL ? T.M3a : T.M3b[s], 0, kRows, 1, n3p, n3p / kKC, R.tmem},
+                      {T.M3b[0], 0, kRows, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p}};
     if (threadIdx.x >= kThreads + 32) {
         mma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);
     } else if (threadIdx.x >= kThreads) {
@@ -421,27 +450,36 @@ __global__ void __launch_bounds__(kBlock, 1)
         const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
         const bool valid = r < tile_rows;
         const int i = (int)((row0 + r) % n1q);
-        run_gemm(R.P, gs[0], [&](int c, char* hi, char* lo, const float* raw) {
-            float v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int kk = h * 8 + q;
-                v[q] = (valid && c * 16 + kk < n3) ? raw[kk * tile_rows + r] : 0.f;
-            }
-            store_row8(hi, lo, r, h, v);
-        });
-        uint32_t last = 0;
-        if constexpr (GEO == GEO_BALL) {
-            run_gemm(R.P, gs[1], [&](int c, char* hi, char* lo, const float* raw) {
-                float v[8];
-                tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+        const float* Yr = Ys + row0 + r;
+        run_gemm(
+            R.P, gs[0],
+            [&](int c, Pre8& p) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int kk = h * 8 + q;
-                    v[q] = (valid && c * 16 + kk < n3) ? v[q] * raw[kk * n1q + i] : 0.f;
+                    const int k = c * 16 + h * 8 + q;
+                    p.v[q] = (valid && k < n3) ? __ldg(Yr + k * plane) : 0.f;
                 }
-                store_row8(hi, lo, r, h, v);
-            });
+            },
+            [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
+        uint32_t last = 0;
+        if constexpr (GEO == GEO_BALL) {
+            const float* hp = T.had_phi + (long long)s * n3 * n1q + i;
+            run_gemm(
+                R.P, gs[1],
+                [&](int c, Pre8& p) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int k = c * 16 + h * 8 + q;
+                        p.v[q] = (valid && k < n3) ? __ldg(hp + (long long)k * n1q) : 0.f;
+                    }
+                },
+                [&](int c, char* hi, char* lo, const Pre8& p) {
+                    float v[8];
+                    tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
+                    store_row8(hi, lo, r, h, v);
+                });
             last = (uint32_t)n3p;
         }
         for (int c = 0; c < n3p / 16; ++c) {
@@ -479,9 +517,9 @@ __device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, uint
     cols[0] = 0;
     cols[1] = T - (uint32_t)(m2 * n1p);
     cols[2] = 0;
-    gs[0] = GemmSpec{J.QT, 0, kRows, 1, n2p, n2p / kKC, tmem + cols[0], AuxCopy{J.Y, J.n1q, J.n1q, J.n2}};
-    gs[1] = GemmSpec{J.Q, 1, n1p, m2, n1p, n2p / kKC, tmem + cols[1], AuxCopy{J.had, J.n1q, J.n1q, J.n2}};
-    gs[2] = GemmSpec{J.P, 0, kRows * m2, m2, n1p, n1p / kKC, tmem + cols[2], AuxCopy{nullptr, 0, 0, 0}};
+    gs[0] = GemmSpec{J.QT, 0, kRows, 1, n2p, n2p / kKC, tmem + cols[0]};
+    gs[1] = GemmSpec{J.Q, 1, n1p, m2, n1p, n2p / kKC, tmem + cols[1]};
+    gs[2] = GemmSpec{J.P, 0, kRows * m2, m2, n1p, n1p / kKC, tmem + cols[2]};
 }
 
 // F of one disk species at (i, j0 + q), q < 8, from FP64-accurate differences of
@@ -539,38 +577,38 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
 
     // G1: X[i][j'] = sum_j Y[i][j] Q[j][j']          (Y x_2 Q_theta^T), rows i
     const int n1q = J.n1q;
+    // eight values of row r, columns 16c + 8h + q, of a [j][n1q] table, 0 outside the slab
+    auto load_rows = [&](const float* base) {
+        return [=](int c, Pre8& p) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = c * 16 + h * 8 + q;
+                p.v[q] = (r < n1 && j < n2) ? __ldg(base + (long long)j * n1q + r) : 0.f;
+            }
+        };
+    };
     if (BI) {
-        run_gemm(P, gs[0], [&](int c, char* hi, char* lo, const float*) {
+        run_gemm(P, gs[0], [&](int c, char* hi, char* lo, const Pre8&) {
             float v[8];
             disk_F8(*BI, inst_base, species, r, c * 16 + h * 8, v);
             store_row8(hi, lo, r, h, v);
         });
     } else {
-        run_gemm(P, gs[0], [&](int c, char* hi, char* lo, const float* raw) {
-            float v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int jl = h * 8 + q;
-                v[q] = (r < n1 && c * 16 + jl < n2) ? raw[jl * n1q + r] : 0.f;
-            }
-            store_row8(hi, lo, r, h, v);
-        });
+        run_gemm(P, gs[0], load_rows(J.Y),
+                 [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
     }
     // G2: Z^T[j][i] = sum_j' Q[j][j'] (Phi o X)[i][j']   (x_2 Q_theta), data in B, rows j
-    run_gemm(P, gs[1], [&](int c, char* hi, char* lo, const float* raw) {
+    run_gemm(P, gs[1], load_rows(J.had), [&](int c, char* hi, char* lo, const Pre8& p) {
         float v[8];
         tmem_ld8(tmem + lane_base + c1 + (uint32_t)(c * 16 + h * 8), v);
         if (r < n1p) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int jl = h * 8 + q;
-                v[q] = (r < n1 && c * 16 + jl < n2) ? v[q] * raw[jl * n1q + r] : 0.f;
-            }
+            for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
             store_row8(hi, lo, r, h, v);
         }
     });
     // G3: R^T[j][i'] = sum_i Z^T[j][i] P[i'][i]      (x_1 phi_1(tau d A_rho)), rows j
-    run_gemm(P, gs[2], [&](int c, char* hi, char* lo, const float*) {
+    run_gemm(P, gs[2], [&](int c, char* hi, char* lo, const Pre8&) {
         for (int mt = 0; mt < m2; ++mt) {
             float v[8];
             tmem_ld8(tmem + lane_base + c2 + (uint32_t)(mt * n1p + c * 16 + h * 8), v);
@@ -621,10 +659,10 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
 }
 
 __global__ void __launch_bounds__(kBlock, 1)
-    k_tc_slab(SplitTables T, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
-                                              uint32_t tmem_cols) {
+    k_tc_slab(SplitTables T, TcShape sh) {
     extern __shared__ char smem_raw[];
-    CtaRes R = cta_begin(smem_raw, stage_bytes, nst, raw_bytes, tmem_cols, T.err);
+    const uint32_t tmem_cols = sh.tmem_cols;
+    CtaRes R = cta_begin(smem_raw, sh, T.err);
     const int k = blockIdx.x, s = blockIdx.y;
     const long long n12 = (long long)T.n1 * T.n2;
     const long long plane = (long long)T.n2 * T.n1q;
@@ -646,7 +684,7 @@ __global__ void __launch_bounds__(kBlock, 1)
     slab_specs(J, R.tmem, tmem_cols, gs, cols);
     if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
     else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
-    else slab_compute(J, gs, cols, R.P, R.tmem, R.P.stages);
+    else slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
     cta_end(R, tmem_cols);
 }
 
@@ -656,11 +694,11 @@ __global__ void __launch_bounds__(kBlock, 1)
 // F from the previous state, x_2 Q_theta^T, Hadamard, x_2 Q_theta, x_1
 // phi_1(tau d A_rho) -- writing the updated species into the other state buffer.
 __global__ void __launch_bounds__(kBlock, 1)
-    k_tc_batch(BatchTables B, uint32_t stage_bytes, uint32_t nst, uint32_t raw_bytes,
-                                              uint32_t tmem_cols) {
+    k_tc_batch(BatchTables B, TcShape sh) {
     extern __shared__ char smem_raw[];
     __shared__ int s_item;
-    CtaRes R = cta_begin(smem_raw, stage_bytes, nst, raw_bytes, tmem_cols, B.err);
+    const uint32_t tmem_cols = sh.tmem_cols;
+    CtaRes R = cta_begin(smem_raw, sh, B.err);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(B.counter, 1);
         tc_fence_before();
@@ -691,7 +729,7 @@ __global__ void __launch_bounds__(kBlock, 1)
         slab_specs(J, R.tmem, tmem_cols, gs, cols);
         if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
         else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
-        else slab_compute(J, gs, cols, R.P, R.tmem, R.P.stages, &I, B.W_in + I.w_off, s);
+        else slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots, &I, B.W_in + I.w_off, s);
     }
     cta_end(R, tmem_cols);
 }
@@ -707,15 +745,34 @@ static uint32_t pow2_cols(uint32_t c) {
     return p;
 }
 
-// Stage-ring depth and shared-memory size: three stages when two CTAs still fit
-// on one SM (228 KB per SM, 1 KB reserved per CTA), else two.
-static void ring(TcShape& sh, uint32_t min_body) {
-    const uint32_t pair_limit = 228 * 1024 / 2 - 1024 - 128;   // 128: alignment slack of the ring
-    sh.nst = 3;
-    if (kHeaderBytes + 3 * sh.stage_bytes > pair_limit && kHeaderBytes + 2 * sh.stage_bytes >= min_body) sh.nst = 2;
-    uint32_t body = sh.nst * sh.stage_bytes;
+// Ring depths and shared-memory size.  With `pair`, the rings are sized so
+// that two CTAs share an SM (228 KB per SM, 1 KB reserved per CTA): three data
+// slots and as many matrix slots (up to kMaxMat) as fit, fewer data slots only
+// if three matrix slots would not fit; otherwise (or if even two and two do not
+// fit) one CTA takes the SM's 227 KB.
+static void rings(TcShape& sh, uint32_t min_body, bool pair) {
+    const uint32_t slack = 128 + kHeaderBytes;                 // ring alignment + barriers
+    const uint32_t pair_limit = 228 * 1024 / 2 - 1024 - slack;
+    const uint32_t solo_limit = 227 * 1024 - slack;
+    auto fit = [&](uint32_t limit) {
+        for (uint32_t nd = 3; nd >= 2; --nd) {
+            if (nd * sh.data_bytes >= limit) continue;
+            uint32_t nm = (limit - nd * sh.data_bytes) / sh.mat_bytes;
+            nm = nm > (uint32_t)kMaxMat ? (uint32_t)kMaxMat : nm;
+            if (nm >= 3 || (nd == 2 && nm >= 2)) {
+                sh.nd = nd;
+                sh.nm = nm;
+                return true;
+            }
+        }
+        return false;
+    };
+    if (!(pair && fit(pair_limit)) && !fit(solo_limit)) {
+        sh.nd = sh.nm = 2;                                     // reported as too large by the caller
+    }
+    uint32_t body = sh.nm * sh.mat_bytes + sh.nd * sh.data_bytes;
     if (body < min_body) body = min_body;
-    sh.smem_bytes = 128 + kHeaderBytes + body;
+    sh.smem_bytes = slack + body;
 }
 
 TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3) {
@@ -723,10 +780,10 @@ TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3) {
     (void)n2;
     TcShape sh{};
     const uint32_t n3p = round_up(n3, 16);
-    sh.raw_bytes = raw_bytes_for(kRows);
-    sh.stage_bytes = round_up(2u * kRows * kTileRowBytes + 2u * n3p * kTileRowBytes + sh.raw_bytes, 128);
+    sh.data_bytes = 2u * kRows * kTileRowBytes;
+    sh.mat_bytes = 2u * n3p * kTileRowBytes;
     sh.tmem_cols = pow2_cols(geometry == GEO_BALL ? 2 * n3p : n3p);
-    ring(sh, 0);
+    rings(sh, 0, true);
     return sh;
 }
 
@@ -738,21 +795,22 @@ uint32_t slab_tmem_cols(int n1, int n2) {
     return pow2_cols(need);
 }
 
-TcShape tc_slab_shape(int n1, int n2) {
+// Slots of the three slab products: matrix rows n2p (G1), 128 m2 (G2, A operand),
+// n1p (G3); data rows 128 (G1), n1p (G2, B operand), 128 m2 (G3).
+static TcShape slab_shape(int n1, int n2, bool pair) {
     TcShape sh{};
     const uint32_t n1p = round_up(n1, 16), n2p = round_up(n2, 16), m2 = (n2 + 127) / 128;
-    const uint32_t rows1 = kRows + n2p;                 // G1: data 128 rows, matrix n2p rows
-    const uint32_t rows2 = n1p + kRows * m2;            // G2: data n1p rows, matrix 128 m2 rows
-    const uint32_t rows3 = kRows * m2 + n1p;            // G3
-    uint32_t rows = rows1 > rows2 ? rows1 : rows2;
-    rows = rows > rows3 ? rows : rows3;
-    sh.raw_bytes = raw_bytes_for((int)round_up(n1, 4));
-    sh.stage_bytes = round_up(2u * rows * kTileRowBytes + sh.raw_bytes, 128);
-    const uint32_t epi = kRows * (n1p + 1) * 4u;       // epilogue staging reuses the ring
+    const uint32_t mat_rows = std::max(std::max(n2p, kRows * m2), n1p);
+    const uint32_t data_rows = std::max(kRows * m2, n1p);
+    sh.mat_bytes = 2u * mat_rows * kTileRowBytes;
+    sh.data_bytes = 2u * data_rows * kTileRowBytes;
+    const uint32_t epi = kRows * (n1p + 1) * 4u;       // epilogue staging reuses the rings
     sh.tmem_cols = slab_tmem_cols(n1, n2);
-    ring(sh, epi);
+    rings(sh, epi, pair);
     return sh;
 }
+
+TcShape tc_slab_shape(int n1, int n2) { return slab_shape(n1, n2, true); }
 
 cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     cudaError_t e = cudaSuccess;
@@ -776,15 +834,15 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid((unsigned)((T.n1q * (long long)T.n2 + kRows - 1) / kRows), T.S);
     if (T.geometry == GEO_BALL)
-        k_tc_mode3<GEO_BALL><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
+        k_tc_mode3<GEO_BALL><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
     else
-        k_tc_mode3<GEO_CYLINDER><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
+        k_tc_mode3<GEO_CYLINDER><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid(T.geometry == GEO_DISK ? 1 : T.n3, T.S);
-    k_tc_slab<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
+    k_tc_slab<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
     return cudaGetLastError();
 }
 
@@ -824,7 +882,7 @@ static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
 }
 
 TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols) {
-    TcShape sh = tc_slab_shape(max_n1, max_n2);
+    TcShape sh = slab_shape(max_n1, max_n2, false);        // one persistent CTA per SM
     sh.tmem_cols = std::max(sh.tmem_cols, tmem_cols);
     return sh;
 }
@@ -836,7 +894,7 @@ cudaError_t tc_prepare_batch(uint32_t smem) {
 cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(B.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_tc_batch<<<152, kBlock, sh.smem_bytes, st>>>(B, sh.stage_bytes, sh.nst, sh.raw_bytes, sh.tmem_cols);
+    k_tc_batch<<<152, kBlock, sh.smem_bytes, st>>>(B, sh);
     return cudaGetLastError();
 }
 

@@ -19,12 +19,13 @@ cudaError_t launch_wdot(const double* a, const double* b, const double* wt, long
 cudaError_t launch_scale(double* x, double a, long long n, cudaStream_t st);
 
 // Split-TF32 tensor-core path.
+// Shared-memory rings and tensor-memory columns of a tensor-core kernel.
 struct TcShape {
-    uint32_t stage_bytes;
+    uint32_t mat_bytes;    // bytes per matrix slot (hi + lo tiles of the widest product)
+    uint32_t data_bytes;   // bytes per data slot
+    uint32_t nm, nd;       // slots in the matrix and data rings
     uint32_t tmem_cols;
     uint32_t smem_bytes;
-    uint32_t nst;          // stages in the ring
-    uint32_t raw_bytes;    // staged-row region at the end of every stage
 };
 TcShape tc_mode3_shape(int geometry, int n1, int n2, int n3);
 TcShape tc_slab_shape(int n1, int n2);

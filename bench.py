@@ -322,7 +322,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": list(n), "species": S, "dof": dof, "tau": w["tau"],
                    "precision": "split_tf32", "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "tuned": {"stencil_tile_j": info["stencil_tile_j"], "ring_slots": info["ring_slots"]}},
         "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": 1e3 * fp64_s / args.fp64_steps,
                  "steps": args.fp64_steps, "kernel_ms": kms64},
         "speedup_split_over_fp64": value / fp64_value,

@@ -98,6 +98,9 @@ typedef struct {
     int64_t state_elems;        /* FP64 elements of the whole state                         */
     int64_t workspace_bytes;    /* device bytes owned by the plan                           */
     double setup_ms;            /* host wall time of the FP64 setup                         */
+    int32_t stencil_tile_j;     /* split path: j-lines per stencil tile (measured at setup)  */
+    int32_t ring_slots[2];      /* split path: matrix and data slots of the slab pass ring   */
+    float stencil_tile_us;      /* split path: measured stencil time at that tile height     */
 } sexpe_plan_info;
 
 /* Build a plan: FP64 host setup of the 1-D axes (Section 3: eqs. A_theta,

@@ -48,7 +48,9 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("geometry", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_species", ctypes.c_int32),
                 ("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("n_instances", ctypes.c_int32),
                 ("kernels_per_step", ctypes.c_int32), ("npts", ctypes.c_int64), ("state_elems", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
+                ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
+                ("stencil_tile_j", ctypes.c_int32), ("ring_slots", ctypes.c_int32 * 2),
+                ("stencil_tile_us", ctypes.c_float)]
 
 
 _lib = None
@@ -158,7 +160,7 @@ class Plan:
     def info(self):
         inf = PlanInfo()
         _check(lib().sexpe_plan_get_info(self.handle, ctypes.byref(inf)), "sexpe_plan_get_info")
-        return {f: (list(getattr(inf, f)) if f == "n" else getattr(inf, f)) for f, _ in PlanInfo._fields_}
+        return {f: (list(getattr(inf, f)) if f in ("n", "ring_slots") else getattr(inf, f)) for f, _ in PlanInfo._fields_}
 
     def step(self, state, n_steps, stream=None):
         _check(lib().sexpe_step(self.handle, _data_ptr(state), int(n_steps), _stream_ptr(stream)), "sexpe_step")

@@ -97,6 +97,7 @@ struct SplitTables {
     Image M3a, M3b[kMaxSpecies];   // ball: Vinv (M3a) and V (M3b[0]); cylinder: Pz_s in M3b[s]
     const float* had_phi;          // ball: Phi table of the phi direction, [s][k'][n1q]
     int* err;
+    int rhs_tj;                    // j-lines per stencil tile (chosen by measurement at setup; 0 = model)
 };
 
 // ---------------- batched independent disks (split-TF32) -------------------

@@ -310,7 +310,14 @@ __device__ __forceinline__ float sdiff(float2 a, float2 b) { return (a.x - b.x) 
 
 constexpr int kTileBatch = 8;   // global loads in flight per thread while filling the tile
 
-constexpr int kRhsThreads = 512;   // 128 lanes along rho x 4 line parities
+constexpr int kRhsThreads = 512;   // threads of a stencil CTA, spread over (line, i) items
+
+// floor(q / d) by a multiply-high with m = floor(2^32 / d) + 1: q m / 2^32 lies in
+// [q/d, q/d + q/2^32], and the excess cannot reach the next integer while
+// q < 2^20 and d < 2^12 (the fractional part of q/d is at most 1 - 1/d).  For
+// d = 1 the multiplier does not fit in 32 bits; it is encoded as 0.
+__host__ __device__ constexpr uint32_t div_magic(uint32_t d) { return d == 1 ? 0u : (uint32_t)((1ull << 32) / d + 1); }
+__device__ __forceinline__ int div_by(int q, uint32_t m) { return m ? (int)__umulhi((uint32_t)q, m) : q; }
 
 template <int GEO>
 __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, const double* __restrict__ Wall,
@@ -325,8 +332,7 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
     const int rows = S * nK * nJ;
     const long long npts = tb.npts;
     const long long n12 = (long long)n1 * n2;
-    constexpr int NP = kRhsThreads / 128;            // line parities
-    const int lane = threadIdx.x & 127, rpar = threadIdx.x >> 7;
+    const uint32_t m_n1 = div_magic((uint32_t)n1), m_tj = div_magic((uint32_t)TJ);
     for (int row = threadIdx.x; row < rows; row += blockDim.x) {
         const int jj = row % nJ, kk = (row / nJ) % nK, sp = row / (nJ * nK);
         int j = j0 - 1 + jj;
@@ -336,20 +342,21 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
         row_off[row] = ok ? sp * npts + (long long)k * n12 + (long long)j * n1 : -1;
     }
     __syncthreads();
-    for (int row0 = rpar; row0 < rows; row0 += NP * kTileBatch) {
-        for (int i = lane; i < n1; i += 128) {
-            double v[kTileBatch];
+    // tile fill: (row, i) items over all threads, kTileBatch loads in flight per thread
+    const int items = rows * n1;
+    for (int q0 = threadIdx.x; q0 < items; q0 += kRhsThreads * kTileBatch) {
+        double v[kTileBatch];
 #pragma unroll
-            for (int u = 0; u < kTileBatch; ++u) {
-                const int row = row0 + NP * u;
-                const long long off = row < rows ? row_off[row] : -1;
-                v[u] = off >= 0 ? __ldg(Wall + off + i) : 0.0;
-            }
+        for (int u = 0; u < kTileBatch; ++u) {
+            const int q = q0 + u * kRhsThreads;
+            const int row = div_by(q, m_n1);
+            const long long off = q < items ? row_off[row] : -1;
+            v[u] = off >= 0 ? __ldg(Wall + off + (q - row * n1)) : 0.0;
+        }
 #pragma unroll
-            for (int u = 0; u < kTileBatch; ++u) {
-                const int row = row0 + NP * u;
-                if (row < rows) tile[row * n1 + i] = split_f64(v[u]);
-            }
+        for (int u = 0; u < kTileBatch; ++u) {
+            const int q = q0 + u * kRhsThreads;
+            if (q < items) tile[q] = split_f64(v[u]);
         }
     }
     if (threadIdx.x < TJ) {
@@ -367,54 +374,57 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
         ck[3][t] = (GEO == GEO_BALL) ? tb.Dp[k] : 1.f;
     }
     __syncthreads();
+    // stencil + reaction: (line, i) items over all threads, line = kl * TJ + jl
     const int species_stride = nK * nJ * n1;
-    for (int i = lane; i < n1; i += 128) {
-        const StencilAxis<float>& a1 = tb.ax[0];
-        const float lo1 = a1.lower[i], up1 = a1.upper[i], rs1 = a1.rs[i];
-        const float dr = (GEO == GEO_SPHERE) ? 1.f : tb.Dr[i];
+    const StencilAxis<float>& a1 = tb.ax[0];
+    const int total = TS::TK * TJ * n1;
+    for (int q = threadIdx.x; q < total; q += kRhsThreads) {
+        const int line = div_by(q, m_n1);
+        const int i = q - line * n1;
+        const int kl = TS::k3 ? div_by(line, m_tj) : 0;
+        const int jl = line - kl * TJ;
+        const int j = j0 + jl, k = k0 + kl;
+        if (j >= n2 || k >= n3) continue;
+        const float lo1 = __ldg(a1.lower + i), up1 = __ldg(a1.upper + i), rs1 = __ldg(a1.rs + i);
+        const float dr = (GEO == GEO_SPHERE) ? 1.f : __ldg(tb.Dr + i);
         const bool has_m = i > 0 || TS::periodic1, has_p = i < n1 - 1 || TS::periodic1;
-        const int im = i > 0 ? i - 1 : n1 - 1, ip = i < n1 - 1 ? i + 1 : 0;
-        for (int line = rpar; line < TS::TK * TJ; line += NP) {
-            const int kl = line / TJ, jl = line - kl * TJ;
-            const int j = j0 + jl, k = k0 + kl;
-            if (j >= n2 || k >= n3) continue;
-            const int cidx = ((kl + TS::KH) * nJ + (jl + 1)) * n1 + i;
-            float w[kMaxSpecies];
+        const int dm = i > 0 ? -1 : n1 - 1, dp = i < n1 - 1 ? 1 : 1 - n1;
+        const int cidx = ((kl + TS::KH) * nJ + (jl + 1)) * n1 + i;
+        float w[kMaxSpecies];
 #pragma unroll
-            for (int r = 0; r < kMaxSpecies; ++r) {
-                if (r < S) {
-                    const float2 c = tile[r * species_stride + cidx];
-                    w[r] = c.x + c.y;
-                } else {
-                    w[r] = 0.f;
-                }
+        for (int r = 0; r < kMaxSpecies; ++r) {
+            if (r < S) {
+                const float2 c = tile[r * species_stride + cidx];
+                w[r] = c.x + c.y;
+            } else {
+                w[r] = 0.f;
             }
-            const long long idx = (long long)k * n12 + (long long)j * n1 + i;
+        }
+        float* Fo = F + ((long long)k * n2 + j) * n1q + i;
 #pragma unroll
-            for (int s = 0; s < kMaxSpecies; ++s) {
-                if (s >= S) break;
-                const float2* row = tile + s * species_stride + cidx - i;
-                const float2 c = row[i];
-                float t0 = rs1 * (c.x + c.y);
-                if (has_m) t0 += lo1 * sdiff(row[im], c);
-                if (has_p) t0 += up1 * sdiff(row[ip], c);
-                float t1 = cj[0][jl] * (c.x + c.y);
-                if (j > 0 || TS::periodic2) t1 += cj[1][jl] * sdiff(row[i - n1], c);
-                if (j < n2 - 1 || TS::periodic2) t1 += cj[2][jl] * sdiff(row[i + n1], c);
-                float lap;
-                if constexpr (GEO == GEO_DISK) {
-                    lap = t0 + dr * t1;
-                } else if constexpr (GEO == GEO_SPHERE) {
-                    lap = tb.Dp[j] * t0 + t1;
-                } else {
-                    float t2 = ck[0][kl] * (c.x + c.y);
-                    if (k > 0) t2 += ck[1][kl] * sdiff(row[i - nJ * n1], c);
-                    if (k < n3 - 1) t2 += ck[2][kl] * sdiff(row[i + nJ * n1], c);
-                    if constexpr (GEO == GEO_BALL) lap = t0 + dr * (ck[3][kl] * t1 + t2);
-                    else lap = t0 + dr * t1 + t2;
-                }
-                F[s * ys + ((long long)k * n2 + j) * n1q + i] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
+        for (int s = 0; s < kMaxSpecies; ++s) {
+            if (s >= S) break;
+            const float2* pc = tile + s * species_stride + cidx;
+            const float2 c = pc[0];
+            float t0 = rs1 * (c.x + c.y);
+            if (has_m) t0 += lo1 * sdiff(pc[dm], c);
+            if (has_p) t0 += up1 * sdiff(pc[dp], c);
+            float t1 = cj[0][jl] * (c.x + c.y);
+            if (j > 0 || TS::periodic2) t1 += cj[1][jl] * sdiff(pc[-n1], c);
+            if (j < n2 - 1 || TS::periodic2) t1 += cj[2][jl] * sdiff(pc[n1], c);
+            float lap;
+            if constexpr (GEO == GEO_DISK) {
+                lap = t0 + dr * t1;
+            } else if constexpr (GEO == GEO_SPHERE) {
+                lap = tb.Dp[j] * t0 + t1;
+            } else {
+                float t2 = ck[0][kl] * (c.x + c.y);
+                if (k > 0) t2 += ck[1][kl] * sdiff(pc[-nJ * n1], c);
+                if (k < n3 - 1) t2 += ck[2][kl] * sdiff(pc[nJ * n1], c);
+                if constexpr (GEO == GEO_BALL) lap = t0 + dr * (ck[3][kl] * t1 + t2);
+                else lap = t0 + dr * t1 + t2;
             }
+            Fo[s * ys] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
         }
     }
 }
@@ -874,11 +884,22 @@ static int rhs_tile_tj(const SplitTables& T) {
 template <int GEO>
 static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
     using TS = TileShape<GEO>;
-    const int tj = rhs_tile_tj<GEO>(T);
+    if (T.n1 >= 4096) return cudaErrorInvalidValue;      // exactness bound of div_by
+    const int tj = T.rhs_tj > 0 ? T.rhs_tj : rhs_tile_tj<GEO>(T);
     const size_t smem = sizeof(float2) * (size_t)T.S * (TS::TK + 2 * TS::KH) * (tj + 2) * T.n1;
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + TS::TK - 1) / TS::TK, 1);
     k_rhs_tile<GEO><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, T.n1q, T.ys);
     return cudaGetLastError();
+}
+
+// Stencil tile heights whose all-species tile fits the 220 KB budget.
+int rhs_tile_candidates(const SplitTables& T, int* out, int max_out) {
+    const bool k3 = T.geometry == GEO_BALL || T.geometry == GEO_CYLINDER;
+    const size_t per_line = sizeof(float2) * (size_t)T.S * (k3 ? 10 : 1) * T.n1;
+    int n = 0;
+    for (int tj = 1; tj <= (k3 ? 16 : 32) && tj <= T.n2 && n < max_out; ++tj)
+        if (per_line * (tj + 2) + 8 * 1024 <= 220 * 1024) out[n++] = tj;
+    return n;
 }
 
 TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols) {

@@ -240,6 +240,57 @@ sexpe_status build_fp64(sexpe_plan* p, cudaStream_t st) {
     return SEXPE_OK;
 }
 
+// Measured choice of the stencil tile height (the autotuner of the split path):
+// every feasible height is timed with CUDA events -- one warm-up launch, then
+// three launches -- on a zeroed scratch state of the plan's shape, and the
+// fastest is kept.  The model in the launcher ranks heights by waves and halo
+// rows, but the halo's real cost (each halo line is loaded and split again)
+// and the overlap of co-resident CTAs are only known by running them.  Runs
+// once at setup, before any graph capture; the scratch state is freed here.
+static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
+    SplitTables T = p->tabs;
+    int cand[40];
+    const int nc = rhs_tile_candidates(T, cand, 40);
+    if (nc == 0) return SEXPE_EUNSUPPORTED;
+    double* scratch = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)p->S * p->npts;
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SEXPE_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sexpe_status rc = SEXPE_OK;
+    float best_ms = 1e30f;
+    int best = cand[0];
+    if (cudaMemsetAsync(scratch, 0, bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        rc = SEXPE_ECUDA;
+    } else {
+        T.state = scratch;
+        for (int c = 0; c < nc && rc == SEXPE_OK; ++c) {
+            T.rhs_tj = cand[c];
+            bool ok = launch_rhs_split(T, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_rhs_split(T, st) == cudaSuccess;
+            float ms = 0.f;
+            ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            if (!ok) rc = SEXPE_ECUDA;
+            else if (ms < best_ms) {
+                best_ms = ms;
+                best = cand[c];
+            }
+        }
+    }
+    if (rc != SEXPE_OK) cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    p->tabs.rhs_tj = best;
+    p->rhs_tj_us = best_ms * 1000.f / 3.f;
+    return rc;
+}
+
 sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     if (p->geometry == SEXPE_SPHERE) return SEXPE_EUNSUPPORTED;
     const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
@@ -317,7 +368,7 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     if (p->shs.tmem_cols > 512 || (p->ndim == 3 && p->sh3.tmem_cols > 512)) return SEXPE_EUNSUPPORTED;
     SX_CUDA(tc_prepare(p->ndim == 3 ? p->sh3.smem_bytes : 0, p->shs.smem_bytes));
     p->kernels_per_step = p->ndim == 3 ? 3 : 2;
-    return SEXPE_OK;
+    return tune_stencil(p, st);
 }
 
 // Mode-mu product of all species: out = X x_mu L (L row-major n_mu x n_mu,
@@ -981,6 +1032,15 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
     info->state_elems = p->batch ? (int64_t)p->inst_off.back() : (int64_t)p->S * p->npts;
     info->workspace_bytes = (int64_t)p->bytes;
     info->setup_ms = p->setup_ms;
+    if (!p->batch && p->precision == SEXPE_SPLIT_TF32) {
+        info->stencil_tile_j = p->tabs.rhs_tj;
+        info->ring_slots[0] = (int32_t)p->shs.nm;
+        info->ring_slots[1] = (int32_t)p->shs.nd;
+        info->stencil_tile_us = p->rhs_tj_us;
+    } else if (p->batch) {
+        info->ring_slots[0] = (int32_t)p->bsh.nm;
+        info->ring_slots[1] = (int32_t)p->bsh.nd;
+    }
     return SEXPE_OK;
 }
 

@@ -76,5 +76,6 @@ struct sexpe_plan {
     int bparity = 0;                          // steps enqueued in the current sexpe_step call, mod 2
     int kernels_per_step = 0;
     double setup_ms = 0.0;
+    float rhs_tj_us = 0.f;     // measured stencil time at the chosen tile height
 };
 

@@ -159,3 +159,15 @@ def test_unsupported_and_invalid_on_gpu():
                                 "split_tf32") == 5
     assert binding.setup_status("disk", (16, 300), [1.0, 2.0], "schnakenberg", [1, 2, 3], 1e-3,
                                 "split_tf32") == 5
+
+
+def test_plan_info_reports_measured_tile_choices():
+    """The split plan times every feasible stencil tile height at setup and keeps the fastest."""
+    from paper_2604_11558_gb300 import binding
+    for w in (ball((20, 24, 18)), disk((30, 40))):
+        plan = binding.Plan.from_workload(w, precision="split_tf32")
+        inf = plan.info()
+        plan.close()
+        assert 1 <= inf["stencil_tile_j"] <= min(32, w["n"][1])
+        assert inf["stencil_tile_us"] > 0
+        assert inf["ring_slots"][0] >= 2 and inf["ring_slots"][1] >= 2

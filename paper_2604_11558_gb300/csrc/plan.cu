@@ -788,32 +788,65 @@ sexpe_status build_adjoint(sexpe_plan* p, cudaStream_t st) {
     return SEXPE_OK;
 }
 
+// Forward chain of the FP64 step at state W: X[0] = F, then every direction in
+// order -- X[q] its input, H[q] = Phi o (V^{-1} X[q]) for a direction in an
+// eigenbasis, X[q + 1] its output.  With `upd`, the last direction's output is
+// added (times tau) to upd, which completes the step when upd == W; without it
+// the chain stops once every quantity the adjoint step reads is formed (the
+// last direction's input, and its H for an eigen direction).
+sexpe_status forward_chain(sexpe_plan* p, const double* W, double* const* X, double* const* H, double* upd,
+                           cudaStream_t st) {
+    SX_CUDA(launch_rhs64(p->geometry, p->rhs64, W, X[0], st));
+    const int nd = (int)p->dirs64.size();
+    for (int q = 0; q < nd; ++q) {
+        const Dir64& d = p->dirs64[q];
+        const long long nmu = p->n[d.mu - 1];
+        const bool last = q + 1 == nd;
+        if (last && !upd && !d.eigen) break;
+        if (d.eigen) {
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.Vinv, 0, X[q], H[q], d.had, nullptr), p->S, st));
+            if (!last || upd)
+                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.V, 0, H[q], last ? nullptr : X[q + 1], nullptr,
+                                                last ? upd : nullptr), p->S, st));
+        } else {
+            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.P, nmu * nmu, X[q], last ? nullptr : X[q + 1], nullptr,
+                                            last ? upd : nullptr), p->S, st));
+        }
+    }
+    return SEXPE_OK;
+}
+
+// Buffers of one step's saved forward chain: nd inputs X[q], then one H per
+// eigen direction (indexed by direction; unused entries left null).
+int saved_slots(const sexpe_plan* p) {
+    int n = (int)p->dirs64.size();
+    for (const Dir64& d : p->dirs64) n += d.eigen ? 1 : 0;
+    return n;
+}
+
+void chain_views(const sexpe_plan* p, double* base, size_t E, double** X, double** H) {
+    const int nd = (int)p->dirs64.size();
+    int slot = 0;
+    for (int q = 0; q < nd; ++q) X[q] = base + (size_t)slot++ * E;
+    for (int q = 0; q < nd; ++q) H[q] = p->dirs64[q].eigen ? base + (size_t)slot++ * E : nullptr;
+}
+
 // One adjoint step: lam <- lam_n from lam_{n+1} at the state W_n, accumulating
-// the parameter gradient in p->adj_red.
-sexpe_status adjoint_step(sexpe_plan* p, const double* Wn, double* lam, cudaStream_t st) {
+// the parameter gradient in p->adj_red.  `saved` holds the forward chain at W_n
+// (from the replay of the checkpoint segment), or is null and the chain is
+// formed here.
+sexpe_status adjoint_step(sexpe_plan* p, const double* Wn, double* lam, double* saved, cudaStream_t st) {
     const size_t E = (size_t)p->S * p->npts;
     double* B = p->adj_buf;
-    double* X[4] = {B, B + E, B + 2 * E, B + 3 * E};     // X[q] = input of direction q (X[0] = F)
-    double* H[3] = {B + 4 * E, B + 5 * E, B + 6 * E};    // eigen: Phi o (V^{-1} X[q])
+    double* X[4];
+    double* H[4];
+    chain_views(p, saved ? saved : B, E, X, H);          // work buffers: slots 0..6 of adj_buf
     double* Y[2] = {B + 7 * E, B + 8 * E};
     double* HA = B + 9 * E;
     double* Z = B + 10 * E;
     double* MU = B + 11 * E;
     const int nd = (int)p->dirs64.size();
-    // forward chain at W_n, keeping every direction's input
-    SX_CUDA(launch_rhs64(p->geometry, p->rhs64, Wn, X[0], st));
-    for (int q = 0; q < nd; ++q) {
-        const Dir64& d = p->dirs64[q];
-        const long long nmu = p->n[d.mu - 1];
-        if (q + 1 == nd && !d.eigen) break;               // last plain direction: only its input is needed
-        if (d.eigen) {
-            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.Vinv, 0, X[q], H[q], d.had, nullptr), p->S, st));
-            if (q + 1 < nd)
-                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.V, 0, H[q], X[q + 1], nullptr, nullptr), p->S, st));
-        } else {
-            SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.P, nmu * nmu, X[q], X[q + 1], nullptr, nullptr), p->S, st));
-        }
-    }
+    if (!saved) SX_TRY(forward_chain(p, Wn, X, H, nullptr, st));
     // transposed chain: phi_1(tau d M_1)^T first, with the d-derivative terms
     double* acc_d = p->adj_red + 16;
     const double* y = lam;
@@ -1077,6 +1110,19 @@ sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_c
         p->adj_seg = seg;
         p->adj_seg_cap = every;
     }
+    // The replay of a segment keeps each step's forward chain, so the adjoint
+    // steps do not form it again; without room for it they do.
+    const int ns = saved_slots(p);
+    if (every > 1 && p->adj_save_cap < every) {
+        double* sv = nullptr;
+        if (alloc_dev(p, (size_t)(every - 1) * ns * E, &sv) == SEXPE_OK) {
+            p->adj_save = sv;
+            p->adj_save_cap = every;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    const bool keep = every > 1 && p->adj_save_cap >= every;
     double* lam = dL_dW0;                      // the adjoint variable lives in the output buffer
     if (lam != dL_dWT) SX_CUDA(cudaMemcpyAsync(lam, dL_dWT, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
     SX_CUDA(cudaMemsetAsync(p->adj_red, 0, 32 * sizeof(double), st));
@@ -1086,9 +1132,18 @@ sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_c
         for (int j = 1; j < every; ++j) {
             double* w = p->adj_seg + (size_t)j * E;
             SX_CUDA(cudaMemcpyAsync(w, w - E, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            SX_TRY(enqueue_step(p, w, st));
+            if (keep) {
+                double* X[4];
+                double* H[4];
+                chain_views(p, p->adj_save + (size_t)(j - 1) * ns * E, E, X, H);
+                SX_TRY(forward_chain(p, w, X, H, w, st));     // chain at W_{j-1}, then W_j in place
+            } else {
+                SX_TRY(enqueue_step(p, w, st));
+            }
         }
-        for (int j = every - 1; j >= 0; --j) SX_TRY(adjoint_step(p, p->adj_seg + (size_t)j * E, lam, st));
+        for (int j = every - 1; j >= 0; --j)
+            SX_TRY(adjoint_step(p, p->adj_seg + (size_t)j * E, lam,
+                                keep && j < every - 1 ? p->adj_save + (size_t)j * ns * E : nullptr, st));
     }
     if (dL_dparams) {
         double red[32];

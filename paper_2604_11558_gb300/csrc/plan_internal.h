@@ -62,9 +62,11 @@ struct sexpe_plan {
     // adjoint (FP64 plans; built on the first sexpe_adjoint call)
     std::vector<sexpe::DirAdj> adj;
     sexpe::RhsTables<double> adj_diag{};   // rs slot holds the full diagonal a_l for M^T
-    double* adj_buf = nullptr;              // work buffers, see adjoint.cu
+    double* adj_buf = nullptr;              // work buffers of adjoint_step (plan.cu)
     double* adj_seg = nullptr;              // recomputed states of one checkpoint segment
     int adj_seg_cap = 0;
+    double* adj_save = nullptr;             // forward chains of a segment's replayed steps
+    int adj_save_cap = 0;
     double* adj_red = nullptr;              // device accumulators of the parameter gradient
     // batched independent disks (sexpe_batch_setup)
     bool batch = false;

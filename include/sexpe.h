@@ -101,6 +101,9 @@ typedef struct {
     int32_t stencil_tile_j;     /* split path: j-lines per stencil tile (measured at setup)  */
     int32_t ring_slots[2];      /* split path: matrix and data slots of the slab pass ring   */
     float stencil_tile_us;      /* split path: measured stencil time at that tile height     */
+    int32_t stencil_planes;     /* split path: 0 = tiled stencil kernel, else k-planes per CTA
+                                   of the rolling-window kernel (measured at setup)          */
+    int32_t stencil_ctas_per_sm; /* split path: CTAs per SM the stencil's registers allow    */
 } sexpe_plan_info;
 
 /* Build a plan: FP64 host setup of the 1-D axes (Section 3: eqs. A_theta,
@@ -162,6 +165,17 @@ sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_s
 sexpe_status sexpe_synchronize(sexpe_plan* plan, void* stream);
 
 sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_host);
+
+/* Override the stencil configuration that sexpe_setup measured for a split
+ * plan (no counterpart in the paper: the tile shapes are this implementation's
+ * own): tile_j j-lines per CTA with planes = 0 and ctas_per_sm = 1 for the
+ * tiled kernel, or planes k-planes per CTA of the rolling-window kernel (3-D
+ * geometries) with its registers capped for ctas_per_sm (1 or 2) CTAs per SM.
+ * The triple must be one the setup timed (sexpe_plan_info reports the chosen one);
+ * others give SEXPE_EINVAL, FP64 and batch plans SEXPE_EUNSUPPORTED.  A graph
+ * captured by an earlier sexpe_step is dropped and captured again.  Host-side
+ * only; call it when no step of the plan is being enqueued by another thread. */
+sexpe_status sexpe_set_stencil(sexpe_plan* plan, int32_t tile_j, int32_t planes, int32_t ctas_per_sm);
 
 /* Free every device table of the plan (after synchronising its device). */
 sexpe_status sexpe_destroy(sexpe_plan* plan);

@@ -50,7 +50,8 @@ class PlanInfo(ctypes.Structure):
                 ("kernels_per_step", ctypes.c_int32), ("npts", ctypes.c_int64), ("state_elems", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
                 ("stencil_tile_j", ctypes.c_int32), ("ring_slots", ctypes.c_int32 * 2),
-                ("stencil_tile_us", ctypes.c_float)]
+                ("stencil_tile_us", ctypes.c_float), ("stencil_planes", ctypes.c_int32),
+                ("stencil_ctas_per_sm", ctypes.c_int32)]
 
 
 _lib = None
@@ -77,6 +78,7 @@ def lib():
         L.sexpe_step_noalloc.argtypes = [_P, _P, ctypes.c_int64, _P]
         L.sexpe_synchronize.argtypes = [_P, _P]
         L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
+        L.sexpe_set_stencil.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.sexpe_destroy.argtypes = [_P]
         L.sexpe_step_checkpointed.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
         L.sexpe_adjoint.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _DP, _P]
@@ -88,7 +90,7 @@ def lib():
         for name in ["sexpe_setup", "sexpe_batch_setup", "sexpe_state_offsets", "sexpe_step", "sexpe_step_host",
                      "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
                      "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
-                     "sexpe_step_checkpointed", "sexpe_adjoint",
+                     "sexpe_step_checkpointed", "sexpe_adjoint", "sexpe_set_stencil",
                      "sexpe_axis_phi1", "sexpe_axis_eigen"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
@@ -161,6 +163,10 @@ class Plan:
         inf = PlanInfo()
         _check(lib().sexpe_plan_get_info(self.handle, ctypes.byref(inf)), "sexpe_plan_get_info")
         return {f: (list(getattr(inf, f)) if f in ("n", "ring_slots") else getattr(inf, f)) for f, _ in PlanInfo._fields_}
+
+    def set_stencil(self, tile_j, planes=0, ctas_per_sm=1):
+        """sexpe_set_stencil: override the measured stencil configuration."""
+        _check(lib().sexpe_set_stencil(self.handle, int(tile_j), int(planes), int(ctas_per_sm)), "sexpe_set_stencil")
 
     def step(self, state, n_steps, stream=None):
         _check(lib().sexpe_step(self.handle, _data_ptr(state), int(n_steps), _stream_ptr(stream)), "sexpe_step")

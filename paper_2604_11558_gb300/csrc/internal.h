@@ -98,6 +98,8 @@ struct SplitTables {
     const float* had_phi;          // ball: Phi table of the phi direction, [s][k'][n1q]
     int* err;
     int rhs_tj;                    // j-lines per stencil tile (chosen by measurement at setup; 0 = model)
+    int rhs_ks;                    // 0: tiled stencil kernel; > 0: rolling-window kernel, planes per CTA
+    int rhs_mb;                    // rolling-window kernel: registers capped for this many CTAs per SM
 };
 
 // ---------------- batched independent disks (split-TF32) -------------------

@@ -312,6 +312,61 @@ constexpr int kTileBatch = 8;   // global loads in flight per thread while filli
 
 constexpr int kRhsThreads = 512;   // threads of a stencil CTA, spread over (line, i) items
 
+// Coefficients of the stencil at one point: axis 1 at i, axis 2 at j, axis 3 at k.
+struct PointCoef {
+    float lo1, up1, rs1, dr;     // A_rho row i (A_theta row i on the sphere), rho_i^-2
+    float rs2, lo2, up2;         // axis-2 row j
+    float rs3, lo3, up3, dp3;    // axis-3 row k, sin^-2 phi_k (ball)
+};
+
+// F of every species at one point from split (hi, lo) pairs in shared memory:
+// pc[s * ss] is the centre of species s; in-plane neighbours at -1/+1 (i, with
+// the periodic wrap dm/dp) and -/+ jstride (j); the k-neighbours at km/kp
+// (relative to pc).  Differences of pairs keep FP32 relative accuracy of the
+// difference (Section 2 Kronecker sums, applied in difference form).
+template <int GEO>
+__device__ __forceinline__ void rhs_point(const RhsTables<float>& tb, const float2* pc, int ss, int jstride,
+                                          long long km, long long kp, int dm, int dp, bool has_m, bool has_p,
+                                          bool has_jm, bool has_jp, bool has_km, bool has_kp, const PointCoef& cf,
+                                          float* Fo, long long ys, float dpj) {
+    const int S = tb.S;
+    float w[kMaxSpecies];
+#pragma unroll
+    for (int r = 0; r < kMaxSpecies; ++r) {
+        if (r < S) {
+            const float2 c = pc[r * ss];
+            w[r] = c.x + c.y;
+        } else {
+            w[r] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        if (s >= S) break;
+        const float2* q = pc + s * ss;
+        const float2 c = q[0];
+        float t0 = cf.rs1 * (c.x + c.y);
+        if (has_m) t0 += cf.lo1 * sdiff(q[dm], c);
+        if (has_p) t0 += cf.up1 * sdiff(q[dp], c);
+        float t1 = cf.rs2 * (c.x + c.y);
+        if (has_jm) t1 += cf.lo2 * sdiff(q[-jstride], c);
+        if (has_jp) t1 += cf.up2 * sdiff(q[jstride], c);
+        float lap;
+        if constexpr (GEO == GEO_DISK) {
+            lap = t0 + cf.dr * t1;
+        } else if constexpr (GEO == GEO_SPHERE) {
+            lap = dpj * t0 + t1;
+        } else {
+            float t2 = cf.rs3 * (c.x + c.y);
+            if (has_km) t2 += cf.lo3 * sdiff(q[km], c);
+            if (has_kp) t2 += cf.up3 * sdiff(q[kp], c);
+            if constexpr (GEO == GEO_BALL) lap = t0 + cf.dr * (cf.dp3 * t1 + t2);
+            else lap = t0 + cf.dr * t1 + t2;
+        }
+        Fo[s * ys] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
+    }
+}
+
 // floor(q / d) by a multiply-high with m = floor(2^32 / d) + 1: q m / 2^32 lies in
 // [q/d, q/d + q/2^32], and the excess cannot reach the next integer while
 // q < 2^20 and d < 2^12 (the fractional part of q/d is at most 1 - 1/d).  For
@@ -385,47 +440,120 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
         const int jl = line - kl * TJ;
         const int j = j0 + jl, k = k0 + kl;
         if (j >= n2 || k >= n3) continue;
-        const float lo1 = __ldg(a1.lower + i), up1 = __ldg(a1.upper + i), rs1 = __ldg(a1.rs + i);
-        const float dr = (GEO == GEO_SPHERE) ? 1.f : __ldg(tb.Dr + i);
-        const bool has_m = i > 0 || TS::periodic1, has_p = i < n1 - 1 || TS::periodic1;
-        const int dm = i > 0 ? -1 : n1 - 1, dp = i < n1 - 1 ? 1 : 1 - n1;
+        PointCoef cf;
+        cf.lo1 = __ldg(a1.lower + i);
+        cf.up1 = __ldg(a1.upper + i);
+        cf.rs1 = __ldg(a1.rs + i);
+        cf.dr = (GEO == GEO_SPHERE) ? 1.f : __ldg(tb.Dr + i);
+        cf.rs2 = cj[0][jl];
+        cf.lo2 = cj[1][jl];
+        cf.up2 = cj[2][jl];
+        if (TS::k3) {
+            cf.rs3 = ck[0][kl];
+            cf.lo3 = ck[1][kl];
+            cf.up3 = ck[2][kl];
+            cf.dp3 = ck[3][kl];
+        }
         const int cidx = ((kl + TS::KH) * nJ + (jl + 1)) * n1 + i;
-        float w[kMaxSpecies];
+        rhs_point<GEO>(tb, tile + cidx, species_stride, n1, -(long long)nJ * n1, (long long)nJ * n1,
+                       i > 0 ? -1 : n1 - 1, i < n1 - 1 ? 1 : 1 - n1, i > 0 || TS::periodic1,
+                       i < n1 - 1 || TS::periodic1, j > 0 || TS::periodic2, j < n2 - 1 || TS::periodic2, k > 0,
+                       k < n3 - 1, cf, F + ((long long)k * n2 + j) * n1q + i, ys,
+                       GEO == GEO_SPHERE ? tb.Dp[j] : 1.f);
+    }
+}
+
+// Stencil pass of the 3-D geometries as a rolling window along k: the CTA owns
+// TJ theta-lines x KS planes (all rho, all species) and keeps four planes
+// (k - 1, k, k + 1 and the one being filled) in a shared-memory ring.  The
+// loads of plane k + 2 are in flight in registers while plane k is computed,
+// so HBM latency overlaps the stencil work; each plane is split once.
+// RV = values per thread and plane (S (TJ + 2) n1 <= RV * 512); MINB = CTAs
+// per SM the registers are capped for (2: 64 registers, two CTAs' warps hide
+// each other's latency; 1: no cap, no spills).
+template <int GEO, int RV, int MINB>
+__global__ void __launch_bounds__(kRhsThreads, MINB) k_rhs_roll(RhsTables<float> tb, const double* __restrict__ Wall,
+                                                          float* __restrict__ F, int TJ, int KS, int n1q,
+                                                          long long ys) {
+    extern __shared__ float2 ring[];                 // [4][S][nJ][n1]
+    __shared__ float cj[3][32];
+    __shared__ long long line_off[kMaxSpecies * 34];   // offset of (species, j-line) within a plane, -1 outside
+    const int n1 = tb.n1, n2 = tb.n2, n3 = tb.n3, S = tb.S;
+    const int j0 = blockIdx.x * TJ, k0 = blockIdx.y * KS;
+    const int kend = min(k0 + KS, n3);
+    const int nJ = TJ + 2;
+    const int lines = S * nJ;
+    const int pv = lines * n1;                       // values per plane
+    const long long npts = tb.npts;
+    const long long n12 = (long long)n1 * n2;
+    const uint32_t m_n1 = div_magic((uint32_t)n1);
+    for (int l = threadIdx.x; l < lines; l += kRhsThreads) {
+        const int jj = l % nJ, sp = l / nJ;
+        int j = j0 - 1 + jj;
+        j = j < 0 ? j + n2 : (j >= n2 ? j - n2 : j);   // theta is periodic
+        line_off[l] = (j >= 0 && j < n2) ? sp * npts + (long long)j * n1 : -1;
+    }
+    if (threadIdx.x < TJ) {
+        const int j = min(j0 + (int)threadIdx.x, n2 - 1);
+        cj[0][threadIdx.x] = tb.ax[1].rs[j];
+        cj[1][threadIdx.x] = tb.ax[1].lower[j];
+        cj[2][threadIdx.x] = tb.ax[1].upper[j];
+    }
+    __syncthreads();
+    double v[RV];
+    auto load_plane = [&](int k) {
 #pragma unroll
-        for (int r = 0; r < kMaxSpecies; ++r) {
-            if (r < S) {
-                const float2 c = tile[r * species_stride + cidx];
-                w[r] = c.x + c.y;
-            } else {
-                w[r] = 0.f;
-            }
+        for (int u = 0; u < RV; ++u) {
+            const int q = threadIdx.x + u * kRhsThreads;
+            const int line = div_by(q, m_n1);
+            const long long off = (q < pv && k >= 0 && k < n3) ? line_off[line] : -1;
+            v[u] = off >= 0 ? __ldg(Wall + off + (long long)k * n12 + (q - line * n1)) : 0.0;
         }
-        float* Fo = F + ((long long)k * n2 + j) * n1q + i;
+    };
+    auto store_plane = [&](int k) {
+        float2* P = ring + (size_t)((k - k0 + 1) & 3) * pv;
 #pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) {
-            if (s >= S) break;
-            const float2* pc = tile + s * species_stride + cidx;
-            const float2 c = pc[0];
-            float t0 = rs1 * (c.x + c.y);
-            if (has_m) t0 += lo1 * sdiff(pc[dm], c);
-            if (has_p) t0 += up1 * sdiff(pc[dp], c);
-            float t1 = cj[0][jl] * (c.x + c.y);
-            if (j > 0 || TS::periodic2) t1 += cj[1][jl] * sdiff(pc[-n1], c);
-            if (j < n2 - 1 || TS::periodic2) t1 += cj[2][jl] * sdiff(pc[n1], c);
-            float lap;
-            if constexpr (GEO == GEO_DISK) {
-                lap = t0 + dr * t1;
-            } else if constexpr (GEO == GEO_SPHERE) {
-                lap = tb.Dp[j] * t0 + t1;
-            } else {
-                float t2 = ck[0][kl] * (c.x + c.y);
-                if (k > 0) t2 += ck[1][kl] * sdiff(pc[-nJ * n1], c);
-                if (k < n3 - 1) t2 += ck[2][kl] * sdiff(pc[nJ * n1], c);
-                if constexpr (GEO == GEO_BALL) lap = t0 + dr * (ck[3][kl] * t1 + t2);
-                else lap = t0 + dr * t1 + t2;
-            }
-            Fo[s * ys] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
+        for (int u = 0; u < RV; ++u) {
+            const int q = threadIdx.x + u * kRhsThreads;
+            if (q < pv) P[q] = split_f64(v[u]);
         }
+    };
+    load_plane(k0 - 1);
+    store_plane(k0 - 1);
+    load_plane(k0);
+    store_plane(k0);
+    load_plane(k0 + 1);
+    store_plane(k0 + 1);
+    __syncthreads();
+    const StencilAxis<float>& a1 = tb.ax[0];
+    const int total = TJ * n1;
+    for (int k = k0; k < kend; ++k) {
+        if (k + 2 <= kend) load_plane(k + 2);        // lands while plane k is computed
+        PointCoef cf;
+        cf.rs3 = tb.ax[2].rs[k];
+        cf.lo3 = tb.ax[2].lower[k];
+        cf.up3 = tb.ax[2].upper[k];
+        cf.dp3 = (GEO == GEO_BALL) ? tb.Dp[k] : 1.f;
+        const float2* Pc = ring + (size_t)((k - k0 + 1) & 3) * pv;
+        const long long km = (long long)(((k - k0) & 3) - ((k - k0 + 1) & 3)) * pv;
+        const long long kp = (long long)(((k - k0 + 2) & 3) - ((k - k0 + 1) & 3)) * pv;
+        for (int q = threadIdx.x; q < total; q += kRhsThreads) {
+            const int jl = div_by(q, m_n1);
+            const int i = q - jl * n1;
+            const int j = j0 + jl;
+            if (j >= n2) continue;
+            cf.lo1 = __ldg(a1.lower + i);
+            cf.up1 = __ldg(a1.upper + i);
+            cf.rs1 = __ldg(a1.rs + i);
+            cf.dr = __ldg(tb.Dr + i);
+            cf.rs2 = cj[0][jl];
+            cf.lo2 = cj[1][jl];
+            cf.up2 = cj[2][jl];
+            rhs_point<GEO>(tb, Pc + (jl + 1) * n1 + i, nJ * n1, n1, km, kp, -1, 1, i > 0, i < n1 - 1, true, true,
+                           k > 0, k < n3 - 1, cf, F + ((long long)k * n2 + j) * n1q + i, ys, 1.f);
+        }
+        if (k + 2 <= kend) store_plane(k + 2);       // slot of plane k - 2, free since the last barrier
+        __syncthreads();
     }
 }
 
@@ -838,6 +966,16 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_tile<GEO_SPHERE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_tile<GEO_BALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_tile<GEO_CYLINDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    const int ring = 4 * 8 * kRhsThreads * (int)sizeof(float2);    // four planes of at most 8 values per thread
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_BALL, 4, 1>, A, ring);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_BALL, 8, 1>, A, ring);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_BALL, 4, 2>, A, ring);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_BALL, 8, 2>, A, ring);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 4, 1>, A, ring);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 8, 1>, A, ring);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 4, 2>, A, ring);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 8, 2>, A, ring);
     return e;
 }
 
@@ -892,14 +1030,42 @@ static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Stencil tile heights whose all-species tile fits the 220 KB budget.
-int rhs_tile_candidates(const SplitTables& T, int* out, int max_out) {
+// Stencil configurations the autotuner times: (tile height, 0, 1) for the tiled
+// kernel whose all-species tile fits 220 KB, and, for the 3-D geometries,
+// (tile height, planes per CTA, register cap for 1 or 2 CTAs per SM) for the
+// rolling-window kernel whose plane holds at most 8 values per thread.
+int rhs_candidates(const SplitTables& T, int3* out, int max_out) {
     const bool k3 = T.geometry == GEO_BALL || T.geometry == GEO_CYLINDER;
     const size_t per_line = sizeof(float2) * (size_t)T.S * (k3 ? 10 : 1) * T.n1;
     int n = 0;
     for (int tj = 1; tj <= (k3 ? 16 : 32) && tj <= T.n2 && n < max_out; ++tj)
-        if (per_line * (tj + 2) + 8 * 1024 <= 220 * 1024) out[n++] = tj;
+        if (per_line * (tj + 2) + 8 * 1024 <= 220 * 1024) out[n++] = make_int3(tj, 0, 1);
+    if (k3) {
+        for (int tj = 2; tj <= 24 && tj <= T.n2 + 1; tj += 2) {
+            if ((long long)T.S * (tj + 2) * T.n1 > 8 * kRhsThreads) break;
+            for (int ks = 2; ks <= 16 && ks <= T.n3; ks *= 2)
+                for (int mb = 1; mb <= 2 && n < max_out; ++mb) out[n++] = make_int3(tj, ks, mb);
+        }
+    }
     return n;
+}
+
+template <int GEO>
+static cudaError_t launch_rhs_roll_geo(const SplitTables& T, cudaStream_t st) {
+    const int tj = T.rhs_tj, ks = T.rhs_ks;
+    const long long pv = (long long)T.S * (tj + 2) * T.n1;
+    if (tj < 1 || tj > 32 || pv > 8 * kRhsThreads) return cudaErrorInvalidValue;
+    const size_t smem = 4 * sizeof(float2) * (size_t)pv;
+    dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + ks - 1) / ks, 1);
+    const bool small = pv <= 4 * kRhsThreads;
+    if (T.rhs_mb == 2) {
+        if (small) k_rhs_roll<GEO, 4, 2><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+        else k_rhs_roll<GEO, 8, 2><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+    } else {
+        if (small) k_rhs_roll<GEO, 4, 1><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+        else k_rhs_roll<GEO, 8, 1><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+    }
+    return cudaGetLastError();
 }
 
 TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols) {
@@ -920,6 +1086,11 @@ cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_
 }
 
 cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st) {
+    if (T.rhs_ks > 0) {
+        if (T.geometry == GEO_BALL) return launch_rhs_roll_geo<GEO_BALL>(T, st);
+        if (T.geometry == GEO_CYLINDER) return launch_rhs_roll_geo<GEO_CYLINDER>(T, st);
+        return cudaErrorInvalidValue;
+    }
     switch (T.geometry) {
     case GEO_DISK: return launch_rhs_tile_geo<GEO_DISK>(T, st);
     case GEO_SPHERE: return launch_rhs_tile_geo<GEO_SPHERE>(T, st);

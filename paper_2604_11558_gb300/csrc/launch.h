@@ -35,7 +35,7 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab);
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st);
-int rhs_tile_candidates(const SplitTables& T, int* out, int max_out);
+int rhs_candidates(const SplitTables& T, int3* out, int max_out);
 // Batched disks: one persistent launch per step.
 TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols);
 cudaError_t tc_prepare_batch(uint32_t smem);

@@ -249,8 +249,8 @@ sexpe_status build_fp64(sexpe_plan* p, cudaStream_t st) {
 // once at setup, before any graph capture; the scratch state is freed here.
 static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
     SplitTables T = p->tabs;
-    int cand[40];
-    const int nc = rhs_tile_candidates(T, cand, 40);
+    int3 cand[160];
+    const int nc = rhs_candidates(T, cand, 160);
     if (nc == 0) return SEXPE_EUNSUPPORTED;
     double* scratch = nullptr;
     const size_t bytes = sizeof(double) * (size_t)p->S * p->npts;
@@ -261,14 +261,16 @@ static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     sexpe_status rc = SEXPE_OK;
     float best_ms = 1e30f;
-    int best = cand[0];
+    int3 best = cand[0];
     if (cudaMemsetAsync(scratch, 0, bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess) {
         rc = SEXPE_ECUDA;
     } else {
         T.state = scratch;
         for (int c = 0; c < nc && rc == SEXPE_OK; ++c) {
-            T.rhs_tj = cand[c];
+            T.rhs_tj = cand[c].x;
+            T.rhs_ks = cand[c].y;
+            T.rhs_mb = cand[c].z;
             bool ok = launch_rhs_split(T, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess;
             for (int r = 0; r < 3 && ok; ++r) ok = launch_rhs_split(T, st) == cudaSuccess;
             float ms = 0.f;
@@ -286,7 +288,9 @@ static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
     cudaFree(scratch);
-    p->tabs.rhs_tj = best;
+    p->tabs.rhs_tj = best.x;
+    p->tabs.rhs_ks = best.y;
+    p->tabs.rhs_mb = best.z;
     p->rhs_tj_us = best_ms * 1000.f / 3.f;
     return rc;
 }
@@ -986,6 +990,24 @@ sexpe_status sexpe_state_offsets(const sexpe_plan* plan, int64_t* offsets_host) 
     return SEXPE_OK;
 }
 
+sexpe_status sexpe_set_stencil(sexpe_plan* p, int32_t tile_j, int32_t planes, int32_t ctas_per_sm) {
+    if (!p) return SEXPE_EINVAL;
+    if (p->batch || p->precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
+    int3 cand[160];
+    const int nc = rhs_candidates(p->tabs, cand, 160);
+    bool ok = false;
+    for (int c = 0; c < nc; ++c) ok = ok || (cand[c].x == tile_j && cand[c].y == planes && cand[c].z == ctas_per_sm);
+    if (!ok) return SEXPE_EINVAL;
+    p->tabs.rhs_tj = tile_j;
+    p->tabs.rhs_ks = planes;
+    p->tabs.rhs_mb = ctas_per_sm;
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    return SEXPE_OK;
+}
+
 sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* stream) {
     if (!p || !state || n_steps < 0) return SEXPE_EINVAL;
     if (((uintptr_t)state & 7u) != 0) return SEXPE_EINVAL;
@@ -1070,6 +1092,8 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
         info->ring_slots[0] = (int32_t)p->shs.nm;
         info->ring_slots[1] = (int32_t)p->shs.nd;
         info->stencil_tile_us = p->rhs_tj_us;
+        info->stencil_planes = p->tabs.rhs_ks;
+        info->stencil_ctas_per_sm = p->tabs.rhs_mb;
     } else if (p->batch) {
         info->ring_slots[0] = (int32_t)p->bsh.nm;
         info->ring_slots[1] = (int32_t)p->bsh.nd;

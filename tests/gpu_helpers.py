@@ -35,11 +35,14 @@ def emulated_fp32_errors(w, ref):
     return rel_errors(emu, ref)
 
 
-def gpu_run(w, precision, steps=None, single_calls=False):
+def gpu_run(w, precision, steps=None, single_calls=False, stencil=None):
+    """stencil: optional (tile_j, planes) forced through sexpe_set_stencil."""
     import torch
     from paper_2604_11558_gb300 import binding
     plan = binding.Plan(w["geometry"], w["n"], w["d"], w["reaction"], w["params"], w["tau"], precision,
                         z_bc=w.get("z_bc", "neumann"))
+    if stencil is not None:
+        plan.set_stencil(*stencil)
     x = torch.from_numpy(np.ascontiguousarray(w["W0"])).cuda()
     n = w["steps"] if steps is None else steps
     if single_calls:

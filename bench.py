@@ -358,8 +358,9 @@ def main():
 
 
 def measure_extras(flush):
-    """The other workloads: cylinder 64x128x128 (3 species), 256 uneven disks (one persistent
-    launch per step), and the sphere 256x512 adjoint cost relative to its forward."""
+    """The other workloads: cylinder 64x128x128 (3 species), sphere 256x512 (split and FP64), 256
+    uneven disks (one persistent launch per step), and the sphere 256x512 adjoint cost relative to
+    its forward."""
     import numpy as np
     import torch
     from paper_2604_11558_gb300 import binding
@@ -377,6 +378,18 @@ def measure_extras(flush):
         res[prec] = {"ms_per_step": sum(ms) / steps, "value": dof * steps / (sum(ms) / 1e3)}
         plan.close()
     out["cylinder_64x128x128_3species"] = {"unit": UNIT, "dof": dof, **res}
+    # sphere 256x512, split and FP64 (forward steps)
+    w = wl.schnakenberg_sphere(steps=1)
+    dof = len(w["d"]) * int(np.prod(w["n"]))
+    res = {}
+    for prec, steps in (("split_tf32", 100), ("fp64", 5)):
+        plan = binding.Plan.from_workload(w, precision=prec)
+        x = torch.from_numpy(w["W0"]).cuda()
+        plan.step(x, 2)
+        ms, kms = timed_steps(plan, x, steps, flush, profile=True)
+        res[prec] = {"ms_per_step": sum(ms) / steps, "value": dof * steps / (sum(ms) / 1e3), "kernel_ms": kms}
+        plan.close()
+    out["sphere_256x512_2species"] = {"unit": UNIT, "dof": dof, **res}
     # batched disks
     ws = wl.batched_disks(steps=1)
     dof = sum(2 * wq["n"][0] * wq["n"][1] for wq in ws)

@@ -96,6 +96,12 @@ struct SplitTables {
     // mode-3 pass
     Image M3a, M3b[kMaxSpecies];   // ball: Vinv (M3a) and V (M3b[0]); cylinder: Pz_s in M3b[s]
     const float* had_phi;          // ball: Phi table of the phi direction, [s][k'][n1q]
+    // sphere (mode 1 theta, mode 2 phi): phi direction (plain) into Y2, then theta (scaled) + update
+    Image Pphi[kMaxSpecies];       // phi_1(tau d_s A_phi) as B operand, N-tiled: tile t (rows
+                                   // [t phi_nt, (t + 1) phi_nt)) at ptr + t * k_chunks * chunk_floats
+    int phi_nt;                    // output phi rows per CTA of the phi product
+    float* Y2;                     // phi product output, layout of Y
+    const float* had_sph;          // phi_1(tau d_s sin^-2 phi_j lambda_theta'), [s][j][n1q]
     int* err;
     int rhs_tj;                    // j-lines per stencil tile (chosen by measurement at setup; 0 = model)
     int rhs_ks;                    // 0: tiled stencil kernel; > 0: rolling-window kernel, planes per CTA

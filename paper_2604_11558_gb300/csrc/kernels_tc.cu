@@ -660,6 +660,49 @@ __device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, uint
     gs[2] = GemmSpec{J.P, 0, kRows * m2, m2, n1p, n1p / kKC, tmem + cols[2]};
 }
 
+// Update of up to 128 state rows from an FP32 accumulator in tensor memory:
+// W[row][i] = Win[row][i] + tau * D[row][i] for row < rows, i < n1, with D at
+// tensor-memory columns [dcol, dcol + n1p) of lane `row` and the rows n1
+// apart in global memory.  The accumulator is staged through shared memory
+// (`epi`, 128 (n1p + 1) floats) so the FP64 read-modify-write is coalesced;
+// the increment is rounded to FP32 and widened exactly by integer operations:
+// one FP64 add per point, eight independent read-modify-writes in flight per
+// thread.  Called by the 256 producer threads.
+__device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int n1p, const double* Win,
+                                            double* W, float tau_f, char* epi) {
+    const int tid = threadIdx.x;
+    const int r = tid & (kRows - 1), h = tid >> 7;
+    const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
+    float* E = reinterpret_cast<float*>(epi);
+    const int pitch = n1p + 1;
+    for (int c = 0; c < n1p / 16; ++c) {
+        float v[8];
+        tmem_ld8(dcol + lane_base + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) E[r * pitch + c * 16 + h * 8 + q] = v[q];
+    }
+    compute_sync();
+    const int count = rows * n1;
+    const uint32_t m_n1 = div_magic((uint32_t)n1);
+    for (int f0 = tid; f0 < count; f0 += kThreads * 8) {
+        double w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * kThreads;
+            w[u] = f < count ? Win[f] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * kThreads;
+            if (f < count) {
+                const int jl = div_by(f, m_n1), i = f - jl * n1;
+                W[f] = w[u] + f32_to_f64(tau_f * E[jl * pitch + i]);
+            }
+        }
+    }
+    compute_sync();
+}
+
 // F of one disk species at (i, j0 + q), q < 8, from FP64-accurate differences of
 // the state (both species of the instance at `inst_base`), 0 outside the grid.
 __device__ __forceinline__ void disk_F8(const BatchInstance& I, const double* inst_base, int s, int i, int j0,
@@ -759,41 +802,10 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
             store_row8(hi, lo, mt * kRows + r, h, v);
         }
     });
-    // w[k][j][i'] += tau R^T[j][i'], staged through shared memory for coalesced FP64 RMW.
-    float* E = reinterpret_cast<float*>(epi);
-    const int pitch = n1p + 1;
-    for (int mt = 0; mt < m2; ++mt) {
-        for (int c = 0; c < n1p / 16; ++c) {
-            float v[8];
-            tmem_ld8(tmem + lane_base + c3 + (uint32_t)(mt * n1p + c * 16 + h * 8), v);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) E[r * pitch + c * 16 + h * 8 + q] = v[q];
-        }
-        compute_sync();
-        const int rows = min(kRows, n2 - mt * kRows);
-        const int count = rows * n1;
-        double* Wt = J.W + (long long)mt * kRows * n1;
-        const double* Wi = J.Win + (long long)mt * kRows * n1;
-        // increment rounded to FP32, widened exactly by integer operations: one FP64 add per
-        // point; eight independent read-modify-writes in flight per thread
-        for (int f0 = tid; f0 < count; f0 += kThreads * 8) {
-            double w[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int f = f0 + u * kThreads;
-                w[u] = f < count ? Wi[f] : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int f = f0 + u * kThreads;
-                if (f < count) {
-                    const int jl = f / n1, i = f - jl * n1;
-                    Wt[f] = w[u] + f32_to_f64(J.tau_f * E[jl * pitch + i]);
-                }
-            }
-        }
-        compute_sync();
-    }
+    // w[k][j][i'] += tau R^T[j][i']
+    for (int mt = 0; mt < m2; ++mt)
+        update_rows(tmem + c3 + (uint32_t)(mt * n1p), min(kRows, n2 - mt * kRows), n1, n1p,
+                    J.Win + (long long)mt * kRows * n1, J.W + (long long)mt * kRows * n1, J.tau_f, epi);
 }
 
 __global__ void __launch_bounds__(kBlock, 1)
@@ -823,6 +835,115 @@ __global__ void __launch_bounds__(kBlock, 1)
     if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
     else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
     else slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
+    cta_end(R, tmem_cols);
+}
+
+// ------------------------------------------------------------------------------
+// Sphere (eq. ee_sphere; mode 1 = theta, contiguous; mode 2 = phi).
+//
+// phi direction (plain): Y2[s][j'][i] = sum_j phi_1(tau d_s A_phi)[j'][j] Y[s][j][i].
+// CTA = 128 consecutive theta points (rows) x phi_nt output phi rows (the B
+// operand's N-tile blockIdx.y) of species blockIdx.z; K runs over all phi.
+__global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcShape sh) {
+    extern __shared__ char smem_raw[];
+    const uint32_t tmem_cols = sh.tmem_cols;
+    CtaRes R = cta_begin(smem_raw, sh, T.err);
+    const int s = blockIdx.z, nt = blockIdx.y;
+    const int n1 = T.n1, n2 = T.n2, n1q = T.n1q, NT = T.phi_nt;
+    const int i0 = blockIdx.x * kRows;
+    Image mat = T.Pphi[s];
+    mat.ptr += (long long)nt * mat.k_chunks * mat.chunk_floats;
+    GemmSpec gs[1] = {{mat, 0, kRows, 1, NT, mat.k_chunks, R.tmem}};
+    if (threadIdx.x >= kThreads + 32) {
+        mma_issuer(R.P, gs, 1);
+    } else if (threadIdx.x >= kThreads) {
+        tma_issuer(R.P, gs, 1);
+    } else {
+        const int tid = threadIdx.x;
+        const int r = tid & (kRows - 1), h = tid >> 7;
+        const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
+        const int i = i0 + r;
+        const bool valid = i < n1;
+        const float* Yi = T.Y + (long long)s * T.ys + i;
+        run_gemm(
+            R.P, gs[0],
+            [&](int c, Pre8& p) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = c * 16 + h * 8 + q;
+                    p.v[q] = (valid && j < n2) ? __ldg(Yi + (long long)j * n1q) : 0.f;
+                }
+            },
+            [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
+        float* Yo = T.Y2 + (long long)s * T.ys + i;
+        for (int c = 0; c < NT / 16; ++c) {
+            float v[8];
+            tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = nt * NT + c * 16 + h * 8 + q;
+                if (valid && j < n2) Yo[(long long)j * n1q] = v[q];
+            }
+        }
+    }
+    cta_end(R, tmem_cols);
+}
+
+// theta direction (scaled) + update: rows = 128 phi rows j of species blockIdx.y;
+// G1: X = Y2 x_1 Q_theta^T, Hadamard Phi(j, theta'), G2: x_1 Q_theta, then
+// w[s][j][i] += tau * result.  Accumulators: G1 at [0, n1p), G2 at [n1p, 2 n1p).
+__global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, TcShape sh) {
+    extern __shared__ char smem_raw[];
+    const uint32_t tmem_cols = sh.tmem_cols;
+    CtaRes R = cta_begin(smem_raw, sh, T.err);
+    const int s = blockIdx.y;
+    const int n1 = T.n1, n2 = T.n2, n1q = T.n1q;
+    const int n1p = (n1 + 15) & ~15;
+    const int j0 = blockIdx.x * kRows;
+    GemmSpec gs[2] = {{T.QT, 0, kRows, 1, n1p, n1p / kKC, R.tmem},
+                      {T.Q, 0, kRows, 1, n1p, n1p / kKC, R.tmem + (uint32_t)n1p}};
+    if (threadIdx.x >= kThreads + 32) {
+        mma_issuer(R.P, gs, 2);
+    } else if (threadIdx.x >= kThreads) {
+        tma_issuer(R.P, gs, 2);
+    } else {
+        const int tid = threadIdx.x;
+        const int r = tid & (kRows - 1), h = tid >> 7;
+        const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
+        const int j = j0 + r;
+        const bool valid = j < n2;
+        // eight consecutive theta values of row j (16-byte aligned: n1q and 8-column groups)
+        auto load_row8 = [&](const float* row) {
+            return [=](int c, Pre8& p) {
+                const int i = c * 16 + h * 8;
+                if (valid && i + 8 <= n1q) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(row + i));
+                    const float4 b = __ldg(reinterpret_cast<const float4*>(row + i + 4));
+                    p.v[0] = a.x; p.v[1] = a.y; p.v[2] = a.z; p.v[3] = a.w;
+                    p.v[4] = b.x; p.v[5] = b.y; p.v[6] = b.z; p.v[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) p.v[q] = (valid && i + q < n1q) ? __ldg(row + i + q) : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (i + q >= n1) p.v[q] = 0.f;
+            };
+        };
+        const long long roff = (long long)s * T.ys + (long long)(valid ? j : 0) * n1q;
+        run_gemm(R.P, gs[0], load_row8(T.Y2 + roff),
+                 [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
+        run_gemm(R.P, gs[1], load_row8(T.had_sph + roff), [&](int c, char* hi, char* lo, const Pre8& p) {
+            float v[8];
+            tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
+            store_row8(hi, lo, r, h, v);
+        });
+        const long long n12 = (long long)n1 * n2;
+        double* W = T.state_upd + (long long)s * n12 + (long long)j0 * n1;
+        update_rows(R.tmem + (uint32_t)n1p, min(kRows, n2 - j0), n1, n1p, W, W, T.tau, R.P.mat_slots);
+    }
     cta_end(R, tmem_cols);
 }
 
@@ -949,6 +1070,47 @@ static TcShape slab_shape(int n1, int n2, bool pair) {
 }
 
 TcShape tc_slab_shape(int n1, int n2) { return slab_shape(n1, n2, true); }
+
+// Sphere phi product: data tile 128 rows, matrix N-tile nt rows, accumulator nt columns.
+TcShape tc_sphere_phi_shape(int nt) {
+    TcShape sh{};
+    sh.data_bytes = 2u * kRows * kTileRowBytes;
+    sh.mat_bytes = 2u * (uint32_t)nt * kTileRowBytes;
+    sh.tmem_cols = pow2_cols((uint32_t)nt);
+    rings(sh, 0, sh.tmem_cols <= 256);
+    return sh;
+}
+
+// Sphere theta product pair: matrices n1p rows, accumulators 2 n1p columns, update staging.
+TcShape tc_sphere_theta_shape(int n1) {
+    TcShape sh{};
+    const uint32_t n1p = round_up(n1, 16);
+    sh.data_bytes = 2u * kRows * kTileRowBytes;
+    sh.mat_bytes = 2u * n1p * kTileRowBytes;
+    sh.tmem_cols = pow2_cols(2 * n1p);
+    rings(sh, kRows * (n1p + 1) * 4u, sh.tmem_cols <= 256);
+    return sh;
+}
+
+cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_sphere_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_phi);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tc_sphere_theta, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_theta);
+    return e;
+}
+
+cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
+    const int n2p = (T.n2 + 15) & ~15;
+    dim3 grid((T.n1 + kRows - 1) / kRows, (n2p + T.phi_nt - 1) / T.phi_nt, T.S);
+    k_tc_sphere_phi<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
+    dim3 grid((T.n2 + kRows - 1) / kRows, T.S);
+    k_tc_sphere_theta<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
+    return cudaGetLastError();
+}
 
 cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     cudaError_t e = cudaSuccess;

@@ -35,6 +35,12 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab);
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st);
+// Sphere: phi product (plain), then theta pair (scaled) + update.
+TcShape tc_sphere_phi_shape(int nt);
+TcShape tc_sphere_theta_shape(int n1);
+cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta);
+cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaStream_t st);
+cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 int rhs_candidates(const SplitTables& T, int3* out, int max_out);
 // Batched disks: one persistent launch per step.
 TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols);

@@ -295,8 +295,72 @@ static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
     return rc;
 }
 
+// Split-TF32 sphere (eq. ee_sphere): mode 1 theta (scaled by sin^-2 phi_j),
+// mode 2 phi (plain); phi first, then theta with the update.
+sexpe_status build_split_sphere(sexpe_plan* p, cudaStream_t st) {
+    const int n1 = p->n[0], n2 = p->n[1];
+    if (n1 > 256) return SEXPE_EUNSUPPORTED;
+    SplitTables& T = p->tabs;
+    T.geometry = p->geometry;
+    T.S = p->S;
+    T.n1 = n1;
+    T.n2 = n2;
+    T.n3 = 1;
+    T.npts = p->npts;
+    T.tau = (float)p->tau;
+    T.tau_d = p->tau;
+    SX_TRY(build_rhs_tables<float>(p, &T.rhs, st));
+    T.n1q = (n1 + 3) & ~3;
+    T.ys = (long long)n2 * T.n1q;
+    SX_TRY(alloc_dev(p, (size_t)p->S * T.ys, &T.Y));
+    SX_TRY(alloc_dev(p, (size_t)p->S * T.ys, &T.Y2));
+    SX_CUDA(cudaMemsetAsync(T.Y, 0, sizeof(float) * (size_t)p->S * T.ys, st));
+    SX_CUDA(cudaMemsetAsync(T.Y2, 0, sizeof(float) * (size_t)p->S * T.ys, st));
+    T.err = p->d_err;
+    const int n1p = rup16(n1), n2p = rup16(n2);
+    // theta: Q_theta (closed form), as B operands of both products
+    Eigen th = theta_eigen(p->ax[0]);
+    SX_TRY(upload_image(p, n1, n1, n1p, n1p, [&](int r, int k) { return th.V(k, r); }, &T.QT, st));
+    SX_TRY(upload_image(p, n1, n1, n1p, n1p, [&](int r, int k) { return th.V(r, k); }, &T.Q, st));
+    std::vector<float> hs((size_t)p->S * T.ys, 0.f);
+    for (int s = 0; s < p->S; ++s)
+        for (int j = 0; j < n2; ++j)
+            for (int ip = 0; ip < n1; ++ip)
+                hs[(size_t)s * T.ys + (size_t)j * T.n1q + ip] =
+                    (float)phi1_scalar(p->tau * p->d[s] * dir_scale(p, 1, 0, j, 0) * th.lam[ip]);
+    SX_TRY(upload(p, hs, &T.had_sph, st));
+    // phi: phi_1(tau d_s A_phi), N-tiled so several CTAs share the product of one theta tile
+    T.phi_nt = n2p <= 128 ? n2p : 128;
+    const int ntiles = (n2p + T.phi_nt - 1) / T.phi_nt;
+    const Mat Aphi = p->ax[1].dense();
+    for (int s = 0; s < p->S; ++s) {
+        Mat X(n2);
+        for (size_t q = 0; q < X.a.size(); ++q) X.a[q] = p->tau * p->d[s] * Aphi.a[q];
+        const Mat Ps = phi1_pade(X);
+        if (!all_finite(Ps.a)) return SEXPE_ENUMERIC;
+        std::vector<float> img;
+        for (int t = 0; t < ntiles; ++t) {
+            const int r0 = t * T.phi_nt;
+            const std::vector<float> part = make_image(std::min(T.phi_nt, n2 - r0), n2, T.phi_nt, n2p,
+                                                       [&](int r, int k) { return Ps(r0 + r, k); });
+            img.insert(img.end(), part.begin(), part.end());
+        }
+        const float* dptr = nullptr;
+        SX_TRY(upload(p, img, &dptr, st));
+        T.Pphi[s] = Image{dptr, T.phi_nt, n2p / kKC, 2LL * T.phi_nt * kKC};
+    }
+    p->sh3 = tc_sphere_phi_shape(T.phi_nt);
+    p->shs = tc_sphere_theta_shape(n1);
+    if (p->shs.smem_bytes > 227 * 1024 || p->sh3.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
+    if (p->shs.tmem_cols > 512 || p->sh3.tmem_cols > 512) return SEXPE_EUNSUPPORTED;
+    SX_CUDA(tc_prepare(0, 0));
+    SX_CUDA(tc_prepare_sphere(p->sh3.smem_bytes, p->shs.smem_bytes));
+    p->kernels_per_step = 3;
+    return tune_stencil(p, st);
+}
+
 sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
-    if (p->geometry == SEXPE_SPHERE) return SEXPE_EUNSUPPORTED;
+    if (p->geometry == SEXPE_SPHERE) return build_split_sphere(p, st);
     const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
     if (n1 > 128 || n2 > 256 || (p->ndim == 3 && n3 > 256)) return SEXPE_EUNSUPPORTED;
     SplitTables& T = p->tabs;
@@ -465,6 +529,13 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
     T.state_upd = state;
     SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_rhs_split(T, st));
+    if (p->geometry == SEXPE_SPHERE) {
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_tc_sphere_phi(T, p->sh3, st));
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_tc_sphere_theta(T, p->shs, st));
+        return SEXPE_OK;
+    }
     if (p->ndim == 3) {
         SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_tc_mode3(T, p->sh3, st));
@@ -897,6 +968,11 @@ sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float
     T.state_upd = state;
     T.Y = Y;
     SX_CUDA(launch_rhs_split(T, st));
+    if (p->geometry == SEXPE_SPHERE) {        // the phi product's output stays in the plan's own buffer
+        SX_CUDA(launch_tc_sphere_phi(T, p->sh3, st));
+        SX_CUDA(launch_tc_sphere_theta(T, p->shs, st));
+        return SEXPE_OK;
+    }
     if (p->ndim == 3) SX_CUDA(launch_tc_mode3(T, p->sh3, st));
     SX_CUDA(launch_tc_slab(T, p->shs, st));
     return SEXPE_OK;

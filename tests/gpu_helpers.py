@@ -26,13 +26,21 @@ def oracle_run(w, steps=None):
     return run(p, w["W0"], w["steps"] if steps is None else steps)
 
 
-def emulated_fp32_errors(w, ref):
+def emulated_fp32_errors(w, ref, increments=False):
     """Per-species relative error of the oracle run with FP32 storage of F, of every
-    direction's result and of the increment (the storage floor of an FP32 chain)."""
+    direction's result and of the increment (the storage floor of an FP32 chain); with
+    `increments`, also the relative error of W_n - W_0."""
     g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"))
     p = Problem(g, w["d"], oracle_reaction(w), w["tau"])
     emu = run(p, w["W0"], w["steps"], fp32_storage=True)
-    return rel_errors(emu, ref)
+    if not increments:
+        return rel_errors(emu, ref)
+    return rel_errors(emu, ref), increment_errors(emu, ref, w["W0"])
+
+
+def increment_errors(got, ref, W0):
+    return [float(np.linalg.norm((got[s] - W0[s]) - (ref[s] - W0[s])) / max(np.linalg.norm(ref[s] - W0[s]), 1e-300))
+            for s in range(ref.shape[0])]
 
 
 def gpu_run(w, precision, steps=None, single_calls=False, stencil=None):

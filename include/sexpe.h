@@ -177,6 +177,15 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_h
  * only; call it when no step of the plan is being enqueued by another thread. */
 sexpe_status sexpe_set_stencil(sexpe_plan* plan, int32_t tile_j, int32_t planes, int32_t ctas_per_sm);
 
+/* Self-test of the failure path of every device wait (no counterpart in the
+ * paper): one thread waits on a barrier nobody arrives on, with a limit of
+ * about 1 ms; the wait gives up, records the timeout in a device error word
+ * and the kernel returns.  Returns SEXPE_ETIMEOUT -- the status a plan's
+ * sexpe_synchronize reports after such a timeout -- when that happened, and
+ * the CUDA context stays usable; SEXPE_ECUDA if the word was not written.
+ * Allocates and frees one int of device memory; synchronises `stream`. */
+sexpe_status sexpe_selftest_wait_timeout(void* stream);
+
 /* Free every device table of the plan (after synchronising its device). */
 sexpe_status sexpe_destroy(sexpe_plan* plan);
 

@@ -79,6 +79,7 @@ def lib():
         L.sexpe_synchronize.argtypes = [_P, _P]
         L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
         L.sexpe_set_stencil.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.sexpe_selftest_wait_timeout.argtypes = [_P]
         L.sexpe_destroy.argtypes = [_P]
         L.sexpe_step_checkpointed.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
         L.sexpe_adjoint.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _DP, _P]
@@ -91,6 +92,7 @@ def lib():
                      "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
                      "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
                      "sexpe_step_checkpointed", "sexpe_adjoint", "sexpe_set_stencil",
+                     "sexpe_selftest_wait_timeout",
                      "sexpe_axis_phi1", "sexpe_axis_eigen"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
@@ -102,6 +104,12 @@ def header_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(sexpe_\w+)\s*\(", text)))
+
+
+def selftest_wait_timeout(stream=None):
+    """sexpe_selftest_wait_timeout: returns the status (SEXPE_ETIMEOUT = 4 when the bounded wait
+    gave up and reported as designed)."""
+    return int(lib().sexpe_selftest_wait_timeout(_stream_ptr(stream)))
 
 
 def _check(status, where):

@@ -212,6 +212,13 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
             mma_commit(&P.mat_empty[sm]);
         }
     }
+    // No MMA of this CTA may be in flight when its tensor memory is freed, also
+    // after a timed-out wait made the chain run ahead: wait (bounded) for the
+    // last commit.  In a healthy run it completes within the MMAs' latency.
+    if (P.g > 0) {
+        const uint32_t sd = P.sd ? P.sd - 1 : P.nd - 1, pd = P.sd ? P.pd : P.pd ^ 1u;
+        pipe_wait(P, &P.data_empty[sd], pd, DERR_TIMEOUT_MMA);
+    }
 }
 
 // TMA side: one lane of the extra warp walks the K-chunks of every product of
@@ -231,6 +238,15 @@ __device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
             mbar_arrive_expect_tx(&P.mat_full[s], 2 * tile);
             tma_bulk_g2s(slot, src, 2 * tile, &P.mat_full[s]);
         }
+    }
+    // No copy of this CTA may still be landing when the CTA exits or its shared
+    // memory is reused, also after a timed-out wait: wait (bounded) for the
+    // last copy of every slot.  In a healthy run these phases completed long ago.
+    const uint32_t last = P.g < P.nm ? P.g : P.nm;
+    for (uint32_t b = 1; b <= last; ++b) {
+        const uint32_t sm = (P.sm + P.nm - b) % P.nm;
+        const uint32_t pm = b > P.sm ? P.pm ^ 1u : P.pm;
+        pipe_wait(P, &P.mat_full[sm], pm, DERR_TIMEOUT_TMA);
     }
 }
 
@@ -1244,6 +1260,24 @@ cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_
     cudaError_t e = cudaMemsetAsync(B.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     k_tc_batch<<<152, kBlock, sh.smem_bytes, st>>>(B, sh);
+    return cudaGetLastError();
+}
+
+// Self-test of the bounded-wait path every pipeline wait uses: one thread waits
+// on an mbarrier nobody arrives on; after `limit_cycles` the wait gives up,
+// records DERR_TIMEOUT_MMA in *err and the kernel returns normally.
+__global__ void k_wait_selftest(int* err, long long limit_cycles) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, err, DERR_TIMEOUT_MMA, limit_cycles);
+}
+
+cudaError_t launch_wait_selftest(int* err, long long limit_cycles, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(err, limit_cycles);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab);
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st);
+cudaError_t launch_wait_selftest(int* err, long long limit_cycles, cudaStream_t st);
 // Sphere: phi product (plain), then theta pair (scaled) + update.
 TcShape tc_sphere_phi_shape(int nt);
 TcShape tc_sphere_theta_shape(int n1);

@@ -1137,6 +1137,23 @@ sexpe_status sexpe_step_host(sexpe_plan* p, double* state_host, int64_t n_steps,
     return sexpe_synchronize(p, stream);
 }
 
+sexpe_status sexpe_selftest_wait_timeout(void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int* err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return SEXPE_ENOMEM;
+    }
+    int host = -1;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_wait_selftest(err, 2000000LL, st);   // ~1 ms at 2 GHz
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&host, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_status(e);
+    return host == DERR_TIMEOUT_MMA ? SEXPE_ETIMEOUT : SEXPE_ECUDA;
+}
+
 sexpe_status sexpe_synchronize(sexpe_plan* p, void* stream) {
     if (!p) return SEXPE_EINVAL;
     SX_CUDA(cudaStreamSynchronize((cudaStream_t)stream));

@@ -29,6 +29,24 @@
 
 namespace sexpe {
 
+// Launch with programmatic stream serialization (see pdl_wait in tc_ptx.cuh):
+// the kernel's prologue overlaps the tail of the previous kernel in the stream.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 constexpr int kRows = 128;                 // MMA M and tensor-memory lanes
 constexpr int kThreads = 256;              // producer threads: two per row, columns 0-7 / 8-15 of a chunk
 constexpr int kBlock = kThreads + 64;      // + one warp issuing TMA copies ahead, one issuing the MMAs
@@ -413,6 +431,8 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
         row_off[row] = ok ? sp * npts + (long long)k * n12 + (long long)j * n1 : -1;
     }
     __syncthreads();
+    pdl_wait();          // the state is the previous step's result
+    pdl_trigger();
     // tile fill: (row, i) items over all threads, kTileBatch loads in flight per thread
     const int items = rows * n1;
     for (int q0 = threadIdx.x; q0 < items; q0 += kRhsThreads * kTileBatch) {
@@ -534,6 +554,8 @@ __global__ void __launch_bounds__(kRhsThreads, MINB) k_rhs_roll(RhsTables<float>
             if (q < pv) P[q] = split_f64(v[u]);
         }
     };
+    pdl_wait();          // the state is the previous step's result
+    pdl_trigger();
     load_plane(k0 - 1);
     store_plane(k0 - 1);
     load_plane(k0);
@@ -595,10 +617,14 @@ __global__ void __launch_bounds__(kBlock, 1)
     GemmSpec gs[2] = {{GEO == GEO_BALL ? T.M3a : T.M3b[s], 0, kRows, 1, n3p, n3p / kKC, R.tmem},
                       {T.M3b[0], 0, kRows, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p}};
     if (threadIdx.x >= kThreads + 32) {
+        pdl_trigger();
         mma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);
     } else if (threadIdx.x >= kThreads) {
-        tma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);
+        pdl_trigger();
+        tma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);     // constant matrices only
     } else {
+        pdl_wait();      // F from the stencil pass
+        pdl_trigger();
         const int tid = threadIdx.x;
         const int r = tid & (kRows - 1), h = tid >> 7;
         const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
@@ -848,9 +874,17 @@ __global__ void __launch_bounds__(kBlock, 1)
     GemmSpec gs[3];
     uint32_t cols[3];
     slab_specs(J, R.tmem, tmem_cols, gs, cols);
-    if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
-    else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
-    else slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
+    if (threadIdx.x >= kThreads + 32) {
+        pdl_trigger();
+        mma_issuer(R.P, gs, 3);
+    } else if (threadIdx.x >= kThreads) {
+        pdl_trigger();
+        tma_issuer(R.P, gs, 3);             // constant matrices only
+    } else {
+        pdl_wait();                         // Y from the earlier directions
+        pdl_trigger();
+        slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
+    }
     cta_end(R, tmem_cols);
 }
 
@@ -871,10 +905,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcSh
     mat.ptr += (long long)nt * mat.k_chunks * mat.chunk_floats;
     GemmSpec gs[1] = {{mat, 0, kRows, 1, NT, mat.k_chunks, R.tmem}};
     if (threadIdx.x >= kThreads + 32) {
+        pdl_trigger();
         mma_issuer(R.P, gs, 1);
     } else if (threadIdx.x >= kThreads) {
+        pdl_trigger();
         tma_issuer(R.P, gs, 1);
     } else {
+        pdl_wait();
+        pdl_trigger();
         const int tid = threadIdx.x;
         const int r = tid & (kRows - 1), h = tid >> 7;
         const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
@@ -919,10 +957,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, Tc
     GemmSpec gs[2] = {{T.QT, 0, kRows, 1, n1p, n1p / kKC, R.tmem},
                       {T.Q, 0, kRows, 1, n1p, n1p / kKC, R.tmem + (uint32_t)n1p}};
     if (threadIdx.x >= kThreads + 32) {
+        pdl_trigger();
         mma_issuer(R.P, gs, 2);
     } else if (threadIdx.x >= kThreads) {
+        pdl_trigger();
         tma_issuer(R.P, gs, 2);
     } else {
+        pdl_wait();
+        pdl_trigger();
         const int tid = threadIdx.x;
         const int r = tid & (kRows - 1), h = tid >> 7;
         const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
@@ -974,6 +1016,8 @@ __global__ void __launch_bounds__(kBlock, 1)
     __shared__ int s_item;
     const uint32_t tmem_cols = sh.tmem_cols;
     CtaRes R = cta_begin(smem_raw, sh, B.err);
+    pdl_wait();          // previous step's state and work-list cursor
+    pdl_trigger();
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(B.counter, 1);
         tc_fence_before();
@@ -1118,14 +1162,12 @@ cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta) {
 cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     const int n2p = (T.n2 + 15) & ~15;
     dim3 grid((T.n1 + kRows - 1) / kRows, (n2p + T.phi_nt - 1) / T.phi_nt, T.S);
-    k_tc_sphere_phi<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
-    return cudaGetLastError();
+    return launch_pdl(k_tc_sphere_phi, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
 }
 
 cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid((T.n2 + kRows - 1) / kRows, T.S);
-    k_tc_sphere_theta<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
-    return cudaGetLastError();
+    return launch_pdl(k_tc_sphere_theta, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
 }
 
 cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
@@ -1160,16 +1202,13 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
 cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid((unsigned)((T.n1q * (long long)T.n2 + kRows - 1) / kRows), T.S);
     if (T.geometry == GEO_BALL)
-        k_tc_mode3<GEO_BALL><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
-    else
-        k_tc_mode3<GEO_CYLINDER><<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
-    return cudaGetLastError();
+        return launch_pdl(k_tc_mode3<GEO_BALL>, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
+    return launch_pdl(k_tc_mode3<GEO_CYLINDER>, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
 }
 
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid(T.geometry == GEO_DISK ? 1 : T.n3, T.S);
-    k_tc_slab<<<grid, kBlock, sh.smem_bytes, st>>>(T, sh);
-    return cudaGetLastError();
+    return launch_pdl(k_tc_slab, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
 }
 
 // j-tile of the stencil pass: among the sizes whose all-species tile fits in
@@ -1204,7 +1243,8 @@ static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
     const int tj = T.rhs_tj > 0 ? T.rhs_tj : rhs_tile_tj<GEO>(T);
     const size_t smem = sizeof(float2) * (size_t)T.S * (TS::TK + 2 * TS::KH) * (tj + 2) * T.n1;
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + TS::TK - 1) / TS::TK, 1);
-    k_rhs_tile<GEO><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, T.n1q, T.ys);
+    cudaError_t e = launch_pdl(k_rhs_tile<GEO>, grid, dim3(kRhsThreads), smem, st, T.rhs, T.state, T.Y, tj, T.n1q, T.ys);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1236,13 +1276,10 @@ static cudaError_t launch_rhs_roll_geo(const SplitTables& T, cudaStream_t st) {
     const size_t smem = 4 * sizeof(float2) * (size_t)pv;
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + ks - 1) / ks, 1);
     const bool small = pv <= 4 * kRhsThreads;
-    if (T.rhs_mb == 2) {
-        if (small) k_rhs_roll<GEO, 4, 2><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
-        else k_rhs_roll<GEO, 8, 2><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
-    } else {
-        if (small) k_rhs_roll<GEO, 4, 1><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
-        else k_rhs_roll<GEO, 8, 1><<<grid, kRhsThreads, smem, st>>>(T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
-    }
+    auto kern = T.rhs_mb == 2 ? (small ? k_rhs_roll<GEO, 4, 2> : k_rhs_roll<GEO, 8, 2>)
+                              : (small ? k_rhs_roll<GEO, 4, 1> : k_rhs_roll<GEO, 8, 1>);
+    cudaError_t e = launch_pdl(kern, grid, dim3(kRhsThreads), smem, st, T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1259,8 +1296,7 @@ cudaError_t tc_prepare_batch(uint32_t smem) {
 cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(B.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_tc_batch<<<152, kBlock, sh.smem_bytes, st>>>(B, sh);
-    return cudaGetLastError();
+    return launch_pdl(k_tc_batch, dim3(152), dim3(kBlock), sh.smem_bytes, st, B, sh);
 }
 
 // Self-test of the bounded-wait path every pipeline wait uses: one thread waits

@@ -73,6 +73,18 @@ __device__ __forceinline__ void l2_prefetch(const void* src, unsigned long long 
     }
 }
 
+// ---- programmatic dependent launch -------------------------------------------
+// A kernel launched with programmatic stream serialization may start while its
+// predecessor in the stream still runs: it does its prologue (shared memory,
+// barriers, tensor memory, copies of constant tables), then pdl_wait() blocks
+// until the predecessor grid completed and its memory is visible.  Every read
+// of data a predecessor wrote, and every write of data it reads, comes after
+// pdl_wait().  pdl_trigger() lets the successor grid be scheduled once every
+// CTA of this grid executed it (or exited).  Both are no-ops for a kernel
+// launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- fences ---------------------------------------------------------------
 // Generic-proxy shared-memory writes -> visible to the async proxy (tcgen05.mma operands).
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

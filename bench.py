@@ -62,6 +62,9 @@ def max_over_ranks(value, world):
 
 
 # ----------------------------------------------------------------------------- algorithmic work
+PROFILE_STENCIL = (18, 4, 1)   # tile j-lines, k-planes per CTA, CTAs per SM of the rolling stencil kernel
+
+
 def kernel_work(n, S):
     """Algorithmic bytes and tensor flops per launch of the three split-path kernels of the ball step.
 
@@ -229,6 +232,9 @@ def main():
     info = plan.info()
     x = torch.from_numpy(w["W0"]).cuda()
     if args.profile_case:
+        # the setup's tuner times candidates in this process; under a profiler those timings are
+        # distorted, so the capture pins the configuration the unprofiled tuner picks on this workload
+        plan.set_stencil(*PROFILE_STENCIL)
         plan.step(x, 3)                  # untimed warm-up
         plan.synchronize()
         torch.cuda.nvtx.range_push("sexpe_step")   # ncu --nvtx --nvtx-include "sexpe_step/" captures only these

@@ -112,6 +112,7 @@ struct SplitTables {
 struct BatchInstance {
     int n1, n2;                     // rho, theta points
     long long w_off;                // element offset of the instance's state (species blocks of n1 n2)
+    long long f_off;                // float offset of the instance's F block, [s][j][n1q]
     Image QT, Q, P[2];              // theta transforms and phi_1(tau d_s A_rho) images
     const float* had;               // Phi of the theta direction, [s][j'][n1q], n1q = n1 rounded up to 4
     StencilAxis<float> ax_rho, ax_theta;
@@ -124,7 +125,11 @@ struct BatchTables {
     const BatchInstance* inst;
     const int2* items;              // (instance, species), longest first
     int n_items;
-    int* counter;                   // work-list cursor, zeroed before every launch
+    int* counter;                   // [0] chain work-list cursor, [1] grid barrier, [2] stencil-tile cursor;
+                                    // zeroed before every launch
+    const int2* ftiles;             // phase-1 stencil tiles (instance, first theta-line)
+    int n_ftiles;
+    float* F;                       // F of every instance (phase 1 -> phase 2)
     const double* W_in;             // state before the step (all instances)
     double* W_out;                  // state after the step
     float tau;

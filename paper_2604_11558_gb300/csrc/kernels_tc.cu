@@ -745,52 +745,8 @@ __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int
     compute_sync();
 }
 
-// F of one disk species at (i, j0 + q), q < 8, from FP64-accurate differences of
-// the state (both species of the instance at `inst_base`), 0 outside the grid.
-__device__ __forceinline__ void disk_F8(const BatchInstance& I, const double* inst_base, int s, int i, int j0,
-                                        float* v) {
-    const int n1 = I.n1, n2 = I.n2;
-    const long long n12 = (long long)n1 * n2;
-    const double* Ws = inst_base + s * n12;
-    const double* Wo = inst_base + (1 - s) * n12;
-    const bool iv = i < n1;
-    const int ii = iv ? i : 0;
-    double c[8], m1[8], p1[8], m2[8], p2[8], o[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int j = j0 + q;
-        const int jj = j < n2 ? j : 0;
-        const long long idx = (long long)jj * n1 + ii;
-        c[q] = Ws[idx];
-        m1[q] = ii > 0 ? Ws[idx - 1] : 0.0;
-        p1[q] = ii < n1 - 1 ? Ws[idx + 1] : 0.0;
-        m2[q] = Ws[(long long)(jj > 0 ? jj - 1 : n2 - 1) * n1 + ii];
-        p2[q] = Ws[(long long)(jj < n2 - 1 ? jj + 1 : 0) * n1 + ii];
-        o[q] = Wo[idx];
-    }
-    const float lo1 = I.ax_rho.lower[ii], up1 = I.ax_rho.upper[ii], rs1 = I.ax_rho.rs[ii], dr = I.Dr[ii];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int j = j0 + q;
-        const int jj = j < n2 ? j : 0;
-        const float2 cc = split_f64(c[q]);
-        float t0 = rs1 * (cc.x + cc.y);
-        if (ii > 0) t0 += lo1 * sdiff(split_f64(m1[q]), cc);
-        if (ii < n1 - 1) t0 += up1 * sdiff(split_f64(p1[q]), cc);
-        float t1 = I.ax_theta.rs[jj] * (cc.x + cc.y) + I.ax_theta.lower[jj] * sdiff(split_f64(m2[q]), cc) +
-                   I.ax_theta.upper[jj] * sdiff(split_f64(p2[q]), cc);
-        const float2 oo = split_f64(o[q]);
-        float w[kMaxSpecies] = {0.f, 0.f, 0.f, 0.f};
-        w[s] = cc.x + cc.y;
-        w[1 - s] = oo.x + oo.y;
-        const float f = I.d[s] * (t0 + dr * t1) + reaction<float>(I.reac, w, s);
-        v[q] = (iv && j < n2) ? f : 0.f;
-    }
-}
-
 __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* gs, const uint32_t* cols, Pipe& P,
-                                             uint32_t tmem, char* epi, const BatchInstance* BI = nullptr,
-                                             const double* inst_base = nullptr, int species = 0) {
+                                             uint32_t tmem, char* epi) {
     const int tid = threadIdx.x;
     const int r = tid & (kRows - 1), h = tid >> 7;
     const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
@@ -810,16 +766,8 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
             }
         };
     };
-    if (BI) {
-        run_gemm(P, gs[0], [&](int c, char* hi, char* lo, const Pre8&) {
-            float v[8];
-            disk_F8(*BI, inst_base, species, r, c * 16 + h * 8, v);
-            store_row8(hi, lo, r, h, v);
-        });
-    } else {
-        run_gemm(P, gs[0], load_rows(J.Y),
-                 [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
-    }
+    run_gemm(P, gs[0], load_rows(J.Y),
+             [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
     // G2: Z^T[j][i] = sum_j' Q[j][j'] (Phi o X)[i][j']   (x_2 Q_theta), data in B, rows j
     run_gemm(P, gs[1], load_rows(J.had), [&](int c, char* hi, char* lo, const Pre8& p) {
         float v[8];
@@ -1006,18 +954,101 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, Tc
 }
 
 // ------------------------------------------------------------------------------
-// Batched disks: a persistent CTA per SM takes (instance, species) items from the
-// LPT-ordered work list and runs the whole disk chain of eq. ee_disk for it --
-// F from the previous state, x_2 Q_theta^T, Hadamard, x_2 Q_theta, x_1
-// phi_1(tau d A_rho) -- writing the updated species into the other state buffer.
-__global__ void __launch_bounds__(kBlock, 1)
-    k_tc_batch(BatchTables B, TcShape sh) {
+// Batched disks: one persistent CTA per SM, launched cooperatively (all CTAs
+// resident).  Phase 1: the CTAs take (instance, 16 theta-lines) tiles from a
+// work list and evaluate F = d M w + g(w) of both species (eq. disk_discr, the
+// Schnakenberg or other reaction) into an FP32 buffer, each FP64 value split
+// once into an FP32 pair in shared memory.  A grid-wide barrier (bounded wait)
+// separates the phases.  Phase 2: the CTAs take (instance, species) items from
+// the LPT-ordered work list and run the disk chain of eq. ee_disk on F --
+// x_2 Q_theta^T, Hadamard, x_2 Q_theta, x_1 phi_1(tau d A_rho) -- writing the
+// updated species into the other state buffer.
+constexpr int kBatchTJ = 16;     // theta-lines per phase-1 tile
+
+__device__ __forceinline__ void batch_stencil_tile(const BatchInstance& I, const double* Win, float* Fout, int j0,
+                                                   float2* tile) {
+    const int n1 = I.n1, n2 = I.n2, n1q = (n1 + 3) & ~3;
+    const int lines = min(kBatchTJ, n2 - j0);
+    const int nJ = lines + 2;                           // lines j0 - 1 .. j0 + lines: one wrap at most
+    const long long n12 = (long long)n1 * n2;
+    const int per_sp = nJ * n1;
+    const int items = 2 * per_sp;
+    const uint32_t m_n1 = div_magic((uint32_t)n1);
+    for (int q = threadIdx.x; q < items; q += kBlock) {
+        const int sp = q >= per_sp;
+        const int qq = q - sp * per_sp;
+        const int jj = div_by(qq, m_n1), i = qq - jj * n1;
+        int j = j0 - 1 + jj;
+        j = j < 0 ? j + n2 : (j >= n2 ? j - n2 : j);      // theta is periodic
+        tile[q] = split_f64(__ldg(Win + sp * n12 + (long long)j * n1 + i));
+    }
+    __syncthreads();
+    const int total = lines * n1;
+    for (int q = threadIdx.x; q < total; q += kBlock) {
+        const int jl = div_by(q, m_n1), i = q - jl * n1;
+        const int j = j0 + jl;
+        const float lo1 = __ldg(I.ax_rho.lower + i), up1 = __ldg(I.ax_rho.upper + i), rs1 = __ldg(I.ax_rho.rs + i);
+        const float dr = __ldg(I.Dr + i);
+        const float rs2 = __ldg(I.ax_theta.rs + j), lo2 = __ldg(I.ax_theta.lower + j), up2 = __ldg(I.ax_theta.upper + j);
+        const int c0 = (jl + 1) * n1 + i;
+        float w[kMaxSpecies] = {0.f, 0.f, 0.f, 0.f};
+        w[0] = tile[c0].x + tile[c0].y;
+        w[1] = tile[per_sp + c0].x + tile[per_sp + c0].y;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float2* pc = tile + s * per_sp + c0;
+            const float2 c = pc[0];
+            float t0 = rs1 * (c.x + c.y);
+            if (i > 0) t0 += lo1 * sdiff(pc[-1], c);
+            if (i < n1 - 1) t0 += up1 * sdiff(pc[1], c);
+            const float t1 = rs2 * (c.x + c.y) + lo2 * sdiff(pc[-n1], c) + up2 * sdiff(pc[n1], c);
+            Fout[(long long)s * n2 * n1q + (long long)j * n1q + i] = I.d[s] * (t0 + dr * t1) + reaction<float>(I.reac, w, s);
+        }
+    }
+    __syncthreads();
+}
+
+// Grid-wide barrier of a cooperative launch, bounded: after ~2 s the waiting
+// thread records a timeout and the CTA goes on (the results are then invalid
+// and sexpe_synchronize reports SEXPE_ETIMEOUT).
+__device__ __forceinline__ void grid_barrier(int* bar, int nblocks, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1);
+        const long long t0 = clock64();
+        for (long long it = 0; it < (1LL << 32); ++it) {
+            if (*reinterpret_cast<volatile int*>(bar) >= nblocks) break;
+            if (clock64() - t0 > 4000000000LL) {
+                atomicCAS(err, 0, DERR_TIMEOUT_MMA);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBlock, 1) k_tc_batch(BatchTables B, TcShape sh) {
     extern __shared__ char smem_raw[];
     __shared__ int s_item;
     const uint32_t tmem_cols = sh.tmem_cols;
     CtaRes R = cta_begin(smem_raw, sh, B.err);
-    pdl_wait();          // previous step's state and work-list cursor
-    pdl_trigger();
+    // phase 1: F of every instance
+    float2* tile = reinterpret_cast<float2*>(R.P.mat_slots);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(B.counter + 2, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= B.n_ftiles) break;
+        const int2 t = B.ftiles[it];
+        const BatchInstance& I = B.inst[t.x];
+        batch_stencil_tile(I, B.W_in + I.w_off, B.F + I.f_off, t.y, tile);
+    }
+    grid_barrier(B.counter + 1, gridDim.x, B.err);
+    // phase 2: the chains
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(B.counter, 1);
         tc_fence_before();
@@ -1034,7 +1065,7 @@ __global__ void __launch_bounds__(kBlock, 1)
         J.n1 = I.n1;
         J.n2 = I.n2;
         J.n1q = (I.n1 + 3) & ~3;
-        J.Y = nullptr;
+        J.Y = B.F + I.f_off + (long long)s * I.n2 * J.n1q;
         J.Win = B.W_in + I.w_off + s * n12;
         J.W = B.W_out + I.w_off + s * n12;
         J.QT = I.QT;
@@ -1048,7 +1079,7 @@ __global__ void __launch_bounds__(kBlock, 1)
         slab_specs(J, R.tmem, tmem_cols, gs, cols);
         if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
         else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
-        else slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots, &I, B.W_in + I.w_off, s);
+        else slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
     }
     cta_end(R, tmem_cols);
 }
@@ -1293,10 +1324,30 @@ cudaError_t tc_prepare_batch(uint32_t smem) {
     return cudaFuncSetAttribute(k_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(B.counter, 0, sizeof(int), st);
+// Cooperative launch: every CTA resident, as the grid barrier between the phases requires.
+cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(B.counter, 0, 3 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_tc_batch, dim3(152), dim3(kBlock), sh.smem_bytes, st, B, sh);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = sh.smem_bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tc_batch, B, sh);
+}
+
+// CTAs of the batch kernel that can be resident at once (the cooperative grid).
+int batch_grid(const TcShape& sh) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_batch, kBlock, sh.smem_bytes) != cudaSuccess)
+        return 0;
+    return sms * per_sm;
 }
 
 // Self-test of the bounded-wait path every pipeline wait uses: one thread waits

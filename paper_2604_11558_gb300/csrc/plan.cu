@@ -496,7 +496,7 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
         B.W_in = p->bparity ? p->bstate : state;
         B.W_out = p->bparity ? state : p->bstate;
         SX_CUDA(prof_mark(p, st));
-        SX_CUDA(launch_tc_batch(B, p->bsh, st));
+        SX_CUDA(launch_tc_batch(B, p->bsh, p->batch_grid, st));
         p->bparity ^= 1;
         return SEXPE_OK;
     }
@@ -656,6 +656,7 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
     std::vector<Offs> offs(count);
     std::vector<BatchInstance> inst(count);
     p->inst_off.assign(count + 1, 0);
+    long long f_total = 0;
     int max_n1 = 0, max_n2 = 0;
     uint32_t tmem_cols = 32;
     for (int q = 0; q < count; ++q) {
@@ -725,6 +726,8 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
         I.ax_theta.n = n2;
         I.ax_theta.periodic = 1;
         p->inst_off[q + 1] = p->inst_off[q] + 2LL * n1 * n2;
+        I.f_off = f_total;
+        f_total += 2LL * n2 * ((n1 + 3) & ~3);
     }
     const float* base = nullptr;
     SX_TRY(upload(p, pool, &base, st));
@@ -762,6 +765,15 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
     SX_TRY(upload(p, ibytes, &dinst, st));
     const int2* ditems = nullptr;
     SX_TRY(upload(p, items, &ditems, st));
+    // phase-1 stencil tiles: 16 theta-lines of one instance each
+    std::vector<int2> ftiles;
+    for (int q = 0; q < count; ++q)
+        for (int j0 = 0; j0 < inst[q].n2; j0 += 16) ftiles.push_back(make_int2(q, j0));
+    const int2* dftiles = nullptr;
+    SX_TRY(upload(p, ftiles, &dftiles, st));
+    float* dF = nullptr;
+    SX_TRY(alloc_dev(p, (size_t)f_total, &dF));
+    SX_CUDA(cudaMemsetAsync(dF, 0, sizeof(float) * (size_t)f_total, st));   // padding columns stay zero
     SX_TRY(alloc_dev(p, 4, &p->d_err));
     SX_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st));
     int* counter = nullptr;
@@ -772,12 +784,17 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
     p->btab.items = ditems;
     p->btab.n_items = (int)items.size();
     p->btab.counter = counter;
+    p->btab.ftiles = dftiles;
+    p->btab.n_ftiles = (int)ftiles.size();
+    p->btab.F = dF;
     p->btab.tau = (float)tau;
     p->btab.err = p->d_err;
     p->bsh = tc_batch_shape(max_n1, max_n2, tmem_cols);
     if (p->bsh.tmem_cols > 512) return SEXPE_EUNSUPPORTED;
     if (p->bsh.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
     SX_CUDA(tc_prepare_batch(p->bsh.smem_bytes));
+    p->batch_grid = batch_grid(p->bsh);
+    if (p->batch_grid < 1) return SEXPE_EUNSUPPORTED;
     p->npts = p->inst_off.back() / 2;
     p->n[0] = max_n1;
     p->n[1] = max_n2;

@@ -79,5 +79,6 @@ struct sexpe_plan {
     int kernels_per_step = 0;
     double setup_ms = 0.0;
     float rhs_tj_us = 0.f;     // measured stencil time at the chosen tile height
+    int batch_grid = 0;        // CTAs of the cooperative batch launch
 };
 

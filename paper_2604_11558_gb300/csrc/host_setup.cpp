@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <stdexcept>
 
 namespace sexpe {
@@ -137,45 +138,62 @@ Eigen theta_eigen(const Axis& ax) {
     return e;
 }
 
-// Cyclic Jacobi eigen-solver for a dense symmetric matrix (rotations annihilating
-// each off-diagonal pair in turn until the off-diagonal mass is at rounding level).
-static void jacobi_symmetric(Mat& S, Mat& Q) {
-    const int n = S.n;
-    Q = Mat(n);
-    for (int i = 0; i < n; ++i) Q(i, i) = 1.0;
-    double fro = 0.0;
-    for (double v : S.a) fro += v * v;
-    fro = std::sqrt(fro);
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) off += S(p, q) * S(p, q);
-        if (std::sqrt(off) <= 1e-17 * fro) break;
-        for (int p = 0; p < n - 1; ++p) {
-            for (int q = p + 1; q < n; ++q) {
-                double apq = S(p, q);
-                if (std::fabs(apq) <= 1e-300) continue;
-                double theta = (S(q, q) - S(p, p)) / (2.0 * apq);
-                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < n; ++k) {          // columns p, q
-                    double skp = S(k, p), skq = S(k, q);
-                    S(k, p) = c * skp - s * skq;
-                    S(k, q) = s * skp + c * skq;
+// Eigen-decomposition of a symmetric tridiagonal matrix (diagonal d, off-diagonal
+// e[i] coupling i and i + 1) by the implicit QL method with Wilkinson-type shifts
+// (Bowdler, Martin, Reinsch & Wilkinson, Numer. Math. 11, 1968): each sweep
+// chases a plane rotation from the bottom of the unreduced block up to row l.
+// On return d holds the eigenvalues and row k of Zt the unit eigenvector of
+// d[k] (rows, so every rotation updates two contiguous rows).  False if an
+// eigenvalue needs more than 60 sweeps.
+static bool tridiag_ql(std::vector<double>& d, std::vector<double> e, Mat& Zt) {
+    const int n = (int)d.size();
+    e.resize(n, 0.0);
+    Zt = Mat(n);
+    for (int i = 0; i < n; ++i) Zt(i, i) = 1.0;
+    const double eps = std::numeric_limits<double>::epsilon();
+    for (int l = 0; l < n; ++l) {
+        for (int sweep = 0;; ++sweep) {
+            int m = l;
+            while (m < n - 1 && std::fabs(e[m]) > eps * (std::fabs(d[m]) + std::fabs(d[m + 1]))) ++m;
+            if (m == l) break;
+            if (sweep == 60) return false;
+            // shift: the eigenvalue of the leading 2 x 2 block nearer to d[l]
+            const double theta = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double g = d[m] - d[l] + e[l] / (theta + std::copysign(std::hypot(theta, 1.0), theta));
+            double s = 1.0, c = 1.0, p = 0.0;
+            bool deflated = false;
+            for (int i = m - 1; i >= l; --i) {
+                const double f = s * e[i], b = c * e[i];
+                const double r = std::hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {                  // the bulge vanished: split the block here
+                    d[i + 1] -= p;
+                    e[m] = 0.0;
+                    deflated = true;
+                    break;
                 }
-                for (int k = 0; k < n; ++k) {          // rows p, q
-                    double spk = S(p, k), sqk = S(q, k);
-                    S(p, k) = c * spk - s * sqk;
-                    S(q, k) = s * spk + c * sqk;
-                }
+                s = f / r;
+                c = g / r;
+                const double h = d[i + 1] - p;
+                const double t = (d[i] - h) * s + 2.0 * c * b;
+                p = s * t;
+                d[i + 1] = h + p;
+                g = c * t - b;
+                double* zi = &Zt.a[(size_t)i * n];
+                double* zj = zi + n;
                 for (int k = 0; k < n; ++k) {
-                    double qkp = Q(k, p), qkq = Q(k, q);
-                    Q(k, p) = c * qkp - s * qkq;
-                    Q(k, q) = s * qkp + c * qkq;
+                    const double zk = zj[k];
+                    zj[k] = s * zi[k] + c * zk;
+                    zi[k] = c * zi[k] - s * zk;
                 }
             }
+            if (deflated) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0.0;
         }
     }
+    return true;
 }
 
 Eigen tridiag_eigen(const Axis& ax) {
@@ -183,29 +201,32 @@ Eigen tridiag_eigen(const Axis& ax) {
     const int n = ax.n;
     std::vector<double> xi(n, 1.0);
     for (int l = 1; l < n; ++l) xi[l] = xi[l - 1] * std::sqrt(ax.lower[l] / ax.upper[l - 1]);
-    Mat S(n);
-    for (int r = 0; r < n; ++r) {
-        S(r, r) = ax.diag[r];
-        if (r < n - 1) {
-            double off = std::sqrt(ax.upper[r] * ax.lower[r + 1]);
-            S(r, r + 1) = S(r + 1, r) = off;
-        }
+    std::vector<double> dg(ax.diag.begin(), ax.diag.end()), off(n > 1 ? n - 1 : 0);
+    for (int r = 0; r + 1 < n; ++r) off[r] = std::sqrt(ax.upper[r] * ax.lower[r + 1]);
+    Mat Zt;
+    if (!tridiag_ql(dg, off, Zt)) {       // no convergence: NaN tables, reported as SEXPE_ENUMERIC
+        Eigen bad;
+        bad.lam.assign(n, std::nan(""));
+        bad.V = Mat(n);
+        bad.Vinv = Mat(n);
+        for (double& v : bad.V.a) v = std::nan("");
+        for (double& v : bad.Vinv.a) v = std::nan("");
+        return bad;
     }
-    Mat Q;
-    jacobi_symmetric(S, Q);
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return S(a, a) < S(b, b); });
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return dg[a] < dg[b]; });
     Eigen e;
     e.lam.resize(n);
     e.V = Mat(n);
     e.Vinv = Mat(n);
     for (int c = 0; c < n; ++c) {
-        int src = order[c];
-        e.lam[c] = S(src, src);
+        const int src = order[c];
+        e.lam[c] = dg[src];
+        const double* q = &Zt.a[(size_t)src * n];
         for (int r = 0; r < n; ++r) {
-            e.V(r, c) = xi[r] * Q(r, src);
-            e.Vinv(c, r) = Q(r, src) / xi[r];
+            e.V(r, c) = xi[r] * q[r];
+            e.Vinv(c, r) = q[r] / xi[r];
         }
     }
     return e;

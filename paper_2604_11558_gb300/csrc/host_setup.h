@@ -42,7 +42,7 @@ struct Eigen {
 };
 // Closed-form real Fourier eigenbasis of the circulant A_theta (orthogonal, Vinv = V^T).
 Eigen theta_eigen(const Axis& ax);
-// Proposition 1: S = Xi^{-1} A Xi symmetric, cyclic Jacobi on S, V = Xi Q, Vinv = Q^T Xi^{-1}.
+// Proposition 1: S = Xi^{-1} A Xi symmetric tridiagonal, implicit QL on S, V = Xi Q, Vinv = Q^T Xi^{-1}.
 Eigen tridiag_eigen(const Axis& ax);
 
 // phi_1(X) by [13/13] Pade scaling and squaring of expm([[X, I], [0, 0]])

@@ -858,14 +858,18 @@ sexpe_status build_adjoint(sexpe_plan* p, cudaStream_t st) {
                 const Mat Pt = transpose(phi1_pade(X));
                 std::memcpy(&PT[(size_t)s * n * n], Pt.a.data(), sizeof(double) * n * n);
                 // d phi_1(tau d A)/d d = V diag(tau lambda phi_1'(tau d lambda)) V^{-1}
-                for (int r = 0; r < n; ++r)
-                    for (int c = 0; c < n; ++c) {
-                        double acc = 0.0;
-                        for (int m = 0; m < n; ++m)
-                            acc += e.V(r, m) * p->tau * e.lam[m] * dphi1_scalar(p->tau * p->d[s] * e.lam[m]) *
-                                   e.Vinv(m, c);
-                        dP[(size_t)s * n * n + (size_t)r * n + c] = acc;
+                std::vector<double> wm(n);
+                for (int m = 0; m < n; ++m) wm[m] = p->tau * e.lam[m] * dphi1_scalar(p->tau * p->d[s] * e.lam[m]);
+                double* out = &dP[(size_t)s * n * n];
+                for (int r = 0; r < n; ++r) {
+                    double* row = out + (size_t)r * n;
+                    for (int c = 0; c < n; ++c) row[c] = 0.0;
+                    for (int m = 0; m < n; ++m) {
+                        const double vm = e.V(r, m) * wm[m];
+                        const double* vi = &e.Vinv.a[(size_t)m * n];
+                        for (int c = 0; c < n; ++c) row[c] += vm * vi[c];
                     }
+                }
             }
             if (!all_finite(PT) || !all_finite(dP)) return SEXPE_ENUMERIC;
             SX_TRY(upload(p, PT, &q.PT, st));

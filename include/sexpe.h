@@ -110,7 +110,7 @@ typedef struct {
  * disk_discr, ball_discr, syscn/A_phi, A_z), phi_1(tau d_s A_mu) of every plain
  * direction (Pade [13/13] scaling and squaring on [[tau d A, I],[0,0]]), the
  * eigenbases of the scaled directions (closed-form real Fourier basis for
- * A_theta; Proposition 1 symmetrisation + Jacobi for A_phi), the Hadamard
+ * A_theta; Proposition 1 symmetrisation + implicit QL for A_phi), the Hadamard
  * factors phi_1(tau d_s s lambda) (Section 4), then one upload to the device.
  * The plan also owns the intermediate tensors of the chain.  `stream` orders
  * the uploads.  On error *out is set to NULL. */
@@ -234,7 +234,7 @@ sexpe_status sexpe_profile_end(sexpe_plan* plan, double* kernel_ms_host, int32_t
  * sexpe_axis_matrix: A (n x n, row-major) into A_host.
  * sexpe_axis_phi1:   phi_1(t A) by the plan's Pade route into out_host (n x n).
  * sexpe_axis_eigen:  A = V diag(lam) Vinv by the plan's route (closed form for
- *                    theta, Proposition 1 + Jacobi otherwise); any output may be NULL. */
+ *                   theta, Proposition 1 + implicit QL otherwise); any output may be NULL. */
 sexpe_status sexpe_axis_matrix(int32_t axis, int32_t n, double extent, double* A_host);
 sexpe_status sexpe_axis_phi1(int32_t axis, int32_t n, double extent, double t, double* out_host);
 sexpe_status sexpe_axis_eigen(int32_t axis, int32_t n, double extent, double* lam_host, double* V_host,

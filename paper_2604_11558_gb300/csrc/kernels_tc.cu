@@ -2,22 +2,31 @@
 // for the per-step chain of the split exponential Euler method:
 //
 //   stencil pass (all geometries, SIMT): F = d M w + g(w) in FP32 from FP64-
-//       accurate differences, one shared-memory tile per CTA -> Y.
+//       accurate differences -> Y; a tiled kernel and, for the 3-D
+//       geometries, a rolling-window kernel along k (timed against each other
+//       at setup).
 //   mode-3 pass (ball, cylinder), in place on Y: F x_3 V_phi^{-1}, Hadamard
 //       Phi_{rho,.,phi}, x_3 V_phi (ball, eq. ee_ball) or F x_3 phi_1(tau d A_z)
 //       (cylinder, eq. ee_cylinder).
 //   slab pass (disk, ball, cylinder), one k-slab per CTA: Y x_2 Q_theta^T,
 //       Hadamard Phi (theta factor), x_2 Q_theta, x_1 phi_1(tau d A_rho),
 //       w += tau * result (eqs. ee_disk, ee_ball, ee_cylinder).
+//   sphere (eq. ee_sphere): Y x_2 phi_1(tau d A_phi) (N-tiled over CTAs), then
+//       x_1 Q_theta^T, Hadamard, x_1 Q_theta and the update.
+//   batched disks: one cooperative persistent launch per step, a stencil phase
+//       over every instance, a grid barrier, then the disk chain per
+//       (instance, species) item.
 //
 // Every mu-mode product is D = A B^T with FP32 accumulation in tensor memory
 // and three TF32 MMAs per K-step (lo*hi, hi*lo, hi*hi).  The constant matrix of
-// a product arrives by one TMA bulk copy per K-chunk from an image pre-laid in
-// the canonical K-major no-swizzle layout; the data operand is written by the
-// 256 threads (two per row, eight K-columns each), split into TF32 hi/lo on the
-// way.  Intermediates stay in tensor memory: a row (lane) of one product
-// becomes the row of the next operand, so the chain swaps the row mode once
-// (theta -> rho) by putting the data in the B operand of the middle product.
+// a product arrives by one TMA bulk copy per K-chunk, from an image pre-laid in
+// the canonical K-major no-swizzle layout, into a matrix ring; the data operand
+// is written into a data ring by 256 threads (two per row, eight K-columns
+// each), split into TF32 hi/lo on the way.  Intermediates stay in tensor
+// memory: a row (lane) of one product becomes the row of the next operand, so
+// the slab chain swaps the row mode once (theta -> rho) by putting the data in
+// the B operand of the middle product.  Kernels of a step are launched with
+// programmatic stream serialization (prologues overlap the previous kernel).
 #include <cuda_runtime.h>
 
 #include <algorithm>

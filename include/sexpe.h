@@ -57,12 +57,23 @@ typedef enum { SEXPE_FP64 = 0, SEXPE_SPLIT_TF32 = 1 } sexpe_precision;
  *   SCHNAKENBERG (S=2), params {gamma, a, b}: f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)
  *   GRAY_SCOTT   (S=2), params {F, k}:        f = -u v^2 + F(1-u),      g = u v^2 - (F+k) v
  *   LINEAR_CUBIC (S<=4), params K row-major S x S: f_i = sum_j K_ij u_j - u_i^3
+ *   BVAM (S=2), params {alpha1, alpha2, alpha3, beta1, beta2} (Section 5.1, eq. BVAMnl):
+ *       b = alpha1 u (1 - alpha2 v^2) + v (1 - alpha3 u),
+ *       c = beta1 v (1 + alpha1 alpha2 / beta1 u v) + u (beta2 + alpha3 v)
+ *   BVAM_MANUFACTURED (S=2, disk only): BVAM plus the sources of Section 5.1 that
+ *       make u = e^-t (1 - rho)^2 e^{cos(theta)/10}, v = e^-t (1 - rho)^2 e^{sin(theta)/10}
+ *       a solution of eq. (BVAMsys) with diffusion d = (gamma, delta): the source of u is
+ *       u_t - gamma Lap u - b(u, v) at the exact solution (polar Laplacian of eq. lapdisk
+ *       applied analytically), likewise for v; evaluated explicitly at t_n = t0 + n tau,
+ *       n the plan's steps since setup or sexpe_set_time (t0 = 0 at setup).
  *   NONE: g = 0 (any S <= 4, no params).                                            */
 typedef enum {
     SEXPE_REACTION_NONE = 0,
     SEXPE_SCHNAKENBERG = 1,
     SEXPE_GRAY_SCOTT = 2,
-    SEXPE_LINEAR_CUBIC = 3
+    SEXPE_LINEAR_CUBIC = 3,
+    SEXPE_BVAM = 4,
+    SEXPE_BVAM_MANUFACTURED = 5
 } sexpe_reaction;
 
 /* Height axis of the cylinder: NEUMANN = homogeneous Neumann at both caps
@@ -176,6 +187,12 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_h
  * captured by an earlier sexpe_step is dropped and captured again.  Host-side
  * only; call it when no step of the plan is being enqueued by another thread. */
 sexpe_status sexpe_set_stencil(sexpe_plan* plan, int32_t tile_j, int32_t planes, int32_t ctas_per_sm);
+
+/* Time of the next step of a plan with time-dependent sources
+ * (SEXPE_BVAM_MANUFACTURED): the next step evaluates its sources at t, the one
+ * after at t + tau, and so on.  Resets the plan's device step counter (ordered on
+ * `stream`); a captured step graph is dropped.  Other plans: SEXPE_OK, no effect. */
+sexpe_status sexpe_set_time(sexpe_plan* plan, double t, void* stream);
 
 /* Self-test of the failure path of every device wait (no counterpart in the
  * paper): one thread waits on a barrier nobody arrives on, with a limit of

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sexpe.h")
 
 GEOMETRY = {"disk": 0, "sphere": 1, "ball": 2, "cylinder": 3}
 PRECISION = {"fp64": 0, "split_tf32": 1}
-REACTION = {"none": 0, "schnakenberg": 1, "gray_scott": 2, "linear_cubic": 3}
+REACTION = {"none": 0, "schnakenberg": 1, "gray_scott": 2, "linear_cubic": 3, "bvam": 4, "bvam_manufactured": 5}
 ZBC = {"neumann": 0, "paper": 1}
 AXIS = {"theta": 0, "rho2": 1, "rho3": 2, "phi": 3, "z_neumann": 4, "z_paper": 5}
 STATUS = {0: "SEXPE_OK", 1: "SEXPE_EINVAL", 2: "SEXPE_ENOMEM", 3: "SEXPE_ECUDA", 4: "SEXPE_ETIMEOUT",
@@ -80,6 +80,7 @@ def lib():
         L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
         L.sexpe_set_stencil.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.sexpe_selftest_wait_timeout.argtypes = [_P]
+        L.sexpe_set_time.argtypes = [_P, ctypes.c_double, _P]
         L.sexpe_destroy.argtypes = [_P]
         L.sexpe_step_checkpointed.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
         L.sexpe_adjoint.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _DP, _P]
@@ -92,7 +93,7 @@ def lib():
                      "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
                      "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
                      "sexpe_step_checkpointed", "sexpe_adjoint", "sexpe_set_stencil",
-                     "sexpe_selftest_wait_timeout",
+                     "sexpe_selftest_wait_timeout", "sexpe_set_time",
                      "sexpe_axis_phi1", "sexpe_axis_eigen"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
@@ -171,6 +172,10 @@ class Plan:
         inf = PlanInfo()
         _check(lib().sexpe_plan_get_info(self.handle, ctypes.byref(inf)), "sexpe_plan_get_info")
         return {f: (list(getattr(inf, f)) if f in ("n", "ring_slots") else getattr(inf, f)) for f, _ in PlanInfo._fields_}
+
+    def set_time(self, t, stream=None):
+        """sexpe_set_time: time of the next step (plans with time-dependent sources)."""
+        _check(lib().sexpe_set_time(self.handle, float(t), _stream_ptr(stream)), "sexpe_set_time")
 
     def set_stencil(self, tile_j, planes=0, ctas_per_sm=1):
         """sexpe_set_stencil: override the measured stencil configuration."""

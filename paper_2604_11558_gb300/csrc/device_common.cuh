@@ -97,27 +97,63 @@ __device__ __forceinline__ typename Acc::T laplacian(const RhsTables<typename Ac
     return t0 + tb.Dr[i] * t1 + t2;   // cylinder
 }
 
+// a * b + c with one rounding, spelled out so that every kernel that inlines
+// the reaction or the stencil forms the same value (the compiler's own choice of
+// which products to fuse may differ between instantiations)
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_t(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_t(double a, double b) { return __dmul_rn(a, b); }
+
 template <class T>
 __device__ __forceinline__ T reaction(const ReactionParams<T>& rp, const T* w, int s) {
     switch (rp.kind) {
     case R_SCHNAKENBERG: {   // f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)
-        const T u2v = w[0] * w[0] * w[1];
-        return s == 0 ? rp.p[0] * (rp.p[1] - w[0] + u2v) : rp.p[0] * (rp.p[2] - u2v);
+        const T u2v = mul_t(mul_t(w[0], w[0]), w[1]);
+        return s == 0 ? mul_t(rp.p[0], (rp.p[1] - w[0]) + u2v) : mul_t(rp.p[0], rp.p[2] - u2v);
     }
     case R_GRAY_SCOTT: {     // f = -u v^2 + F(1 - u), g = u v^2 - (F + k) v
-        const T uv2 = w[0] * w[1] * w[1];
-        return s == 0 ? -uv2 + rp.p[0] * ((T)1 - w[0]) : uv2 - (rp.p[0] + rp.p[1]) * w[1];
+        const T uv2 = mul_t(mul_t(w[0], w[1]), w[1]);
+        return s == 0 ? fma_t(rp.p[0], (T)1 - w[0], -uv2) : fma_t(-(rp.p[0] + rp.p[1]), w[1], uv2);
+    }
+    case R_BVAM:
+    case R_BVAM_MMS: {       // eq. BVAMnl: b = a1 u (1 - a2 v^2) + v (1 - a3 u), c = b1 v (1 + a1 a2/b1 u v) + u (b2 + a3 v)
+        const T u = w[0], v = w[1];
+        if (s == 0)
+            return fma_t(mul_t(rp.p[0], u), fma_t(-rp.p[1], mul_t(v, v), (T)1), mul_t(v, fma_t(-rp.p[2], u, (T)1)));
+        const T q = mul_t(rp.p[0], rp.p[1]) / rp.p[3];
+        return fma_t(mul_t(rp.p[3], v), fma_t(q, mul_t(u, v), (T)1), mul_t(u, fma_t(rp.p[2], v, rp.p[4])));
     }
     case R_LINEAR_CUBIC: {   // f_i = sum_j K_ij u_j - u_i^3
-        T acc = -w[s] * w[s] * w[s];
+        T acc = -mul_t(mul_t(w[s], w[s]), w[s]);
 #pragma unroll
         for (int r = 0; r < kMaxSpecies; ++r)
-            if (r < rp.S) acc += rp.p[s * rp.S + r] * w[r];
+            if (r < rp.S) acc = fma_t(rp.p[s * rp.S + r], w[r], acc);
         return acc;
     }
     default:
         return (T)0;
     }
+}
+
+// Manufactured source of species s at disk point (rho_i, theta_j) (Section 5.1):
+// u_t - d_s Lap u - g_s(u, v) at the exact solution, whose time factor is et = e^-t.
+template <class T>
+__device__ __forceinline__ T mms_source(const RhsTables<T>& tb, int i, int j, T et, int s) {
+    const int n1 = tb.n1, n2 = tb.n2;
+    const T R = tb.mms_rho[i], LR = tb.mms_rho[n1 + i], IR2 = tb.mms_rho[2 * n1 + i];
+    const T Tt = tb.mms_theta[j], T2 = tb.mms_theta[n2 + j], Sv = tb.mms_theta[2 * n2 + j],
+            S2 = tb.mms_theta[3 * n2 + j];
+    const T eR = mul_t(et, R);
+    T w[kMaxSpecies] = {mul_t(eR, Tt), mul_t(eR, Sv), (T)0, (T)0};
+    const T lap = s == 0 ? mul_t(et, fma_t(LR, Tt, mul_t(IR2, T2))) : mul_t(et, fma_t(LR, Sv, mul_t(IR2, S2)));
+    return fma_t(-tb.d[s], lap, -w[s]) - reaction<T>(tb.reac, w, s);
+}
+
+// e^-t of the current step of a plan with manufactured sources (1 otherwise).
+template <class T>
+__device__ __forceinline__ double mms_time_factor(const RhsTables<T>& tb) {
+    return tb.reac.kind == R_BVAM_MMS ? exp(-(tb.t0 + (double)(*tb.step) * tb.tau_t)) : 1.0;
 }
 
 // F_s at flat index idx = i + n1 (j + n2 k) of species s; Wall = all species.

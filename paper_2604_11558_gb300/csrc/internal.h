@@ -5,7 +5,7 @@
 namespace sexpe {
 
 enum Geo { GEO_DISK = 0, GEO_SPHERE = 1, GEO_BALL = 2, GEO_CYLINDER = 3 };
-enum Reac { R_NONE = 0, R_SCHNAKENBERG = 1, R_GRAY_SCOTT = 2, R_LINEAR_CUBIC = 3 };
+enum Reac { R_NONE = 0, R_SCHNAKENBERG = 1, R_GRAY_SCOTT = 2, R_LINEAR_CUBIC = 3, R_BVAM = 4, R_BVAM_MMS = 5 };
 
 constexpr int kMaxSpecies = 4;
 constexpr int kMaxN = 512;
@@ -43,6 +43,13 @@ struct RhsTables {
     const T* Dp;   // sin^-2 phi_k (phi-mode index), sphere/ball
     T d[kMaxSpecies];
     ReactionParams<T> reac;
+    // manufactured sources (R_BVAM_MMS, disk): per rho_i {R, R'' + R'/rho, R/rho^2} with
+    // R = (1 - rho)^2, per theta_j {T, T'', S, S''} with T = e^{cos/10}, S = e^{sin/10};
+    // time t0 + (*step) tau
+    const T* mms_rho;
+    const T* mms_theta;
+    const long long* step;
+    double t0, tau_t;
 };
 
 // ---------------- FP64 SIMT path ------------------------------------------

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(256) k_rhs64(RhsTables<double> tb, const doubl
                                                double* __restrict__ F) {
     const long long npts = tb.npts;
     const long long total = npts * tb.S;
+    const double et = GEO == GEO_DISK ? mms_time_factor(tb) : 1.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(t / npts);
@@ -22,8 +23,18 @@ __global__ void __launch_bounds__(256) k_rhs64(RhsTables<double> tb, const doubl
         const long long rest = idx / tb.n1;
         const int j = (int)(rest % tb.n2);
         const int k = (int)(rest / tb.n2);
-        F[t] = rhs_point<F64Acc, GEO>(tb, W, s, idx, i, j, k);
+        double f = rhs_point<F64Acc, GEO>(tb, W, s, idx, i, j, k);
+        if (GEO == GEO_DISK && tb.reac.kind == R_BVAM_MMS) f += mms_source<double>(tb, i, j, et, s);
+        F[t] = f;
     }
+}
+
+// Advance the step counter of a plan with time-dependent sources (one thread).
+__global__ void k_tick(long long* step) { *step += 1; }
+
+cudaError_t launch_tick(long long* step, cudaStream_t st) {
+    k_tick<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError();
 }
 
 // C(b, r, c) = sum_k A(b, r, k) B(b, k, c), tiles of 64 x 64, K-chunks of 16,

@@ -371,7 +371,7 @@ template <int GEO>
 __device__ __forceinline__ void rhs_point(const RhsTables<float>& tb, const float2* pc, int ss, int jstride,
                                           long long km, long long kp, int dm, int dp, bool has_m, bool has_p,
                                           bool has_jm, bool has_jp, bool has_km, bool has_kp, const PointCoef& cf,
-                                          float* Fo, long long ys, float dpj) {
+                                          float* Fo, long long ys, float dpj, const float* add = nullptr) {
     const int S = tb.S;
     float w[kMaxSpecies];
 #pragma unroll
@@ -388,25 +388,27 @@ __device__ __forceinline__ void rhs_point(const RhsTables<float>& tb, const floa
         if (s >= S) break;
         const float2* q = pc + s * ss;
         const float2 c = q[0];
-        float t0 = cf.rs1 * (c.x + c.y);
-        if (has_m) t0 += cf.lo1 * sdiff(q[dm], c);
-        if (has_p) t0 += cf.up1 * sdiff(q[dp], c);
-        float t1 = cf.rs2 * (c.x + c.y);
-        if (has_jm) t1 += cf.lo2 * sdiff(q[-jstride], c);
-        if (has_jp) t1 += cf.up2 * sdiff(q[jstride], c);
+        const float cv = c.x + c.y;
+        float t0 = __fmul_rn(cf.rs1, cv);
+        if (has_m) t0 = __fmaf_rn(cf.lo1, sdiff(q[dm], c), t0);
+        if (has_p) t0 = __fmaf_rn(cf.up1, sdiff(q[dp], c), t0);
+        float t1 = __fmul_rn(cf.rs2, cv);
+        if (has_jm) t1 = __fmaf_rn(cf.lo2, sdiff(q[-jstride], c), t1);
+        if (has_jp) t1 = __fmaf_rn(cf.up2, sdiff(q[jstride], c), t1);
         float lap;
         if constexpr (GEO == GEO_DISK) {
-            lap = t0 + cf.dr * t1;
+            lap = __fmaf_rn(cf.dr, t1, t0);
         } else if constexpr (GEO == GEO_SPHERE) {
-            lap = dpj * t0 + t1;
+            lap = __fmaf_rn(dpj, t0, t1);
         } else {
-            float t2 = cf.rs3 * (c.x + c.y);
-            if (has_km) t2 += cf.lo3 * sdiff(q[km], c);
-            if (has_kp) t2 += cf.up3 * sdiff(q[kp], c);
-            if constexpr (GEO == GEO_BALL) lap = t0 + cf.dr * (cf.dp3 * t1 + t2);
-            else lap = t0 + cf.dr * t1 + t2;
+            float t2 = __fmul_rn(cf.rs3, cv);
+            if (has_km) t2 = __fmaf_rn(cf.lo3, sdiff(q[km], c), t2);
+            if (has_kp) t2 = __fmaf_rn(cf.up3, sdiff(q[kp], c), t2);
+            if constexpr (GEO == GEO_BALL) lap = __fmaf_rn(cf.dr, __fmaf_rn(cf.dp3, t1, t2), t0);
+            else lap = __fmaf_rn(cf.dr, t1, t0) + t2;
         }
-        Fo[s * ys] = tb.d[s] * lap + reaction<float>(tb.reac, w, s);
+        const float f = __fmaf_rn(tb.d[s], lap, reaction<float>(tb.reac, w, s));
+        Fo[s * ys] = add ? f + add[s] : f;
     }
 }
 
@@ -440,8 +442,10 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
         row_off[row] = ok ? sp * npts + (long long)k * n12 + (long long)j * n1 : -1;
     }
     __syncthreads();
-    pdl_wait();          // the state is the previous step's result
+    pdl_wait();          // the state (and the step counter) are the previous step's results
     pdl_trigger();
+    __shared__ float s_et;                           // e^-t of this step (manufactured sources)
+    if (GEO == GEO_DISK && threadIdx.x == 0) s_et = (float)mms_time_factor(tb);
     // tile fill: (row, i) items over all threads, kTileBatch loads in flight per thread
     const int items = rows * n1;
     for (int q0 = threadIdx.x; q0 < items; q0 += kRhsThreads * kTileBatch) {
@@ -500,11 +504,17 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_tile(RhsTables<float> tb, c
             cf.dp3 = ck[3][kl];
         }
         const int cidx = ((kl + TS::KH) * nJ + (jl + 1)) * n1 + i;
+        float src[2];
+        const bool mms = GEO == GEO_DISK && tb.reac.kind == R_BVAM_MMS;
+        if (mms) {
+            src[0] = mms_source<float>(tb, i, j, s_et, 0);
+            src[1] = mms_source<float>(tb, i, j, s_et, 1);
+        }
         rhs_point<GEO>(tb, tile + cidx, species_stride, n1, -(long long)nJ * n1, (long long)nJ * n1,
                        i > 0 ? -1 : n1 - 1, i < n1 - 1 ? 1 : 1 - n1, i > 0 || TS::periodic1,
                        i < n1 - 1 || TS::periodic1, j > 0 || TS::periodic2, j < n2 - 1 || TS::periodic2, k > 0,
                        k < n3 - 1, cf, F + ((long long)k * n2 + j) * n1q + i, ys,
-                       GEO == GEO_SPHERE ? tb.Dp[j] : 1.f);
+                       GEO == GEO_SPHERE ? tb.Dp[j] : 1.f, mms ? src : nullptr);
     }
 }
 

@@ -17,6 +17,7 @@ cudaError_t launch_adj_params(int geometry, const RhsTables<double>& tb, const d
 cudaError_t launch_wdot(const double* a, const double* b, const double* wt, long long npts, int S, double scale,
                         double* acc, cudaStream_t st);
 cudaError_t launch_scale(double* x, double a, long long n, cudaStream_t st);
+cudaError_t launch_tick(long long* step, cudaStream_t st);
 
 // Split-TF32 tensor-core path.
 // Shared-memory rings and tensor-memory columns of a tensor-core kernel.

@@ -189,6 +189,37 @@ sexpe_status build_rhs_tables(sexpe_plan* p, RhsTables<T>* tb, cudaStream_t st) 
         SX_TRY(upload(p, dp, &tb->Dp, st));
     }
     for (int s = 0; s < kMaxSpecies; ++s) tb->d[s] = (T)(s < p->S ? p->d[s] : 0.0);
+    tb->mms_rho = tb->mms_theta = nullptr;
+    tb->step = nullptr;
+    tb->t0 = 0.0;
+    tb->tau_t = p->tau;
+    if (p->reaction == SEXPE_BVAM_MANUFACTURED) {        // Section 5.1, disk: tables of the exact solution
+        const int n1 = p->n[0], n2 = p->n[1];
+        std::vector<T> mr(3 * (size_t)n1), mt(4 * (size_t)n2);
+        for (int i = 0; i < n1; ++i) {
+            const double r = p->ax[0].pts[i];
+            const double R = (1.0 - r) * (1.0 - r), dR = -2.0 * (1.0 - r), d2R = 2.0;
+            mr[i] = (T)R;
+            mr[n1 + i] = (T)(d2R + dR / r);
+            mr[2 * n1 + i] = (T)(R / (r * r));
+        }
+        for (int j = 0; j < n2; ++j) {
+            const double th = p->ax[1].pts[j], c = std::cos(th), s = std::sin(th);
+            const double Tt = std::exp(c / 10.0), Sv = std::exp(s / 10.0);
+            mt[j] = (T)Tt;
+            mt[n2 + j] = (T)(Tt * (s * s / 100.0 - c / 10.0));
+            mt[2 * n2 + j] = (T)Sv;
+            mt[3 * n2 + j] = (T)(Sv * (c * c / 100.0 - s / 10.0));
+        }
+        SX_TRY(upload(p, mr, &tb->mms_rho, st));
+        SX_TRY(upload(p, mt, &tb->mms_theta, st));
+        if (!p->d_step) {
+            SX_TRY(alloc_dev(p, 1, &p->d_step));
+            SX_CUDA(cudaMemsetAsync(p->d_step, 0, sizeof(long long), st));
+        }
+        tb->step = p->d_step;
+        tb->t0 = p->t0;
+    }
     tb->reac.kind = p->reaction;
     tb->reac.S = p->S;
     for (int q = 0; q < 16; ++q) tb->reac.p[q] = (T)(q < (int)p->params.size() ? p->params[q] : 0.0);
@@ -522,6 +553,7 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
                 x = t;
             }
         }
+        if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
         return SEXPE_OK;
     }
     SplitTables T = p->tabs;
@@ -542,6 +574,7 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
     }
     SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_tc_slab(T, p->shs, st));
+    if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
     return SEXPE_OK;
 }
 
@@ -568,6 +601,11 @@ sexpe_status validate(const sexpe_grid* g, const sexpe_species* sp, double tau, 
     case SEXPE_GRAY_SCOTT: if (sp->n_species != 2 || sp->n_params != 2) return SEXPE_EINVAL; break;
     case SEXPE_LINEAR_CUBIC:
         if (sp->n_params != sp->n_species * sp->n_species) return SEXPE_EINVAL;
+        break;
+    case SEXPE_BVAM: if (sp->n_species != 2 || sp->n_params != 5 || sp->params_host[3] == 0.0) return SEXPE_EINVAL; break;
+    case SEXPE_BVAM_MANUFACTURED:
+        if (sp->n_species != 2 || sp->n_params != 5 || sp->params_host[3] == 0.0) return SEXPE_EINVAL;
+        if (g->geometry != SEXPE_DISK) return SEXPE_EINVAL;
         break;
     default: return SEXPE_EINVAL;
     }
@@ -996,6 +1034,7 @@ sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float
     }
     if (p->ndim == 3) SX_CUDA(launch_tc_mode3(T, p->sh3, st));
     SX_CUDA(launch_tc_slab(T, p->shs, st));
+    if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
     return SEXPE_OK;
 }
 
@@ -1051,7 +1090,8 @@ sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sex
         const sexpe_status v = validate(&grids[q], &species[q], tau, precision);
         if (v != SEXPE_OK) return v;
         if (grids[q].geometry != SEXPE_DISK || species[q].n_species != 2) return SEXPE_EINVAL;
-        if (species[q].reaction == SEXPE_LINEAR_CUBIC) return SEXPE_EUNSUPPORTED;
+        if (species[q].reaction == SEXPE_LINEAR_CUBIC || species[q].reaction == SEXPE_BVAM_MANUFACTURED)
+            return SEXPE_EUNSUPPORTED;
         if (grids[q].n[0] > 128 || grids[q].n[1] > 256) return SEXPE_EUNSUPPORTED;
     }
     if (precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
@@ -1084,6 +1124,20 @@ sexpe_status sexpe_state_offsets(const sexpe_plan* plan, int64_t* offsets_host) 
     }
     offsets_host[0] = 0;
     offsets_host[1] = (int64_t)plan->S * plan->npts;
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_set_time(sexpe_plan* p, double t, void* stream) {
+    if (!p || !std::isfinite(t)) return SEXPE_EINVAL;
+    if (p->reaction != SEXPE_BVAM_MANUFACTURED || !p->d_step) return SEXPE_OK;
+    p->t0 = t;
+    p->rhs64.t0 = t;
+    p->tabs.rhs.t0 = t;
+    SX_CUDA(cudaMemsetAsync(p->d_step, 0, sizeof(long long), (cudaStream_t)stream));
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
     return SEXPE_OK;
 }
 
@@ -1233,6 +1287,7 @@ sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_c
                            const double* dL_dWT, double* dL_dW0, double* dL_dparams, void* stream) {
     if (!p || !checkpoints || !dL_dWT || !dL_dW0 || n_ckpt < 1 || every < 1) return SEXPE_EINVAL;
     if (p->precision != SEXPE_FP64) return SEXPE_EUNSUPPORTED;
+    if (p->reaction == SEXPE_BVAM || p->reaction == SEXPE_BVAM_MANUFACTURED) return SEXPE_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     try {
         SX_TRY(build_adjoint(p, st));

@@ -80,5 +80,7 @@ struct sexpe_plan {
     double setup_ms = 0.0;
     float rhs_tj_us = 0.f;     // measured stencil time at the chosen tile height
     int batch_grid = 0;        // CTAs of the cooperative batch launch
+    long long* d_step = nullptr;   // steps since setup / sexpe_set_time (time-dependent sources)
+    double t0 = 0.0;               // time of step 0 of the counter
 };
 

@@ -7,8 +7,21 @@ from oracle.operators import Grid
 from oracle.stepper import Problem, run
 
 
-def oracle_reaction(w):
+def oracle_reaction(w, g=None):
     p = w["params"]
+    if w["reaction"] in ("bvam", "bvam_manufactured"):
+        prm = dict(R.BVAM, alpha1=p[0], alpha2=p[1], alpha3=p[2], beta1=p[3], beta2=p[4],
+                   gamma=w["d"][0], delta=w["d"][1])
+        if w["reaction"] == "bvam":
+            return lambda W, t: R.bvam(W, prm)
+        rho = g.points[1][None, :]
+        th = g.points[2][:, None]
+
+        def mms(W, t):                      # sources evaluated at t_n (explicit)
+            b = R.bvam(W, prm)
+            src = R.bvam_sources(t, rho, th, prm)
+            return [b[0] + src[0], b[1] + src[1]]
+        return mms
     if w["reaction"] == "schnakenberg":
         return lambda W, t: R.schnakenberg(W, p[0], p[1], p[2])
     if w["reaction"] == "gray_scott":
@@ -22,7 +35,7 @@ def oracle_reaction(w):
 
 def oracle_run(w, steps=None):
     g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"))
-    p = Problem(g, w["d"], oracle_reaction(w), w["tau"])
+    p = Problem(g, w["d"], oracle_reaction(w, g), w["tau"])
     return run(p, w["W0"], w["steps"] if steps is None else steps)
 
 

@@ -62,6 +62,23 @@ def rho3_axis(n, rho_star=1.0):
     return rho, tridiag(a, b, c)
 
 
+def rho_lambda_axis(n, lam, rho_star=1.0):
+    """Radial axis of the anomalous operator Delta_lambda on the disk, eq. (A_lambda) of
+    Section 5.3, with homogeneous Dirichlet at rho_* (after lifting the boundary values):
+    rho_i = (1 - lam) h/2 + (i - 1) h, h = rho_*/(n + (1 - lam)/2), so rho_{n+1} = rho_*;
+    with x_l = (1 - lam)/2 + l - 1:
+    a_l = -2/(x_l^lam h^(2+lam)), b_l = (1 - lam + l - 1)/(x_l^(1+lam) h^(2+lam)),
+    c_l = l/(x_{l+1}^(1+lam) h^(2+lam))."""
+    h = rho_star / (n + (1.0 - lam) / 2.0)
+    rho = np.array([(1.0 - lam) * h / 2.0 + (i - 1) * h for i in range(1, n + 1)])
+    x = lambda l: (1.0 - lam) / 2.0 + l - 1.0
+    s = h ** (2.0 + lam)
+    a = [-2.0 / (x(l) ** lam * s) for l in range(1, n + 1)]
+    b = [(1.0 - lam + l - 1.0) / (x(l) ** (1.0 + lam) * s) for l in range(1, n)]
+    c = [l / (x(l + 1) ** (1.0 + lam) * s) for l in range(1, n)]
+    return rho, tridiag(a, b, c)
+
+
 def phi_sigma(n):
     """Root sigma in (0, 1/2) of the appendix's f(x) = cot(x pi/(n-1+2x)) - 2(n-1+2x)/pi.
 

@@ -34,10 +34,12 @@ class Grid:
     kind: 'disk' (rho, theta), 'sphere' (theta, phi), 'ball' (rho, theta, phi),
     'cylinder' (rho, theta, z); ``n`` lists the points per mode, mode 1 first.
     ``z_bc`` selects the height axis: 'neumann' (both caps) or 'paper'
-    (Neumann at 0, Dirichlet at z_*, eq. A_z).
+    (Neumann at 0, Dirichlet at z_*, eq. A_z).  ``lam`` (disk only) selects the
+    anomalous operator Delta_lambda of Section 5.3 (eq. anomalous) with
+    homogeneous Dirichlet at rho_*: A_rho from eq. (A_lambda), D_rho = rho^(-2-lam).
     """
 
-    def __init__(self, kind, n, rho_star=1.0, z_star=1.0, z_bc="neumann"):
+    def __init__(self, kind, n, rho_star=1.0, z_star=1.0, z_bc="neumann", lam=None):
         self.kind = kind
         self.n = tuple(int(v) for v in n)
         self.ndim = len(self.n)
@@ -48,13 +50,18 @@ class Grid:
         self.M = {}
         if kind == "disk":
             n1, n2 = self.n
-            rho, A_rho = ax.rho2_axis(n1, rho_star)
+            if lam is None:
+                rho, A_rho = ax.rho2_axis(n1, rho_star)
+                p = -2.0
+            else:
+                rho, A_rho = ax.rho_lambda_axis(n1, lam, rho_star)
+                p = -2.0 - lam
             theta, A_theta = ax.theta_axis(n2)
-            D_rho = np.diag(rho**-2.0)
+            D_rho = np.diag(rho**p)
             I1, I2 = np.eye(n1), np.eye(n2)
             self.points = {1: rho, 2: theta}
             self.A = {1: A_rho, 2: A_theta}
-            self.scale = {1: np.ones((1, 1)), 2: (rho**-2.0)[None, :]}
+            self.scale = {1: np.ones((1, 1)), 2: (rho**p)[None, :]}
             self.M = {1: _kron(I2, A_rho), 2: _kron(A_theta, D_rho)}        # eq. (disk)
         elif kind == "sphere":
             n1, n2 = self.n

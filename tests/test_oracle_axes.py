@@ -6,7 +6,9 @@
   (eigenpairs stated after eq. A_z), A_z with Neumann caps;
 * Proposition 1: positive off-diagonals, e^{tA} >= 0, real nonpositive
   spectrum, ||Xi||_2 = 1 and ||Xi^{-1}||_2 = sqrt(2n-3) (d=2), n-1 (d=3);
-* Appendix A: sigma in ((-(n-1)+sqrt(n^2-1))/2, 1/2) and f(sigma) = 0.
+* Appendix A: sigma in ((-(n-1)+sqrt(n^2-1))/2, 1/2) and f(sigma) = 0;
+* Delta_lambda (Section 5.3): the printed eq. (A_lambda) equals central differences of eq.
+  (anomalous) built independently, consistency order, Appendix B's closed-form Xi and bound.
 """
 import numpy as np
 import pytest
@@ -128,3 +130,72 @@ def test_sigma_appendix_bounds():
     s = ax.phi_sigma(n)
     h = np.pi / (n - 1 + 2 * s)
     assert np.isclose(h, (np.pi - 2 * s * h) / (n - 1))
+
+
+# ---- anomalous diffusion Delta_lambda on the disk (Section 5.3, Appendix B) ----
+LAMBDAS = [-1.95, -1.0, 0.0, 0.5]
+
+
+def _central_difference_lambda(n, lam, rho_star=1.0):
+    """Delta_lambda's radial part (eq. anomalous), (1-lam)/rho^(1+lam) f' + f''/rho^lam, by
+    central differences at the grid points of eq. (A_lambda), u = 0 at rho_{n+1} = rho_*:
+    built from the definition, independently of the printed a_l, b_l, c_l."""
+    h = rho_star / (n + (1.0 - lam) / 2.0)
+    rho = (1.0 - lam) * h / 2.0 + h * np.arange(n)
+    A = np.zeros((n, n))
+    for i in range(n):
+        d2 = 1.0 / (rho[i] ** lam * h * h)
+        d1 = (1.0 - lam) / (rho[i] ** (1.0 + lam) * 2.0 * h)
+        A[i, i] = -2.0 * d2
+        if i > 0:
+            A[i, i - 1] = d2 - d1
+        if i < n - 1:
+            A[i, i + 1] = d2 + d1
+    return rho, A
+
+
+@pytest.mark.parametrize("lam", LAMBDAS)
+def test_lambda_axis_equals_its_definition(lam):
+    """The printed a_l, b_l, c_l of eq. (A_lambda) are the central differences of eq. (anomalous);
+    the coefficient of u_0 vanishes (x_1 - (1-lam)/2 = 0), so no condition at rho = 0 is needed."""
+    for n in [4, 17, 60]:
+        rho, A = ax.rho_lambda_axis(n, lam)
+        rho_d, A_d = _central_difference_lambda(n, lam)
+        assert np.allclose(rho, rho_d, rtol=0, atol=1e-15)
+        assert np.max(np.abs(A - A_d)) <= 1e-12 * np.max(np.abs(A))
+        h = 1.0 / (n + (1.0 - lam) / 2.0)
+        assert np.isclose(rho[-1] + h, 1.0)                   # Dirichlet point rho_{n+1} = rho_*
+
+
+@pytest.mark.parametrize("lam", [-1.95, 0.0, 0.5])
+def test_lambda_axis_consistency_order(lam):
+    """Consistency with the continuous operator on f = cos(pi rho / 2) (f(rho_*) = 0, even at 0):
+    second order for lam <= 0; for lam > 0 the coefficient 1/rho^(1+lam) is singular at the
+    origin and the first points' error decays like h^(2-lam)."""
+    f = lambda r: np.cos(np.pi * r / 2)
+    Lf = lambda r: ((1 - lam) / r ** (1 + lam) * (-np.pi / 2 * np.sin(np.pi * r / 2))
+                    - (np.pi / 2) ** 2 * np.cos(np.pi * r / 2) / r ** lam)
+    errs = _max_err(lambda n: ax.rho_lambda_axis(n, lam), f, Lf, [40, 80, 160])
+    ratio = 0.9 * 2.0 ** min(2.0, 2.0 - lam)
+    assert errs[0] / errs[1] > ratio and errs[1] / errs[2] > ratio, errs
+
+
+def test_lambda_axis_appendix_b():
+    """Appendix B: xi_l^2 = ((1-lam)/((2l-1)-lam))^(1+lam) (l-1)!/prod_{i<l}(i-lam); the largest entry
+    of Xi^{-1} is 1/xi_n for lam < 0, below sqrt(((2n-1-lam)/(1-lam))^(1+lam) e^{-lam(ln(n-1)+1)});
+    an essentially nonnegative matrix with negative eigenvalues."""
+    from math import lgamma
+    for lam in [-1.95, -1.0, -0.3]:
+        for n in [5, 40, 160]:
+            _, A = ax.rho_lambda_axis(n, lam)
+            xi = ax.xi_diagonal(A)
+            for l in range(2, n + 1):
+                log_p = sum(np.log(i - lam) for i in range(1, l)) - lgamma(l)
+                ref = np.sqrt(((1 - lam) / ((2 * l - 1) - lam)) ** (1 + lam) * np.exp(-log_p))
+                assert np.isclose(xi[l - 1], ref, rtol=1e-10), (lam, n, l)
+            assert np.isclose(np.max(1 / xi), 1 / xi[-1])
+            bound = np.sqrt(((2 * n - 1 - lam) / (1 - lam)) ** (1 + lam) * np.exp(-lam * (np.log(n - 1) + 1)))
+            assert 1 / xi[-1] < bound
+            off = A - np.diag(np.diag(A))
+            assert np.all(off >= 0)
+            assert np.max(np.linalg.eigvals(A).real) < 0

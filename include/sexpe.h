@@ -88,6 +88,11 @@ typedef struct {
     double rho_star;    /* radius of disk/ball/cylinder (> 0); sphere is the unit sphere  */
     double z_star;      /* cylinder height (> 0)                                          */
     int32_t z_bc;       /* sexpe_zbc (cylinder only)                                      */
+    int32_t rho_op;     /* disk only: 0 = Laplacian, Neumann at rho_* (eq. disk_discr);     */
+                        /* 1 = anomalous Delta_lambda (Section 5.3, eq. anomalous) with     */
+                        /* homogeneous Dirichlet at rho_* (eq. A_lambda; lift constant      */
+                        /* boundary values with sexpe_species.offset_host), D_rho = rho^(-2-lambda) */
+    double lambda;      /* exponent of Delta_lambda, -3 < lambda < 1 (rho_op = 1)          */
 } sexpe_grid;
 
 typedef struct {
@@ -96,6 +101,9 @@ typedef struct {
     int32_t reaction;       /* sexpe_reaction                                             */
     int32_t n_params;       /* number of entries in params_host                           */
     const double* params_host;
+    const double* offset_host;   /* n_species values c_s or NULL (= 0): the reactions see w_s + c_s,
+                                    the lifting of constant Dirichlet boundary values c_s (the
+                                    state is w = u - c); FP64 adjoint and batches need NULL   */
 } sexpe_species;
 
 typedef struct sexpe_plan sexpe_plan;

@@ -35,13 +35,14 @@ class SexpeError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("geometry", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("rho_star", ctypes.c_double),
-                ("z_star", ctypes.c_double), ("z_bc", ctypes.c_int32)]
+                ("z_star", ctypes.c_double), ("z_bc", ctypes.c_int32), ("rho_op", ctypes.c_int32),
+                ("lam", ctypes.c_double)]
 
 
 class Species(ctypes.Structure):
     _fields_ = [("n_species", ctypes.c_int32), ("d_host", ctypes.POINTER(ctypes.c_double)),
                 ("reaction", ctypes.c_int32), ("n_params", ctypes.c_int32),
-                ("params_host", ctypes.POINTER(ctypes.c_double))]
+                ("params_host", ctypes.POINTER(ctypes.c_double)), ("offset_host", ctypes.POINTER(ctypes.c_double))]
 
 
 class PlanInfo(ctypes.Structure):
@@ -149,12 +150,18 @@ class Plan:
     """A plan of the split exponential Euler step (wraps sexpe_setup / sexpe_batch_setup)."""
 
     def __init__(self, geometry, n, d, reaction="none", params=(), tau=1e-3, precision="split_tf32",
-                 rho_star=1.0, z_star=1.0, z_bc="neumann", stream=None):
+                 rho_star=1.0, z_star=1.0, z_bc="neumann", stream=None, lam=None, offsets=None):
+        """lam: exponent of the anomalous operator Delta_lambda on the disk (Dirichlet at rho_*);
+        offsets: per-species lifting constants the reactions add to the state."""
         L = lib()
         self._d = np.ascontiguousarray(d, dtype=np.float64)
         self._p = np.ascontiguousarray(params if len(params) else [0.0], dtype=np.float64)
         grid = _grid_struct(geometry, n, rho_star, z_star, z_bc)
-        sp = Species(len(self._d), _dptr(self._d), REACTION[reaction], len(params), _dptr(self._p))
+        if lam is not None:
+            grid.rho_op, grid.lam = 1, float(lam)
+        self._off = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.float64)
+        sp = Species(len(self._d), _dptr(self._d), REACTION[reaction], len(params), _dptr(self._p),
+                     None if self._off is None else _dptr(self._off))
         h = _P()
         st = _stream_ptr(stream) if stream is not None else 0
         _check(L.sexpe_setup(ctypes.byref(grid), ctypes.byref(sp), float(tau), PRECISION[precision], st,
@@ -166,7 +173,7 @@ class Plan:
     @classmethod
     def from_workload(cls, w, precision="split_tf32", stream=None):
         return cls(w["geometry"], w["n"], w["d"], w["reaction"], w["params"], w["tau"], precision,
-                   stream=stream)
+                   stream=stream, lam=w.get("lam"), offsets=w.get("offsets"))
 
     def info(self):
         inf = PlanInfo()

@@ -106,7 +106,20 @@ __device__ __forceinline__ float mul_t(float a, float b) { return __fmul_rn(a, b
 __device__ __forceinline__ double mul_t(double a, double b) { return __dmul_rn(a, b); }
 
 template <class T>
-__device__ __forceinline__ T reaction(const ReactionParams<T>& rp, const T* w, int s) {
+__device__ __forceinline__ T reaction(const ReactionParams<T>& rp, const T* w_state, int s) {
+    if (rp.lifted) {
+        // Schnakenberg about the lifting constants c (the polynomial expanded exactly, so that
+        // every term is small when w is and keeps the arithmetic's relative accuracy):
+        // b(c + w) = b(c) - w_u + N + Q, c(c + w) = c(c) - N - Q with
+        // N = 2 c_u c_v w_u + c_u^2 w_v, Q = w_u (c_v w_u + 2 c_u w_v + w_u w_v)
+        const T wu = w_state[0], wv = w_state[1];
+        const T N = fma_t(rp.q[2], wu, mul_t(rp.q[3], wv));
+        const T Q = mul_t(wu, fma_t(rp.q[4], wu, fma_t(rp.q[5], wv, mul_t(wu, wv))));
+        return s == 0 ? mul_t(rp.p[0], (N + Q - wu) + rp.q[0]) : mul_t(rp.p[0], rp.q[1] - (N + Q));
+    }
+    T w[kMaxSpecies];
+#pragma unroll
+    for (int r = 0; r < kMaxSpecies; ++r) w[r] = w_state[r] + rp.off[r];    // lifted boundary values
     switch (rp.kind) {
     case R_SCHNAKENBERG: {   // f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)
         const T u2v = mul_t(mul_t(w[0], w[0]), w[1]);

@@ -38,7 +38,7 @@ double phi_sigma(int n) {
     return 0.5 * (lo + hi);
 }
 
-Axis build_axis(AxisKind kind, int n, double extent) {
+Axis build_axis(AxisKind kind, int n, double extent, double lambda) {
     Axis ax;
     ax.n = n;
     ax.pts.assign(n, 0.0);
@@ -46,6 +46,21 @@ Axis build_axis(AxisKind kind, int n, double extent) {
     ax.diag.assign(n, 0.0);
     ax.upper.assign(n, 0.0);
     double h = 0.0;
+    if (kind == AX_RHO_LAMBDA) {
+        // eq. (A_lambda): rho_i = (1 - lambda) h/2 + (i - 1) h, h = rho_*/(n + (1 - lambda)/2);
+        // x_l = (1 - lambda)/2 + l - 1; a_l = -2/(x_l^lambda h^(2+lambda)),
+        // b_l = (1 - lambda + l - 1)/(x_l^(1+lambda) h^(2+lambda)), c_l = l/(x_{l+1}^(1+lambda) h^(2+lambda))
+        h = extent / (n + 0.5 * (1.0 - lambda));
+        const double s = std::pow(h, 2.0 + lambda);
+        auto x = [&](int l) { return 0.5 * (1.0 - lambda) + l - 1.0; };
+        for (int i = 0; i < n; ++i) ax.pts[i] = 0.5 * (1.0 - lambda) * h + i * h;
+        for (int l = 1; l <= n; ++l) ax.diag[l - 1] = -2.0 / (std::pow(x(l), lambda) * s);
+        for (int l = 1; l <= n - 1; ++l) {
+            ax.upper[l - 1] = (1.0 - lambda + l - 1.0) / (std::pow(x(l), 1.0 + lambda) * s);   // b_l
+            ax.lower[l] = l / (std::pow(x(l + 1), 1.0 + lambda) * s);                       // c_l
+        }
+        return ax;
+    }
     switch (kind) {
     case AX_THETA:  // eq. (A_theta): theta_j = j h, h = 2 pi/n, periodic
         h = 2.0 * kPi / n;
@@ -93,6 +108,8 @@ Axis build_axis(AxisKind kind, int n, double extent) {
         ax.upper[0] = 2.0 / (h * h);
         ax.lower[n - 1] = 2.0 / (h * h);
         break;
+    case AX_RHO_LAMBDA:
+        break;                                                       // built above
     case AX_Z_PAPER:    // eq. (A_z): Neumann at 0, Dirichlet at z_*, h = z_*/n
         h = extent / n;
         for (int k = 0; k < n; ++k) {

@@ -27,10 +27,12 @@ struct Axis {
     Mat dense() const;
 };
 
-enum AxisKind { AX_THETA, AX_RHO2, AX_RHO3, AX_PHI, AX_Z_NEUMANN, AX_Z_PAPER };
+enum AxisKind { AX_THETA, AX_RHO2, AX_RHO3, AX_PHI, AX_Z_NEUMANN, AX_Z_PAPER, AX_RHO_LAMBDA };
 
-// Section 3: eq. (A_theta), (disk_discr), (ball_discr), (syscn)/(A_phi), (A_z).
-Axis build_axis(AxisKind kind, int n, double extent);
+// Section 3: eq. (A_theta), (disk_discr), (ball_discr), (syscn)/(A_phi), (A_z);
+// Section 5.3: eq. (A_lambda), Delta_lambda's radial part with Dirichlet at rho_*
+// (lambda < 1; the diagonal varies by row).
+Axis build_axis(AxisKind kind, int n, double extent, double lambda = 0.0);
 
 // Root of cot(x pi/(n-1+2x)) - 2(n-1+2x)/pi on (0, 1/2) (Appendix A).
 double phi_sigma(int n);

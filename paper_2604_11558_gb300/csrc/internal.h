@@ -29,6 +29,10 @@ struct ReactionParams {
     int kind;
     int S;
     T p[16];     // in the arithmetic type of the kernels that read them (no conversions on the device)
+    T off[kMaxSpecies];   // lifting offsets: the reaction sees w_s + off_s
+    int lifted;           // Schnakenberg with offsets: evaluated in the exact expansion about off
+    T q[6];               // its coefficients (FP64 on the host): g_u(c)/gamma, g_v(c)/gamma, 2 c_u c_v,
+                          // c_u^2, c_v, 2 c_u
 };
 
 // Everything the stencil+reaction evaluation needs (values of type T).

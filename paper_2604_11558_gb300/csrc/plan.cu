@@ -61,7 +61,7 @@ sexpe_status alloc_dev(sexpe_plan* p, size_t count, T** out) {
 // Scale factor of direction mu at grid point (i, j, k): the diagonal factors of
 // the other modes in the Kronecker term M_mu (Section 2).
 double dir_scale(const sexpe_plan* p, int mu, int i, int j, int k) {
-    auto Dr = [&](int ii) { double r = p->ax[0].pts[ii]; return 1.0 / (r * r); };
+    auto Dr = [&](int ii) { return std::pow(p->ax[0].pts[ii], p->rho_pow); };
     auto Dp = [&](int m, int kk) { double s = std::sin(p->ax[m].pts[kk]); return 1.0 / (s * s); };
     switch (p->geometry) {
     case SEXPE_DISK: return mu == 2 ? Dr(i) : 1.0;
@@ -176,7 +176,7 @@ sexpe_status build_rhs_tables(sexpe_plan* p, RhsTables<T>* tb, cudaStream_t st) 
     tb->Dp = nullptr;
     if (p->geometry != SEXPE_SPHERE) {
         std::vector<T> dr(p->n[0]);
-        for (int i = 0; i < p->n[0]; ++i) dr[i] = (T)(1.0 / (p->ax[0].pts[i] * p->ax[0].pts[i]));
+        for (int i = 0; i < p->n[0]; ++i) dr[i] = (T)std::pow(p->ax[0].pts[i], p->rho_pow);
         SX_TRY(upload(p, dr, &tb->Dr, st));
     }
     if (p->geometry == SEXPE_SPHERE || p->geometry == SEXPE_BALL) {
@@ -222,6 +222,21 @@ sexpe_status build_rhs_tables(sexpe_plan* p, RhsTables<T>* tb, cudaStream_t st) 
     }
     tb->reac.kind = p->reaction;
     tb->reac.S = p->S;
+    for (int s = 0; s < kMaxSpecies; ++s) tb->reac.off[s] = (T)(s < (int)p->offset.size() ? p->offset[s] : 0.0);
+    tb->reac.lifted = 0;
+    for (int q = 0; q < 6; ++q) tb->reac.q[q] = (T)0;
+    if (p->reaction == SEXPE_SCHNAKENBERG && !p->offset.empty()) {
+        // b(c), c(c) are differences of O(1) terms that nearly cancel at a steady state and are
+        // then multiplied by gamma: formed in extended precision, rounded once
+        const long double cu = p->offset[0], cv = p->offset[1], a = p->params[1], b = p->params[2];
+        tb->reac.lifted = 1;
+        tb->reac.q[0] = (T)(double)(a - cu + cu * cu * cv);
+        tb->reac.q[1] = (T)(double)(b - cu * cu * cv);
+        tb->reac.q[2] = (T)(double)(2.0L * cu * cv);
+        tb->reac.q[3] = (T)(double)(cu * cu);
+        tb->reac.q[4] = (T)(double)cv;
+        tb->reac.q[5] = (T)(double)(2.0L * cu);
+    }
     for (int q = 0; q < 16; ++q) tb->reac.p[q] = (T)(q < (int)p->params.size() ? p->params[q] : 0.0);
     return SEXPE_OK;
 }
@@ -595,6 +610,11 @@ sexpe_status validate(const sexpe_grid* g, const sexpe_species* sp, double tau, 
     for (int s = 0; s < sp->n_species; ++s)
         if (!(sp->d_host[s] > 0.0) || !std::isfinite(sp->d_host[s])) return SEXPE_EINVAL;
     if (sp->n_params < 0 || sp->n_params > 16 || (sp->n_params > 0 && !sp->params_host)) return SEXPE_EINVAL;
+    if (g->rho_op != 0 && g->rho_op != 1) return SEXPE_EINVAL;
+    if (g->rho_op == 1 && (g->geometry != SEXPE_DISK || !(g->lambda > -3.0 && g->lambda < 1.0))) return SEXPE_EINVAL;
+    if (sp->offset_host)
+        for (int s = 0; s < sp->n_species; ++s)
+            if (!std::isfinite(sp->offset_host[s])) return SEXPE_EINVAL;
     switch (sp->reaction) {
     case SEXPE_REACTION_NONE: break;
     case SEXPE_SCHNAKENBERG: if (sp->n_species != 2 || sp->n_params != 3) return SEXPE_EINVAL; break;
@@ -641,9 +661,15 @@ sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species*
     p->d.assign(sp->d_host, sp->d_host + sp->n_species);
     p->params.assign(sp->params_host, sp->params_host + sp->n_params);
     p->reaction = sp->reaction;
+    if (sp->offset_host) p->offset.assign(sp->offset_host, sp->offset_host + sp->n_species);
     switch (g->geometry) {
     case SEXPE_DISK:
-        p->ax[0] = build_axis(AX_RHO2, p->n[0], g->rho_star);
+        if (g->rho_op == 1) {
+            p->ax[0] = build_axis(AX_RHO_LAMBDA, p->n[0], g->rho_star, g->lambda);
+            p->rho_pow = -2.0 - g->lambda;
+        } else {
+            p->ax[0] = build_axis(AX_RHO2, p->n[0], g->rho_star);
+        }
         p->ax[1] = build_axis(AX_THETA, p->n[1], 0.0);
         break;
     case SEXPE_SPHERE:
@@ -1092,6 +1118,7 @@ sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sex
         if (grids[q].geometry != SEXPE_DISK || species[q].n_species != 2) return SEXPE_EINVAL;
         if (species[q].reaction == SEXPE_LINEAR_CUBIC || species[q].reaction == SEXPE_BVAM_MANUFACTURED)
             return SEXPE_EUNSUPPORTED;
+        if (grids[q].rho_op != 0 || species[q].offset_host) return SEXPE_EUNSUPPORTED;
         if (grids[q].n[0] > 128 || grids[q].n[1] > 256) return SEXPE_EUNSUPPORTED;
     }
     if (precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
@@ -1288,6 +1315,8 @@ sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_c
     if (!p || !checkpoints || !dL_dWT || !dL_dW0 || n_ckpt < 1 || every < 1) return SEXPE_EINVAL;
     if (p->precision != SEXPE_FP64) return SEXPE_EUNSUPPORTED;
     if (p->reaction == SEXPE_BVAM || p->reaction == SEXPE_BVAM_MANUFACTURED) return SEXPE_EUNSUPPORTED;
+    for (double c : p->offset)
+        if (c != 0.0) return SEXPE_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     try {
         SX_TRY(build_adjoint(p, st));

@@ -81,6 +81,8 @@ struct sexpe_plan {
     float rhs_tj_us = 0.f;     // measured stencil time at the chosen tile height
     int batch_grid = 0;        // CTAs of the cooperative batch launch
     long long* d_step = nullptr;   // steps since setup / sexpe_set_time (time-dependent sources)
+    std::vector<double> offset;    // lifting offsets of the reactions (empty = 0)
+    double rho_pow = -2.0;         // D_rho = rho^rho_pow (disk: -2, or -2 - lambda for Delta_lambda)
     double t0 = 0.0;               // time of step 0 of the counter
 };
 

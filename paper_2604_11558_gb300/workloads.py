@@ -112,6 +112,23 @@ def schnakenberg_sphere(n=(256, 512), steps=1000, seed=6, gamma=200.0, a=0.1, b=
                 noise=noise)
 
 
+def anomalous_disk(n=(160, 160), steps=25000, seed=7, lam=-1.95, tau=1e-5):
+    """Schnakenberg with anomalous diffusion on the unit disk (Section 5.3, eq. schnak):
+    u_t = Delta_lambda u + alpha1 b(u, v), v_t = delta Delta_lambda v + alpha1 c(u, v),
+    b = alpha2 - u + u^2 v, c = beta1 - u^2 v, alpha1 = 500, alpha2 = 0.14, beta1 = 1.34,
+    delta = 50, lambda = -1.95; boundary values (u_e, v_e) = (alpha2 + beta1, beta1/(alpha2 + beta1)^2),
+    the uniform steady state.  The state is lifted, w = (u - u_e, v - v_e), with homogeneous
+    Dirichlet boundary values; the reaction sees w + (u_e, v_e).  Initial data: 1e-5 U(0, 1) per
+    point and species.  (The paper does not state tau; 25000 steps are its step count.)"""
+    rng = _rng(seed)
+    a1, a2, b1, delta = 500.0, 0.14, 1.34, 50.0
+    ue, ve = a2 + b1, b1 / (a2 + b1) ** 2
+    shp = _shape(n)
+    W0 = np.stack([1e-5 * rng.uniform(0.0, 1.0, shp), 1e-5 * rng.uniform(0.0, 1.0, shp)])
+    return dict(geometry="disk", n=tuple(n), d=[1.0, delta], reaction="schnakenberg", params=[a1, a2, b1],
+                tau=tau, steps=steps, W0=W0, seed=seed, lam=lam, offsets=[ue, ve], name="anomalous_disk")
+
+
 def random_state(geometry, n, S=2, seed=7, scale=0.1, offset=0.5):
     """Generic seeded field for parity tests: offset + scale * N(0, 1) per point and species."""
     rng = _rng(seed)

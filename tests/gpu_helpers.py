@@ -8,6 +8,21 @@ from oracle.stepper import Problem, run
 
 
 def oracle_reaction(w, g=None):
+    """The workload's reaction for the oracle; with lifting offsets c_s it sees W_s + c_s.  That
+    evaluation runs in extended precision (numpy longdouble) and is rounded once: for W small
+    against c the FP64 formula would cancel to ~eps |c| / |W| relative accuracy."""
+    base = _oracle_reaction(w, g)
+    off = w.get("offsets")
+    if off is None:
+        return base
+
+    def lifted(W, t):
+        ext = [np.asarray(W[s], dtype=np.longdouble) + np.longdouble(off[s]) for s in range(len(W))]
+        return [np.asarray(r, dtype=np.float64) for r in base(ext, t)]
+    return lifted
+
+
+def _oracle_reaction(w, g=None):
     p = w["params"]
     if w["reaction"] in ("bvam", "bvam_manufactured"):
         prm = dict(R.BVAM, alpha1=p[0], alpha2=p[1], alpha3=p[2], beta1=p[3], beta2=p[4],
@@ -34,7 +49,7 @@ def oracle_reaction(w, g=None):
 
 
 def oracle_run(w, steps=None):
-    g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"))
+    g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"), lam=w.get("lam"))
     p = Problem(g, w["d"], oracle_reaction(w, g), w["tau"])
     return run(p, w["W0"], w["steps"] if steps is None else steps)
 
@@ -43,8 +58,8 @@ def emulated_fp32_errors(w, ref, increments=False):
     """Per-species relative error of the oracle run with FP32 storage of F, of every
     direction's result and of the increment (the storage floor of an FP32 chain); with
     `increments`, also the relative error of W_n - W_0."""
-    g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"))
-    p = Problem(g, w["d"], oracle_reaction(w), w["tau"])
+    g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"), lam=w.get("lam"))
+    p = Problem(g, w["d"], oracle_reaction(w, g), w["tau"])
     emu = run(p, w["W0"], w["steps"], fp32_storage=True)
     if not increments:
         return rel_errors(emu, ref)
@@ -61,7 +76,7 @@ def gpu_run(w, precision, steps=None, single_calls=False, stencil=None):
     import torch
     from paper_2604_11558_gb300 import binding
     plan = binding.Plan(w["geometry"], w["n"], w["d"], w["reaction"], w["params"], w["tau"], precision,
-                        z_bc=w.get("z_bc", "neumann"))
+                        z_bc=w.get("z_bc", "neumann"), lam=w.get("lam"), offsets=w.get("offsets"))
     if stencil is not None:
         plan.set_stencil(*stencil)
     x = torch.from_numpy(np.ascontiguousarray(w["W0"])).cuda()

@@ -404,6 +404,8 @@ def measure_extras(flush):
         plan.step(x, 2)
         ms, kms = timed_steps(plan, x, steps, flush, profile=True)
         res[prec] = {"ms_per_step": sum(ms) / steps, "value": dof * steps / (sum(ms) / 1e3), "kernel_ms": kms}
+        if prec == "split_tf32":
+            res[prec]["theta_split"] = plan.info()["theta_split"]
         plan.close()
     out["sphere_256x512_2species"] = {"unit": UNIT, "dof": dof, **res}
     # batched disks

@@ -123,6 +123,9 @@ typedef struct {
     int32_t stencil_planes;     /* split path: 0 = tiled stencil kernel, else k-planes per CTA
                                    of the rolling-window kernel (measured at setup)          */
     int32_t stencil_ctas_per_sm; /* split path: CTAs per SM the stencil's registers allow    */
+    int32_t theta_split;        /* split sphere: CTAs sharing one row tile of the theta kernel,
+                                   each with n_theta_pad / theta_split output columns
+                                   (measured at setup); 0 elsewhere                         */
 } sexpe_plan_info;
 
 /* Build a plan: FP64 host setup of the 1-D axes (Section 3: eqs. A_theta,
@@ -195,6 +198,16 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_h
  * captured by an earlier sexpe_step is dropped and captured again.  Host-side
  * only; call it when no step of the plan is being enqueued by another thread. */
 sexpe_status sexpe_set_stencil(sexpe_plan* plan, int32_t tile_j, int32_t planes, int32_t ctas_per_sm);
+
+/* Override the theta-kernel column split that sexpe_setup measured for a split
+ * sphere plan (no counterpart in the paper).  The theta step of eq. ee_sphere
+ * is two products per tile of 128 phi rows, x_1 Q_theta^T, the Hadamard factor,
+ * then x_1 Q_theta with the update; the second can be split by output theta
+ * columns over `split` CTAs (1, 2, 4 or 8, n_theta rounded up to 16 divisible
+ * by 16 * split), each repeating the first product.  A split the setup did not
+ * build gives SEXPE_EINVAL, other plans SEXPE_EUNSUPPORTED.  A graph captured
+ * by an earlier sexpe_step is dropped.  Host-side only, like sexpe_set_stencil. */
+sexpe_status sexpe_set_theta_split(sexpe_plan* plan, int32_t split);
 
 /* Time of the next step of a plan with time-dependent sources
  * (SEXPE_BVAM_MANUFACTURED): the next step evaluates its sources at t, the one

@@ -52,7 +52,7 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
                 ("stencil_tile_j", ctypes.c_int32), ("ring_slots", ctypes.c_int32 * 2),
                 ("stencil_tile_us", ctypes.c_float), ("stencil_planes", ctypes.c_int32),
-                ("stencil_ctas_per_sm", ctypes.c_int32)]
+                ("stencil_ctas_per_sm", ctypes.c_int32), ("theta_split", ctypes.c_int32)]
 
 
 _lib = None
@@ -80,6 +80,7 @@ def lib():
         L.sexpe_synchronize.argtypes = [_P, _P]
         L.sexpe_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
         L.sexpe_set_stencil.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.sexpe_set_theta_split.argtypes = [_P, ctypes.c_int32]
         L.sexpe_selftest_wait_timeout.argtypes = [_P]
         L.sexpe_set_time.argtypes = [_P, ctypes.c_double, _P]
         L.sexpe_destroy.argtypes = [_P]
@@ -94,7 +95,7 @@ def lib():
                      "sexpe_synchronize", "sexpe_plan_get_info", "sexpe_destroy", "sexpe_axis_matrix",
                      "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
                      "sexpe_step_checkpointed", "sexpe_adjoint", "sexpe_set_stencil",
-                     "sexpe_selftest_wait_timeout", "sexpe_set_time",
+                     "sexpe_set_theta_split", "sexpe_selftest_wait_timeout", "sexpe_set_time",
                      "sexpe_axis_phi1", "sexpe_axis_eigen"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
@@ -187,6 +188,10 @@ class Plan:
     def set_stencil(self, tile_j, planes=0, ctas_per_sm=1):
         """sexpe_set_stencil: override the measured stencil configuration."""
         _check(lib().sexpe_set_stencil(self.handle, int(tile_j), int(planes), int(ctas_per_sm)), "sexpe_set_stencil")
+
+    def set_theta_split(self, split):
+        """sexpe_set_theta_split: override the measured theta-kernel column split of a sphere plan."""
+        _check(lib().sexpe_set_theta_split(self.handle, int(split)), "sexpe_set_theta_split")
 
     def step(self, state, n_steps, stream=None):
         _check(lib().sexpe_step(self.handle, _data_ptr(state), int(n_steps), _stream_ptr(stream)), "sexpe_step")

@@ -113,6 +113,8 @@ struct SplitTables {
     int phi_nt;                    // output phi rows per CTA of the phi product
     float* Y2;                     // phi product output, layout of Y
     const float* had_sph;          // phi_1(tau d_s sin^-2 phi_j lambda_theta'), [s][j][n1q]
+    Image Qsph;                    // Q_theta as B operand of the second theta product, N-tiled by th_nt rows
+    int th_nt;                     // output theta columns per CTA of the theta kernel
     int* err;
     int rhs_tj;                    // j-lines per stencil tile (chosen by measurement at setup; 0 = model)
     int rhs_ks;                    // 0: tiled stencil kernel; > 0: rolling-window kernel, planes per CTA

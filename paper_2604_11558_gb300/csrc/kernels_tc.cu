@@ -722,15 +722,15 @@ __device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, uint
 }
 
 // Update of up to 128 state rows from an FP32 accumulator in tensor memory:
-// W[row][i] = Win[row][i] + tau * D[row][i] for row < rows, i < n1, with D at
-// tensor-memory columns [dcol, dcol + n1p) of lane `row` and the rows n1
-// apart in global memory.  The accumulator is staged through shared memory
-// (`epi`, 128 (n1p + 1) floats) so the FP64 read-modify-write is coalesced;
-// the increment is rounded to FP32 and widened exactly by integer operations:
-// one FP64 add per point, eight independent read-modify-writes in flight per
-// thread.  Called by the 256 producer threads.
+// W[row * stride + i] = Win[...] + tau * D[row][i] for row < rows, i < n1, with D
+// at tensor-memory columns [dcol, dcol + n1p) of lane `row`.  The accumulator is
+// staged through shared memory (`epi`, 128 (n1p + 1) floats) so the FP64
+// read-modify-write is coalesced; the increment is rounded to FP32 and widened
+// exactly by integer operations: one FP64 add per point, eight independent
+// read-modify-writes in flight per thread.  Called by the 256 producer threads.
 __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int n1p, const double* Win,
-                                            double* W, float tau_f, char* epi) {
+                                            double* W, float tau_f, char* epi, int stride = 0) {
+    if (stride == 0) stride = n1;
     const int tid = threadIdx.x;
     const int r = tid & (kRows - 1), h = tid >> 7;
     const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
@@ -750,14 +750,15 @@ __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int f = f0 + u * kThreads;
-            w[u] = f < count ? Win[f] : 0.0;
+            const int jl = div_by(f, m_n1);
+            w[u] = f < count ? Win[(long long)jl * stride + (f - jl * n1)] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int f = f0 + u * kThreads;
             if (f < count) {
                 const int jl = div_by(f, m_n1), i = f - jl * n1;
-                W[f] = w[u] + f32_to_f64(tau_f * E[jl * pitch + i]);
+                W[(long long)jl * stride + i] = w[u] + f32_to_f64(tau_f * E[jl * pitch + i]);
             }
         }
     }
@@ -910,19 +911,25 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcSh
     cta_end(R, tmem_cols);
 }
 
-// theta direction (scaled) + update: rows = 128 phi rows j of species blockIdx.y;
-// G1: X = Y2 x_1 Q_theta^T, Hadamard Phi(j, theta'), G2: x_1 Q_theta, then
-// w[s][j][i] += tau * result.  Accumulators: G1 at [0, n1p), G2 at [n1p, 2 n1p).
+// theta direction (scaled) + update: rows = 128 phi rows j of species blockIdx.y,
+// output theta columns [z th_nt, (z + 1) th_nt) with z = blockIdx.z.
+// G1: X = Y2 x_1 Q_theta^T (all theta', the K of G2), Hadamard Phi(j, theta'),
+// G2: x_1 Q_theta for this column group, then w[s][j][i] += tau * result.
+// Splitting the columns over CTAs repeats G1 in each but multiplies the CTAs of
+// a grid of only (n_phi / 128) x species row tiles.  Accumulators: G1 at
+// [0, n1p), G2 at [n1p, n1p + th_nt).
 __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, TcShape sh) {
     extern __shared__ char smem_raw[];
     const uint32_t tmem_cols = sh.tmem_cols;
     CtaRes R = cta_begin(smem_raw, sh, T.err);
-    const int s = blockIdx.y;
-    const int n1 = T.n1, n2 = T.n2, n1q = T.n1q;
+    const int s = blockIdx.y, z = blockIdx.z;
+    const int n1 = T.n1, n2 = T.n2, n1q = T.n1q, NT = T.th_nt;
     const int n1p = (n1 + 15) & ~15;
     const int j0 = blockIdx.x * kRows;
+    Image qz = T.Qsph;
+    qz.ptr += (long long)z * qz.k_chunks * qz.chunk_floats;
     GemmSpec gs[2] = {{T.QT, 0, kRows, 1, n1p, n1p / kKC, R.tmem},
-                      {T.Q, 0, kRows, 1, n1p, n1p / kKC, R.tmem + (uint32_t)n1p}};
+                      {qz, 0, kRows, 1, NT, n1p / kKC, R.tmem + (uint32_t)n1p}};
     if (threadIdx.x >= kThreads + 32) {
         pdl_trigger();
         mma_issuer(R.P, gs, 2);
@@ -966,8 +973,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, Tc
             store_row8(hi, lo, r, h, v);
         });
         const long long n12 = (long long)n1 * n2;
-        double* W = T.state_upd + (long long)s * n12 + (long long)j0 * n1;
-        update_rows(R.tmem + (uint32_t)n1p, min(kRows, n2 - j0), n1, n1p, W, W, T.tau, R.P.mat_slots);
+        const int i0 = z * NT;
+        double* W = T.state_upd + (long long)s * n12 + (long long)j0 * n1 + i0;
+        update_rows(R.tmem + (uint32_t)n1p, min(kRows, n2 - j0), min(NT, n1 - i0), NT, W, W, T.tau,
+                    R.P.mat_slots, n1);
     }
     cta_end(R, tmem_cols);
 }
@@ -1191,14 +1200,15 @@ TcShape tc_sphere_phi_shape(int nt) {
     return sh;
 }
 
-// Sphere theta product pair: matrices n1p rows, accumulators 2 n1p columns, update staging.
-TcShape tc_sphere_theta_shape(int n1) {
+// Sphere theta product pair: matrices n1p rows, accumulators n1p + nt columns,
+// update staging of nt columns.
+TcShape tc_sphere_theta_shape(int n1, int nt) {
     TcShape sh{};
     const uint32_t n1p = round_up(n1, 16);
     sh.data_bytes = 2u * kRows * kTileRowBytes;
     sh.mat_bytes = 2u * n1p * kTileRowBytes;
-    sh.tmem_cols = pow2_cols(2 * n1p);
-    rings(sh, kRows * (n1p + 1) * 4u, sh.tmem_cols <= 256);
+    sh.tmem_cols = pow2_cols(n1p + (uint32_t)nt);
+    rings(sh, kRows * ((uint32_t)nt + 1) * 4u, sh.tmem_cols <= 256);
     return sh;
 }
 
@@ -1216,7 +1226,8 @@ cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaSt
 }
 
 cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
-    dim3 grid((T.n2 + kRows - 1) / kRows, T.S);
+    const int n1p = (T.n1 + 15) & ~15;
+    dim3 grid((T.n2 + kRows - 1) / kRows, T.S, (n1p + T.th_nt - 1) / T.th_nt);
     return launch_pdl(k_tc_sphere_theta, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
 }
 

@@ -39,7 +39,7 @@ cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st);
 cudaError_t launch_wait_selftest(int* err, long long limit_cycles, cudaStream_t st);
 // Sphere: phi product (plain), then theta pair (scaled) + update.
 TcShape tc_sphere_phi_shape(int nt);
-TcShape tc_sphere_theta_shape(int n1);
+TcShape tc_sphere_theta_shape(int n1, int nt);
 cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta);
 cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cudaStream_t st);

@@ -341,6 +341,56 @@ static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
     return rc;
 }
 
+// Times the theta kernel of the sphere at every column split (one warm-up launch,
+// then three, CUDA events) on a zeroed scratch state and keeps the fastest.
+static sexpe_status tune_sphere_theta(sexpe_plan* p, const std::vector<int>& splits, const std::vector<Image>& qimg,
+                                      cudaStream_t st) {
+    SplitTables T = p->tabs;
+    const int n1p = rup16(p->n[0]);
+    double* scratch = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)p->S * p->npts;
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SEXPE_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sexpe_status rc = SEXPE_OK;
+    float best_ms = 1e30f;
+    size_t best = 0;
+    if (cudaMemsetAsync(scratch, 0, bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        rc = SEXPE_ECUDA;
+    } else {
+        T.state = T.state_upd = scratch;
+        for (size_t c = 0; c < splits.size() && rc == SEXPE_OK; ++c) {
+            T.Qsph = qimg[c];
+            T.th_nt = n1p / splits[c];
+            const TcShape sh = tc_sphere_theta_shape(p->n[0], T.th_nt);
+            bool ok = launch_tc_sphere_theta(T, sh, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_tc_sphere_theta(T, sh, st) == cudaSuccess;
+            float ms = 0.f;
+            ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            if (!ok) rc = SEXPE_ECUDA;
+            else if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    if (rc != SEXPE_OK) cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    p->th_splits = splits;
+    p->th_imgs = qimg;
+    p->tabs.Qsph = qimg[best];
+    p->tabs.th_nt = n1p / splits[best];
+    p->shs = tc_sphere_theta_shape(p->n[0], p->tabs.th_nt);
+    return rc;
+}
+
 // Split-TF32 sphere (eq. ee_sphere): mode 1 theta (scaled by sin^-2 phi_j),
 // mode 2 phi (plain); phi first, then theta with the update.
 sexpe_status build_split_sphere(sexpe_plan* p, cudaStream_t st) {
@@ -396,12 +446,35 @@ sexpe_status build_split_sphere(sexpe_plan* p, cudaStream_t st) {
         T.Pphi[s] = Image{dptr, T.phi_nt, n2p / kKC, 2LL * T.phi_nt * kKC};
     }
     p->sh3 = tc_sphere_phi_shape(T.phi_nt);
-    p->shs = tc_sphere_theta_shape(n1);
-    if (p->shs.smem_bytes > 227 * 1024 || p->sh3.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
-    if (p->shs.tmem_cols > 512 || p->sh3.tmem_cols > 512) return SEXPE_EUNSUPPORTED;
+    if (p->sh3.smem_bytes > 227 * 1024 || p->sh3.tmem_cols > 512) return SEXPE_EUNSUPPORTED;
+    // theta kernel: output columns split over 1, 2, 4 or 8 CTAs per row tile, each split timed
+    // (the splits repeat the first product in every CTA, so the best one depends on the grid)
+    std::vector<int> splits;
+    std::vector<Image> qimg;
+    uint32_t smem_max = 0;
+    for (int sp = 1; sp <= 8; sp *= 2) {
+        const int nt = n1p / sp;
+        if (nt < 16 || nt % 16 != 0 || (sp > 1 && nt * sp != n1p)) continue;
+        const TcShape sh = tc_sphere_theta_shape(n1, nt);
+        if (sh.smem_bytes > 227 * 1024 || sh.tmem_cols > 512) continue;
+        std::vector<float> img;
+        for (int t = 0; t < sp; ++t) {
+            const int r0 = t * nt;
+            const std::vector<float> part = make_image(std::max(0, std::min(nt, n1 - r0)), n1, nt, n1p,
+                                                       [&](int r, int k) { return th.V(r0 + r, k); });
+            img.insert(img.end(), part.begin(), part.end());
+        }
+        const float* dptr = nullptr;
+        SX_TRY(upload(p, img, &dptr, st));
+        splits.push_back(sp);
+        qimg.push_back(Image{dptr, nt, n1p / kKC, 2LL * nt * kKC});
+        smem_max = std::max(smem_max, sh.smem_bytes);
+    }
+    if (splits.empty()) return SEXPE_EUNSUPPORTED;
     SX_CUDA(tc_prepare(0, 0));
-    SX_CUDA(tc_prepare_sphere(p->sh3.smem_bytes, p->shs.smem_bytes));
+    SX_CUDA(tc_prepare_sphere(p->sh3.smem_bytes, smem_max));
     p->kernels_per_step = 3;
+    SX_TRY(tune_sphere_theta(p, splits, qimg, st));
     return tune_stencil(p, st);
 }
 
@@ -1186,6 +1259,23 @@ sexpe_status sexpe_set_stencil(sexpe_plan* p, int32_t tile_j, int32_t planes, in
     return SEXPE_OK;
 }
 
+sexpe_status sexpe_set_theta_split(sexpe_plan* p, int32_t split) {
+    if (!p) return SEXPE_EINVAL;
+    if (p->th_splits.empty()) return SEXPE_EUNSUPPORTED;
+    size_t c = 0;
+    while (c < p->th_splits.size() && p->th_splits[c] != split) ++c;
+    if (c == p->th_splits.size()) return SEXPE_EINVAL;
+    const int n1p = rup16(p->n[0]);
+    p->tabs.Qsph = p->th_imgs[c];
+    p->tabs.th_nt = n1p / split;
+    p->shs = tc_sphere_theta_shape(p->n[0], p->tabs.th_nt);
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    return SEXPE_OK;
+}
+
 sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* stream) {
     if (!p || !state || n_steps < 0) return SEXPE_EINVAL;
     if (((uintptr_t)state & 7u) != 0) return SEXPE_EINVAL;
@@ -1289,6 +1379,7 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
         info->stencil_tile_us = p->rhs_tj_us;
         info->stencil_planes = p->tabs.rhs_ks;
         info->stencil_ctas_per_sm = p->tabs.rhs_mb;
+        if (!p->th_splits.empty()) info->theta_split = rup16(p->n[0]) / p->tabs.th_nt;
     } else if (p->batch) {
         info->ring_slots[0] = (int32_t)p->bsh.nm;
         info->ring_slots[1] = (int32_t)p->bsh.nd;

@@ -80,6 +80,8 @@ struct sexpe_plan {
     double setup_ms = 0.0;
     float rhs_tj_us = 0.f;     // measured stencil time at the chosen tile height
     int batch_grid = 0;        // CTAs of the cooperative batch launch
+    std::vector<int> th_splits;            // split sphere: theta-kernel column splits built at setup
+    std::vector<sexpe::Image> th_imgs;     // their N-tiled Q_theta images
     long long* d_step = nullptr;   // steps since setup / sexpe_set_time (time-dependent sources)
     std::vector<double> offset;    // lifting offsets of the reactions (empty = 0)
     double rho_pow = -2.0;         // D_rho = rho^rho_pow (disk: -2, or -2 - lambda for Delta_lambda)

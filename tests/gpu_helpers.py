@@ -71,14 +71,18 @@ def increment_errors(got, ref, W0):
             for s in range(ref.shape[0])]
 
 
-def gpu_run(w, precision, steps=None, single_calls=False, stencil=None):
-    """stencil: optional (tile_j, planes) forced through sexpe_set_stencil."""
+def gpu_run(w, precision, steps=None, single_calls=False, stencil=None, theta_split=None):
+    """stencil: optional (tile_j, planes) forced through sexpe_set_stencil; theta_split: optional
+    sphere theta-kernel split forced through sexpe_set_theta_split."""
     import torch
     from paper_2604_11558_gb300 import binding
     plan = binding.Plan(w["geometry"], w["n"], w["d"], w["reaction"], w["params"], w["tau"], precision,
                         z_bc=w.get("z_bc", "neumann"), lam=w.get("lam"), offsets=w.get("offsets"))
     if stencil is not None:
         plan.set_stencil(*stencil)
+    if theta_split is not None:
+        plan.set_theta_split(theta_split)
+        assert plan.info()["theta_split"] == theta_split
     x = torch.from_numpy(np.ascontiguousarray(w["W0"])).cuda()
     n = w["steps"] if steps is None else steps
     if single_calls:

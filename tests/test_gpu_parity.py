@@ -230,6 +230,40 @@ def test_every_stencil_configuration_matches_oracle(name, w, configs):
         assert np.array_equal(o, outs[0])
 
 
+def test_every_theta_split_matches_oracle():
+    """The sphere's theta kernel with its output columns split over 1, 2, 4 and 8 CTAs (120 theta
+    points padded to 128: 128, 64, 32 and 16 columns per CTA, the last group ragged; 150 phi rows,
+    two row tiles) gives the oracle's result, and the same result at every split (each column's
+    products see the same operands in the same order)."""
+    w = sphere((120, 150), steps=4)
+    ref = oracle_run(w)
+    outs = []
+    for split in (1, 2, 4, 8):
+        got = gpu_run(w, "split_tf32", theta_split=split)
+        assert_parity(got, ref, w["W0"], 1e-6, 1e-5)
+        outs.append(got)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_set_theta_split_rejects_unbuilt_splits():
+    from paper_2604_11558_gb300 import binding
+    w = sphere((130, 70))
+    plan = binding.Plan.from_workload(w, precision="split_tf32")
+    assert plan.info()["theta_split"] == 1     # 144 padded columns: only the unsplit kernel
+    for bad in (0, 2, 3, 16):
+        with pytest.raises(RuntimeError):
+            plan.set_theta_split(bad)
+    plan.set_theta_split(1)
+    plan.close()
+    for other, prec in ((sphere((24, 13)), "fp64"), (ball((20, 24, 18)), "split_tf32")):
+        p = binding.Plan.from_workload(other, precision=prec)
+        assert p.info()["theta_split"] == 0
+        with pytest.raises(RuntimeError):
+            p.set_theta_split(1)
+        p.close()
+
+
 def test_set_stencil_rejects_untimed_configurations():
     from paper_2604_11558_gb300 import binding
     w = ball((20, 24, 18))

@@ -122,7 +122,9 @@ typedef struct {
     float stencil_tile_us;      /* split path: measured stencil time at that tile height     */
     int32_t stencil_planes;     /* split path: 0 = tiled stencil kernel, else k-planes per CTA
                                    of the rolling-window kernel (measured at setup)          */
-    int32_t stencil_ctas_per_sm; /* split path: CTAs per SM the stencil's registers allow    */
+    int32_t stencil_ctas_per_sm; /* split path: CTAs per SM the rolling-window stencil's
+                                   registers allow (1 or 2); 0 with stencil_planes > 0 = the
+                                   k-marching kernel                                          */
     int32_t theta_split;        /* split sphere: CTAs sharing one row tile of the theta kernel,
                                    each with n_theta_pad / theta_split output columns
                                    (measured at setup); 0 elsewhere                         */
@@ -191,8 +193,10 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* plan, sexpe_plan_info* info_h
 /* Override the stencil configuration that sexpe_setup measured for a split
  * plan (no counterpart in the paper: the tile shapes are this implementation's
  * own): tile_j j-lines per CTA with planes = 0 and ctas_per_sm = 1 for the
- * tiled kernel, or planes k-planes per CTA of the rolling-window kernel (3-D
- * geometries) with its registers capped for ctas_per_sm (1 or 2) CTAs per SM.
+ * tiled kernel; for the 3-D geometries, planes k-planes per CTA of the
+ * rolling-window kernel with its registers capped for ctas_per_sm (1 or 2)
+ * CTAs per SM, or, with ctas_per_sm = 0, of the k-marching kernel (one thread
+ * per (j, i) column of the tile_j lines, k-neighbours in registers).
  * The triple must be one the setup timed (sexpe_plan_info reports the chosen one);
  * others give SEXPE_EINVAL, FP64 and batch plans SEXPE_EUNSUPPORTED.  A graph
  * captured by an earlier sexpe_step is dropped and captured again.  Host-side

@@ -17,20 +17,18 @@ namespace sexpe {
 // coefficients reach ~1e7 near the coordinate singularities, where rounding w
 // itself to FP32 would leave errors far above the difference.
 __device__ __forceinline__ float2 split_f64(double w) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(w);
-    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
-    const int e = (int)((hi32 >> 20) & 0x7FFu);          // biased FP64 exponent
+    const unsigned hi32 = (unsigned)__double2hiint(w), lo32 = (unsigned)__double2loint(w);
     const unsigned sign = hi32 & 0x80000000u;
+    const unsigned e = (hi32 >> 20) & 0x7FFu;           // biased FP64 exponent
+    // hi: a funnel shift brings the low 8 exponent bits and the top 23 fraction bits into
+    // FP32 position; flipping exponent bit 7 rebiases e to e - 896 for every FP32-normal e.
     // |w| < 2^-126 (below FP32 normals) -> signed zero; beyond FP32 range -> infinity.
-    unsigned fb = sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
-    fb = (e < 897) ? sign : fb;
-    fb = (e > 1150) ? (sign | 0x7F800000u) : fb;
-    // remainder: the 29 truncated bits, weight 2^(e-1075) each
-    const unsigned m29 = lo32 & 0x1FFFFFFFu;
-    const int se = max(e - 948, 1);
-    float lo = __uint_as_float(__float_as_uint((float)m29) | sign) * __uint_as_float((unsigned)min(se, 254) << 23);
-    lo = (e >= 949 && e <= 1150) ? lo : 0.f;
-    return make_float2(__uint_as_float(fb), lo);
+    const unsigned f = __funnelshift_l(lo32, hi32, 3);
+    unsigned fb = ((f & 0x7FFFFFFFu) ^ 0x40000000u) | sign;
+    fb = (e - 897u <= 253u) ? fb : (e < 897u ? sign : (sign | 0x7F800000u));
+    // lo: the 29 truncated bits, weight 2^(e - 1075) each (zero below |w| = 2^-74)
+    const float lo = (float)(lo32 & 0x1FFFFFFFu) * __uint_as_float(sign | ((e - 948u) << 23));
+    return make_float2(__uint_as_float(fb), (e - 949u <= 201u) ? lo : 0.f);
 }
 
 // Exact FP32 -> FP64 conversion with integer operations only (FP32 denormals
@@ -146,6 +144,51 @@ __device__ __forceinline__ T reaction(const ReactionParams<T>& rp, const T* w_st
     }
     default:
         return (T)0;
+    }
+}
+
+// Reaction terms of every species at one point, g[s] equal to reaction<T>(rp, w_state, s) bit
+// for bit (the same operations), with the kind tested once per point by uniform branches
+// rather than once per species, and the terms two species share formed once.
+template <class T, int NS>
+__device__ __forceinline__ void reactions(const ReactionParams<T>& rp, const T* w_state, T* g) {
+#pragma unroll
+    for (int r = 0; r < NS; ++r) g[r] = (T)0;
+    if (rp.lifted) {
+        const T wu = w_state[0], wv = w_state[1];
+        const T N = fma_t(rp.q[2], wu, mul_t(rp.q[3], wv));
+        const T Q = mul_t(wu, fma_t(rp.q[4], wu, fma_t(rp.q[5], wv, mul_t(wu, wv))));
+        g[0] = mul_t(rp.p[0], (N + Q - wu) + rp.q[0]);
+        g[1] = mul_t(rp.p[0], rp.q[1] - (N + Q));
+        return;
+    }
+    T w[kMaxSpecies];
+#pragma unroll
+    for (int r = 0; r < kMaxSpecies; ++r) w[r] = r < NS ? w_state[r] + rp.off[r] : (T)0;
+    if (rp.kind == R_GRAY_SCOTT) {
+        const T uv2 = mul_t(mul_t(w[0], w[1]), w[1]);
+        g[0] = fma_t(rp.p[0], (T)1 - w[0], -uv2);
+        g[1] = fma_t(-(rp.p[0] + rp.p[1]), w[1], uv2);
+    } else if (rp.kind == R_SCHNAKENBERG) {
+        const T u2v = mul_t(mul_t(w[0], w[0]), w[1]);
+        g[0] = mul_t(rp.p[0], (rp.p[1] - w[0]) + u2v);
+        g[1] = mul_t(rp.p[0], rp.p[2] - u2v);
+    } else if (rp.kind == R_BVAM || rp.kind == R_BVAM_MMS) {
+        const T u = w[0], v = w[1];
+        g[0] = fma_t(mul_t(rp.p[0], u), fma_t(-rp.p[1], mul_t(v, v), (T)1), mul_t(v, fma_t(-rp.p[2], u, (T)1)));
+        const T q = mul_t(rp.p[0], rp.p[1]) / rp.p[3];
+        g[1] = fma_t(mul_t(rp.p[3], v), fma_t(q, mul_t(u, v), (T)1), mul_t(u, fma_t(rp.p[2], v, rp.p[4])));
+    } else if (rp.kind == R_LINEAR_CUBIC) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (s < rp.S) {
+                T acc = -mul_t(mul_t(w[s], w[s]), w[s]);
+#pragma unroll
+                for (int r = 0; r < NS; ++r)
+                    if (r < rp.S) acc = fma_t(rp.p[s * rp.S + r], w[r], acc);
+                g[s] = acc;
+            }
+        }
     }
 }
 

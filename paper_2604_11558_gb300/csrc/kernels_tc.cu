@@ -362,11 +362,43 @@ struct PointCoef {
     float rs3, lo3, up3, dp3;    // axis-3 row k, sin^-2 phi_k (ball)
 };
 
-// F of every species at one point from split (hi, lo) pairs in shared memory:
-// pc[s * ss] is the centre of species s; in-plane neighbours at -1/+1 (i, with
-// the periodic wrap dm/dp) and -/+ jstride (j); the k-neighbours at km/kp
-// (relative to pc).  Differences of pairs keep FP32 relative accuracy of the
-// difference (Section 2 Kronecker sums, applied in difference form).
+// F of species s at one point from split (hi, lo) pairs: centre c, neighbours
+// along mode 1 (m, p), mode 2 (jm, jp) and mode 3 (km, kp), each used only when
+// its flag is set; g is the species' reaction term at the point.  Differences
+// of pairs keep FP32 relative accuracy of the difference (Section 2 Kronecker
+// sums, applied in difference form).  Every operation is pinned, so all
+// stencil kernels form bit-identical F.
+template <int GEO>
+__device__ __forceinline__ float point_F(const RhsTables<float>& tb, int s, float g, float2 c, float2 m,
+                                         float2 p, float2 jm, float2 jp, float2 km, float2 kp, bool has_m,
+                                         bool has_p, bool has_jm, bool has_jp, bool has_km, bool has_kp,
+                                         const PointCoef& cf, float dpj) {
+    const float cv = c.x + c.y;
+    float t0 = __fmul_rn(cf.rs1, cv);
+    if (has_m) t0 = __fmaf_rn(cf.lo1, sdiff(m, c), t0);
+    if (has_p) t0 = __fmaf_rn(cf.up1, sdiff(p, c), t0);
+    float t1 = __fmul_rn(cf.rs2, cv);
+    if (has_jm) t1 = __fmaf_rn(cf.lo2, sdiff(jm, c), t1);
+    if (has_jp) t1 = __fmaf_rn(cf.up2, sdiff(jp, c), t1);
+    float lap;
+    if constexpr (GEO == GEO_DISK) {
+        lap = __fmaf_rn(cf.dr, t1, t0);
+    } else if constexpr (GEO == GEO_SPHERE) {
+        lap = __fmaf_rn(dpj, t0, t1);
+    } else {
+        float t2 = __fmul_rn(cf.rs3, cv);
+        if (has_km) t2 = __fmaf_rn(cf.lo3, sdiff(km, c), t2);
+        if (has_kp) t2 = __fmaf_rn(cf.up3, sdiff(kp, c), t2);
+        if constexpr (GEO == GEO_BALL) lap = __fmaf_rn(cf.dr, __fmaf_rn(cf.dp3, t1, t2), t0);
+        else lap = __fmaf_rn(cf.dr, t1, t0) + t2;
+    }
+    return __fmaf_rn(tb.d[s], lap, g);
+}
+
+// F of every species at one point from split pairs in shared memory: pc[s * ss]
+// is the centre of species s; in-plane neighbours at -1/+1 (i, with the
+// periodic wrap dm/dp) and -/+ jstride (j); the k-neighbours at km/kp
+// (relative to pc).
 template <int GEO>
 __device__ __forceinline__ void rhs_point(const RhsTables<float>& tb, const float2* pc, int ss, int jstride,
                                           long long km, long long kp, int dm, int dp, bool has_m, bool has_p,
@@ -383,31 +415,18 @@ __device__ __forceinline__ void rhs_point(const RhsTables<float>& tb, const floa
             w[r] = 0.f;
         }
     }
+    float g[kMaxSpecies];
+    reactions<float, kMaxSpecies>(tb.reac, w, g);
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s) {
         if (s >= S) break;
         const float2* q = pc + s * ss;
         const float2 c = q[0];
-        const float cv = c.x + c.y;
-        float t0 = __fmul_rn(cf.rs1, cv);
-        if (has_m) t0 = __fmaf_rn(cf.lo1, sdiff(q[dm], c), t0);
-        if (has_p) t0 = __fmaf_rn(cf.up1, sdiff(q[dp], c), t0);
-        float t1 = __fmul_rn(cf.rs2, cv);
-        if (has_jm) t1 = __fmaf_rn(cf.lo2, sdiff(q[-jstride], c), t1);
-        if (has_jp) t1 = __fmaf_rn(cf.up2, sdiff(q[jstride], c), t1);
-        float lap;
-        if constexpr (GEO == GEO_DISK) {
-            lap = __fmaf_rn(cf.dr, t1, t0);
-        } else if constexpr (GEO == GEO_SPHERE) {
-            lap = __fmaf_rn(dpj, t0, t1);
-        } else {
-            float t2 = __fmul_rn(cf.rs3, cv);
-            if (has_km) t2 = __fmaf_rn(cf.lo3, sdiff(q[km], c), t2);
-            if (has_kp) t2 = __fmaf_rn(cf.up3, sdiff(q[kp], c), t2);
-            if constexpr (GEO == GEO_BALL) lap = __fmaf_rn(cf.dr, __fmaf_rn(cf.dp3, t1, t2), t0);
-            else lap = __fmaf_rn(cf.dr, t1, t0) + t2;
-        }
-        const float f = __fmaf_rn(tb.d[s], lap, reaction<float>(tb.reac, w, s));
+        const bool k3 = GEO == GEO_BALL || GEO == GEO_CYLINDER;
+        const float f = point_F<GEO>(tb, s, g[s], c, has_m ? q[dm] : c, has_p ? q[dp] : c, has_jm ? q[-jstride] : c,
+                                     has_jp ? q[jstride] : c, (k3 && has_km) ? q[km] : c,
+                                     (k3 && has_kp) ? q[kp] : c, has_m, has_p, has_jm, has_jp, has_km, has_kp, cf,
+                                     dpj);
         Fo[s * ys] = add ? f + add[s] : f;
     }
 }
@@ -612,6 +631,147 @@ __global__ void __launch_bounds__(kRhsThreads, MINB) k_rhs_roll(RhsTables<float>
         if (k + 2 <= kend) store_plane(k + 2);       // slot of plane k - 2, free since the last barrier
         __syncthreads();
     }
+}
+
+// Stencil pass of the 3-D geometries marching along k with the k-neighbours in
+// registers: the CTA owns TJ theta-lines x KS planes of every species, thread t
+// the column (jl, i) = (t / n1, t mod n1), jl < TJ.  Each thread keeps the
+// split pairs of planes k - 1 and k of its column in registers; only plane k
+// goes through shared memory (two buffers, with the halo lines j0 - 1 and
+// j0 + TJ, which threads t < 2 n1 carry as well) for the in-plane neighbours:
+// one FP64 load and one split per value and plane, four shared loads per
+// point and species.  The FP64 values of planes k + 1 .. k + kMarchAhead are in
+// flight in a shared-memory ring of asynchronous copies (each thread reads back
+// only its own copies), enough bytes in flight per SM to cover the DRAM latency
+// without holding them in registers; one barrier per plane.  Addresses advance
+// by one plane per step (the kernel issues few instructions per point: it is
+// otherwise issue-bound).  Lines past n2 of a ragged last tile are loaded with
+// the periodic wrap of theta but not computed.  SM: species capacity of the
+// register arrays (2, or 4 with 512 threads).
+constexpr int kMarchAhead = 4;
+
+template <int GEO, int SM>
+__global__ void __launch_bounds__(SM <= 2 ? 1024 : 512, 1)
+    k_rhs_march(RhsTables<float> tb, const double* __restrict__ Wall, float* __restrict__ F, int TJ, int KS, int n1q,
+                long long ys) {
+    extern __shared__ float2 pbuf[];                 // [2][S][TJ + 2][n1] pairs, then the ring
+    const int n1 = tb.n1, n2 = tb.n2, n3 = tb.n3, S = tb.S;
+    const int j0 = blockIdx.x * TJ, k0 = blockIdx.y * KS;
+    const int kend = min(k0 + KS, n3);
+    const int lpv = (TJ + 2) * n1;                   // values per species and buffered plane
+    const int rs = blockDim.x + 2 * n1;              // ring values per species and plane: own, then halo
+    double* ring = reinterpret_cast<double*>(pbuf + 2 * S * lpv);   // [kMarchAhead][S][rs]
+    const long long npts = tb.npts, n12 = (long long)n1 * n2;
+    const int t = threadIdx.x;
+    const int jl = t / n1, i = t - jl * n1;
+    const int jr = j0 + jl;
+    const bool ld = jl < TJ;                         // loads buffer line jl + 1
+    const bool own = ld && jr < n2;                  // and computes its points
+    const int jw = ld ? (jr < n2 ? jr : jr - n2) : 0;
+    const bool halo = t < 2 * n1;
+    const int hline = t < n1 ? 0 : TJ + 1, hi = halo ? (t < n1 ? t : t - n1) : 0;
+    int hj = t < n1 ? j0 - 1 : j0 + TJ;
+    hj = hj < 0 ? hj + n2 : (hj >= n2 ? hj - n2 : hj);
+    const int obuf = (jl + 1) * n1 + i, hbuf = hline * n1 + hi;
+    PointCoef cf{};
+    if (own) {
+        cf.lo1 = __ldg(tb.ax[0].lower + i);
+        cf.up1 = __ldg(tb.ax[0].upper + i);
+        cf.rs1 = __ldg(tb.ax[0].rs + i);
+        cf.dr = __ldg(tb.Dr + i);
+        cf.rs2 = __ldg(tb.ax[1].rs + jr);
+        cf.lo2 = __ldg(tb.ax[1].lower + jr);
+        cf.up2 = __ldg(tb.ax[1].upper + jr);
+    }
+    // next plane to fetch, its global sources and this thread's ring entries
+    int kf = k0 + 1;
+    const double* go = Wall + (long long)jw * n1 + i + (long long)kf * n12;
+    const double* gh = Wall + (long long)(halo ? hj : 0) * n1 + hi + (long long)kf * n12;
+    const uint32_t r_own = smem_u32(ring + t), r_halo = smem_u32(ring + blockDim.x + t);
+    const uint32_t slot_b = (uint32_t)(S * rs) * 8u, sp_b = (uint32_t)rs * 8u;
+    auto fetch = [&]() {
+        if (kf <= kend && kf < n3) {                 // later planes are never read
+            const uint32_t so = (uint32_t)(kf & (kMarchAhead - 1)) * slot_b;
+#pragma unroll
+            for (int s = 0; s < SM; ++s) {
+                if (s < S) {
+                    if (ld) cp_async8(r_own + so + s * sp_b, go + s * npts);
+                    if (halo) cp_async8(r_halo + so + s * sp_b, gh + s * npts);
+                }
+            }
+        }
+        cp_async_commit();
+        go += n12;
+        gh += n12;
+        ++kf;
+    };
+    float2 pm[SM], pc[SM], pn[SM];
+    pdl_wait();          // the state is the previous step's result
+    pdl_trigger();
+    for (int q = 0; q < kMarchAhead; ++q) fetch();
+    {
+        const double* g0 = Wall + (long long)jw * n1 + i + (long long)k0 * n12;
+        const double* h0 = Wall + (long long)(halo ? hj : 0) * n1 + hi + (long long)k0 * n12;
+#pragma unroll
+        for (int s = 0; s < SM; ++s) {
+            const bool v = s < S && ld;
+            pm[s] = split_f64(v && k0 > 0 ? __ldg(g0 + s * npts - n12) : 0.0);
+            pc[s] = split_f64(v ? __ldg(g0 + s * npts) : 0.0);
+            if (v) pbuf[s * lpv + obuf] = pc[s];
+            if (s < S && halo) pbuf[s * lpv + hbuf] = split_f64(__ldg(h0 + s * npts));
+        }
+    }
+    __syncthreads();
+    float* Fo = F + ((long long)k0 * n2 + (own ? jr : 0)) * n1q + i;
+    const long long fstep = (long long)n2 * n1q;
+    const bool hm = i > 0, hp = i < n1 - 1;
+    for (int k = k0; k < kend; ++k, Fo += fstep) {
+        const int b = (k - k0) & 1;
+        const float2* Bc = pbuf + b * S * lpv + obuf;
+        float2* Bn = pbuf + (b ^ 1) * S * lpv;
+        cp_async_wait<kMarchAhead - 1>();            // plane k + 1 landed (this thread's copies)
+        const double* R = ring + (size_t)((k + 1) & (kMarchAhead - 1)) * S * rs + t;
+#pragma unroll
+        for (int s = 0; s < SM; ++s) pn[s] = split_f64(s < S && ld ? R[s * rs] : 0.0);
+        if (own) {
+            cf.rs3 = __ldg(tb.ax[2].rs + k);
+            cf.lo3 = __ldg(tb.ax[2].lower + k);
+            cf.up3 = __ldg(tb.ax[2].upper + k);
+            cf.dp3 = (GEO == GEO_BALL) ? __ldg(tb.Dp + k) : 1.f;
+            float w[kMaxSpecies], g[SM];
+#pragma unroll
+            for (int r = 0; r < kMaxSpecies; ++r) w[r] = 0.f;
+#pragma unroll
+            for (int r = 0; r < SM; ++r)
+                if (r < S) w[r] = pc[r].x + pc[r].y;
+            reactions<float, SM>(tb.reac, w, g);
+            const bool hkm = k > 0, hkp = k < n3 - 1;
+#pragma unroll
+            for (int s = 0; s < SM; ++s) {
+                if (s < S) {
+                    // every neighbour lies inside the buffer (lines 0 .. TJ + 1); the flags drop the absent ones
+                    const float2* q = Bc + s * lpv;
+                    Fo[s * ys] = point_F<GEO>(tb, s, g[s], pc[s], q[-1], q[1], q[-n1], q[n1], pm[s], pn[s], hm, hp,
+                                              true, true, hkm, hkp, cf, 1.f);
+                }
+            }
+        }
+        if (k + 1 < kend) {
+#pragma unroll
+            for (int s = 0; s < SM; ++s) {
+                if (s < S && ld) Bn[s * lpv + obuf] = pn[s];
+                if (s < S && halo) Bn[s * lpv + hbuf] = split_f64(R[s * rs + blockDim.x]);
+            }
+        }
+        __syncthreads();
+        fetch();                                     // plane k + 1 + kMarchAhead, into the slot just read
+#pragma unroll
+        for (int s = 0; s < SM; ++s) {
+            pm[s] = pc[s];
+            pc[s] = pn[s];
+        }
+    }
+    cp_async_wait<0>();                              // no copy may land after the CTA exits
 }
 
 // ------------------------------------------------------------------------------
@@ -1257,6 +1417,11 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 8, 1>, A, ring);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 4, 2>, A, ring);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 8, 2>, A, ring);
+    const int march = 200 * 1024;   // march_smem <= 64 KB of pairs + 4 x 8 B x S (threads + 2 n1) <= 128 KB
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 2>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 4>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 2>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 4>, A, march);
     return e;
 }
 
@@ -1320,6 +1485,15 @@ int rhs_candidates(const SplitTables& T, int3* out, int max_out) {
     for (int tj = 1; tj <= (k3 ? 16 : 32) && tj <= T.n2 && n < max_out; ++tj)
         if (per_line * (tj + 2) + 8 * 1024 <= 220 * 1024) out[n++] = make_int3(tj, 0, 1);
     if (k3) {
+        // marching kernel: one thread per column of TJ lines (at least 2 n1 for the halo lines)
+        const int maxt = T.S <= 2 ? 1024 : 512;
+        const int tjs[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 20, 24, 28, 32};
+        for (int tj : tjs) {
+            if (tj > T.n2 || T.S > 4 || std::max(tj, 2) * T.n1 > maxt) break;
+            const int kss[] = {2, 3, 4, 6, 8, 12, 16};
+            for (int ks : kss)
+                if (ks <= T.n3 && n < max_out) out[n++] = make_int3(tj, ks, 0);
+        }
         for (int tj = 2; tj <= 24 && tj <= T.n2 + 1; tj += 2) {
             if ((long long)T.S * (tj + 2) * T.n1 > 8 * kRhsThreads) break;
             for (int ks = 2; ks <= 16 && ks <= T.n3; ks *= 2)
@@ -1327,6 +1501,26 @@ int rhs_candidates(const SplitTables& T, int3* out, int max_out) {
         }
     }
     return n;
+}
+
+// Shared memory of the marching stencil: two planes of pairs, the ring of FP64 values.
+static size_t march_smem(int S, int tj, int n1, int threads) {
+    return 2 * sizeof(float2) * (size_t)S * (tj + 2) * n1 + sizeof(double) * (size_t)kMarchAhead * S * (threads + 2 * n1);
+}
+
+template <int GEO>
+static cudaError_t launch_rhs_march_geo(const SplitTables& T, cudaStream_t st) {
+    const int tj = T.rhs_tj, ks = T.rhs_ks;
+    const int threads = (std::max(tj, 2) * T.n1 + 31) / 32 * 32;
+    if (tj < 1 || tj > T.n2 || ks < 1 || T.S > kMaxSpecies || threads > (T.S <= 2 ? 1024 : 512))
+        return cudaErrorInvalidValue;
+    const size_t smem = march_smem(T.S, tj, T.n1, threads);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + ks - 1) / ks, 1);
+    auto kern = T.S <= 2 ? k_rhs_march<GEO, 2> : k_rhs_march<GEO, 4>;
+    cudaError_t e = launch_pdl(kern, grid, dim3(threads), smem, st, T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 template <int GEO>
@@ -1399,6 +1593,11 @@ cudaError_t launch_wait_selftest(int* err, long long limit_cycles, cudaStream_t 
 }
 
 cudaError_t launch_rhs_split(const SplitTables& T, cudaStream_t st) {
+    if (T.rhs_ks > 0 && T.rhs_mb == 0) {
+        if (T.geometry == GEO_BALL) return launch_rhs_march_geo<GEO_BALL>(T, st);
+        if (T.geometry == GEO_CYLINDER) return launch_rhs_march_geo<GEO_CYLINDER>(T, st);
+        return cudaErrorInvalidValue;
+    }
     if (T.rhs_ks > 0) {
         if (T.geometry == GEO_BALL) return launch_rhs_roll_geo<GEO_BALL>(T, st);
         if (T.geometry == GEO_CYLINDER) return launch_rhs_roll_geo<GEO_CYLINDER>(T, st);

@@ -295,8 +295,8 @@ sexpe_status build_fp64(sexpe_plan* p, cudaStream_t st) {
 // once at setup, before any graph capture; the scratch state is freed here.
 static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
     SplitTables T = p->tabs;
-    int3 cand[160];
-    const int nc = rhs_candidates(T, cand, 160);
+    int3 cand[256];
+    const int nc = rhs_candidates(T, cand, 256);
     if (nc == 0) return SEXPE_EUNSUPPORTED;
     double* scratch = nullptr;
     const size_t bytes = sizeof(double) * (size_t)p->S * p->npts;
@@ -1244,8 +1244,8 @@ sexpe_status sexpe_set_time(sexpe_plan* p, double t, void* stream) {
 sexpe_status sexpe_set_stencil(sexpe_plan* p, int32_t tile_j, int32_t planes, int32_t ctas_per_sm) {
     if (!p) return SEXPE_EINVAL;
     if (p->batch || p->precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
-    int3 cand[160];
-    const int nc = rhs_candidates(p->tabs, cand, 160);
+    int3 cand[256];
+    const int nc = rhs_candidates(p->tabs, cand, 256);
     bool ok = false;
     for (int c = 0; c < nc; ++c) ok = ok || (cand[c].x == tile_j && cand[c].y == planes && cand[c].z == ctas_per_sm);
     if (!ok) return SEXPE_EINVAL;

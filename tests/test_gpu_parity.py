@@ -208,15 +208,16 @@ def test_plan_info_reports_measured_tile_choices():
 
 
 STENCIL_CASES = [
-    ("ball", ball((37, 29, 23)), [(1, 0), (7, 0), (2, 2), (4, 4), (10, 8, 2), (16, 16), (24, 2, 2)]),
-    ("cylinder", cyl((24, 40, 37), steps=3), [(3, 0), (2, 16, 2), (8, 4), (24, 8, 2)]),
+    ("ball", ball((37, 29, 23)), [(1, 0), (7, 0), (2, 2), (4, 4), (10, 8, 2), (16, 16), (24, 2, 2),
+                                  (1, 2, 0), (5, 3, 0), (24, 16, 0)]),
+    ("cylinder", cyl((24, 40, 37), steps=3), [(3, 0), (2, 16, 2), (8, 4), (24, 8, 2), (3, 4, 0), (20, 12, 0)]),
 ]
 
 
 @pytest.mark.parametrize("name,w,configs", STENCIL_CASES, ids=[c[0] for c in STENCIL_CASES])
 def test_every_stencil_configuration_matches_oracle(name, w, configs):
-    """Both stencil kernels (tiled: planes = 0; rolling window: planes > 0, registers capped for one
-    or two CTAs per SM), forced through sexpe_set_stencil at several tile shapes with ragged last
+    """The stencil kernels (tiled: planes = 0; rolling window: planes > 0, registers capped for one
+    or two CTAs per SM; k-marching: planes > 0, ctas_per_sm = 0), forced through sexpe_set_stencil at several tile shapes with ragged last
     tiles, give the oracle's result; the
     F they write is the same whatever the shape (the rest of the step is identical)."""
     ref = oracle_run(w)
@@ -268,11 +269,15 @@ def test_set_stencil_rejects_untimed_configurations():
     from paper_2604_11558_gb300 import binding
     w = ball((20, 24, 18))
     plan = binding.Plan.from_workload(w, precision="split_tf32")
-    for bad in [(0, 0), (17, 0), (3, 2), (4, 3), (4, 32), (40, 2), (4, 4, 3), (4, 0, 2)]:
+    for bad in [(0, 0), (17, 0), (3, 2), (4, 3), (4, 32), (40, 2), (4, 4, 3), (4, 0, 2), (4, 5, 0), (30, 2, 0),
+                (4, 0, 0)]:
         with pytest.raises(RuntimeError):
             plan.set_stencil(*bad)
     plan.set_stencil(4, 4)
     assert plan.info()["stencil_planes"] == 4 and plan.info()["stencil_tile_j"] == 4
+    plan.set_stencil(6, 3, 0)
+    inf = plan.info()
+    assert (inf["stencil_tile_j"], inf["stencil_planes"], inf["stencil_ctas_per_sm"]) == (6, 3, 0)
     plan.close()
     p64 = binding.Plan.from_workload(w, precision="fp64")
     with pytest.raises(RuntimeError):

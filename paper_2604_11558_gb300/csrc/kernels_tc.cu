@@ -70,9 +70,10 @@ constexpr uint32_t kHeaderBytes = 256;     // barriers + tensor-memory slot + ab
 // tcgen05.commit, so the TMA warp can run nm chunks ahead of the MMAs while
 // the producers run nd chunks ahead.
 struct Pipe {
-    uint64_t* mat_full;     // matrix chunk landed (TMA transaction count)
+    uint64_t* mat_full;     // (unused: the matrix copies complete on data_full)
     uint64_t* mat_empty;    // MMAs reading the matrix slot completed
-    uint64_t* data_full;    // data operand written (one arrive per producer warp)
+    uint64_t* data_full;    // chunk ready: one arrive per producer warp + the matrix copy (TMA
+                            // thread's arrive and transaction count)
     uint64_t* data_empty;   // MMAs reading the data slot completed
     char* mat_slots;
     char* data_slots;
@@ -147,26 +148,36 @@ __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Loader&& lo
     load(0, p0);
     if (G.k_chunks > 1) load(1, p1);
     uint32_t last_sd = 0, last_pd = 0;
+    const bool lane0 = (threadIdx.x & 31) == 0;
     for (int c = 0; c < G.k_chunks; ++c) {
         Pre8 p2;
         if (c + 2 < G.k_chunks) load(c + 2, p2);
         const uint32_t s = P.sd;
-        if (P.g >= P.nd) pipe_wait(P, &P.data_empty[s], P.pd ^ 1u, DERR_TIMEOUT_MMA);
+        // Slot reuse: the MMAs of chunk g - nd completed.  One lane per warp waits, once per
+        // pair of chunks, on the later chunk's slot: MMAs complete (and commit) in issue order,
+        // so that phase implies this one.  Every barrier probe costs the warp ~200+ cycles
+        // while the tensor core streams operands from shared memory.
+        if (lane0 && (c & 1) == 0) {
+            const bool pair = c + 1 < G.k_chunks;
+            const uint32_t s1 = pair ? (s + 1 == P.nd ? 0u : s + 1) : s;
+            const uint32_t p1 = pair && s + 1 == P.nd ? P.pd ^ 1u : P.pd;
+            if (P.g + (pair ? 1u : 0u) >= P.nd) pipe_wait(P, &P.data_empty[s1], p1 ^ 1u, DERR_TIMEOUT_MMA);
+        }
+        __syncwarp();
         char* hi = P.data_slots + (size_t)s * P.data_bytes;
         produce(c, hi, hi + G.data_rows * kTileRowBytes, p0);
         fence_async_smem();
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) {
-            pipe_wait(P, &P.mat_full[P.sm], P.pm, DERR_TIMEOUT_TMA);
-            mbar_arrive(&P.data_full[s]);
-        }
+        if (lane0) mbar_arrive(&P.data_full[s]);
         last_sd = s;
         last_pd = P.pd;
         P.advance();
         p0 = p1;
         p1 = p2;
     }
-    pipe_wait(P, &P.data_empty[last_sd], last_pd, DERR_TIMEOUT_MMA);
+    // the product is complete in tensor memory once the last chunk's MMAs are
+    if (lane0) pipe_wait(P, &P.data_empty[last_sd], last_pd, DERR_TIMEOUT_MMA);
+    __syncwarp();
     tc_fence_after();
 }
 
@@ -176,7 +187,7 @@ __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& 
 }
 
 // MMA side: one lane of the MMA warp walks the K-chunks of every product in
-// order; when a chunk's data barrier completes (data operand written, matrix
+// order; once a chunk's data barrier completes (data operand written, matrix
 // copy landed) it issues the three TF32 MMAs per K-step and commits them to
 // both slots' empty barriers.
 //
@@ -204,7 +215,7 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
         const bool one_tile = G.m_tiles == 1 && n_halves == 1;
         for (int c = 0; c < G.k_chunks; ++c, P.advance()) {
             const uint32_t sm = P.sm, sd = P.sd;
-            pipe_wait(P, &P.data_full[sd], P.pd, DERR_TIMEOUT_MMA);
+            pipe_wait(P, &P.data_full[sd], P.pd, DERR_TIMEOUT_MMA);     // data written, matrix landed
             tc_fence_after();
             const uint64_t om = (uint64_t)sm * mat16, od = (uint64_t)sd * data16;
             const uint64_t mh = dmh + om, ml = dml + om, dh = ddh + od, dl = ddl + od;
@@ -262,18 +273,22 @@ __device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
             if (P.g >= P.nm) pipe_wait(P, &P.mat_empty[s], P.pm ^ 1u, DERR_TIMEOUT_MMA);
             char* slot = P.mat_slots + (size_t)s * P.mat_bytes;
             const float* src = G.mat.ptr + (long long)c * G.mat.chunk_floats;
-            mbar_arrive_expect_tx(&P.mat_full[s], 2 * tile);
-            tma_bulk_g2s(slot, src, 2 * tile, &P.mat_full[s]);
+            // the copy completes on the chunk's data barrier; its previous phase (chunk
+            // g - nd <= g - nm, consumed by the MMA thread before it issued the MMAs whose
+            // completion freed this matrix slot) is over, as nm <= nd
+            mbar_arrive_expect_tx(&P.data_full[P.sd], 2 * tile);
+            tma_bulk_g2s(slot, src, 2 * tile, &P.data_full[P.sd]);
         }
     }
     // No copy of this CTA may still be landing when the CTA exits or its shared
     // memory is reused, also after a timed-out wait: wait (bounded) for the
-    // last copy of every slot.  In a healthy run these phases completed long ago.
-    const uint32_t last = P.g < P.nm ? P.g : P.nm;
+    // data barriers of the last nd chunks.  In a healthy run these phases
+    // completed long ago.
+    const uint32_t last = P.g < P.nd ? P.g : P.nd;
     for (uint32_t b = 1; b <= last; ++b) {
-        const uint32_t sm = (P.sm + P.nm - b) % P.nm;
-        const uint32_t pm = b > P.sm ? P.pm ^ 1u : P.pm;
-        pipe_wait(P, &P.mat_full[sm], pm, DERR_TIMEOUT_TMA);
+        const uint32_t sd = (P.sd + P.nd - b) % P.nd;
+        const uint32_t pd = b > P.sd ? P.pd ^ 1u : P.pd;
+        pipe_wait(P, &P.data_full[sd], pd, DERR_TIMEOUT_TMA);
     }
 }
 
@@ -296,7 +311,7 @@ __device__ __forceinline__ CtaRes cta_begin(char* smem_raw, const TcShape& rs, i
             mbar_init(&bars[kMaxMat + s], 1);                // mat_empty: tcgen05.commit
         }
         for (int s = 0; s < kMaxData; ++s) {
-            mbar_init(&bars[2 * kMaxMat + s], kThreads / 32);          // data_full: producer warps
+            mbar_init(&bars[2 * kMaxMat + s], kThreads / 32 + 1);      // data_full: producer warps + TMA
             mbar_init(&bars[2 * kMaxMat + kMaxData + s], 1);           // data_empty: tcgen05.commit
         }
         *aborted = 0;
@@ -1293,10 +1308,10 @@ static void rings(TcShape& sh, uint32_t min_body, bool pair) {
     const uint32_t pair_limit = 228 * 1024 / 2 - 1024 - slack;
     const uint32_t solo_limit = 227 * 1024 - slack;
     auto fit = [&](uint32_t limit) {
-        for (uint32_t nd = 3; nd >= 2; --nd) {
+        for (uint32_t nd = kMaxData; nd >= 2; --nd) {
             if (nd * sh.data_bytes >= limit) continue;
             uint32_t nm = (limit - nd * sh.data_bytes) / sh.mat_bytes;
-            nm = nm > (uint32_t)kMaxMat ? (uint32_t)kMaxMat : nm;
+            nm = nm > nd ? nd : nm;            // the matrix copies signal the data barriers: nm <= nd
             if (nm >= 3 || (nd == 2 && nm >= 2)) {
                 sh.nd = nd;
                 sh.nm = nm;

@@ -133,6 +133,23 @@ struct Pre8 {
     float v[8];
 };
 
+// Eight values of a producer thread's row at columns k0 .. k0 + 7 of a strided
+// table, base[k * stride], zero where the row is invalid or k >= kmax.  Full
+// groups take unpredicated loads at 32-bit offsets from one row pointer (the
+// producers issue few instructions per chunk: with 8 warps on an SM their
+// instruction chains are not hidden by other warps).
+__device__ __forceinline__ void load8_strided(Pre8& p, const float* base, int stride, int k0, int kmax, bool valid) {
+    if (valid && k0 + 8 <= kmax) {
+        const float* a = base + (long long)k0 * stride;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p.v[q] = __ldg(a + q * stride);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            p.v[q] = (valid && k0 + q < kmax) ? __ldg(base + (long long)(k0 + q) * stride) : 0.f;
+    }
+}
+
 // Producer side of one product.  `load(c, Pre8&)` issues the global loads a
 // thread needs for chunk c (or nothing), `produce(c, hi, lo, const Pre8&)`
 // writes the data operand of chunk c into its slot; loads run two chunks ahead
@@ -824,29 +841,17 @@ __global__ void __launch_bounds__(kBlock, 1)
         const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
         const bool valid = r < tile_rows;
         const int i = (int)((row0 + r) % n1q);
-        const float* Yr = Ys + row0 + r;
+        float* Yr = Ys + row0 + r;
         run_gemm(
             R.P, gs[0],
-            [&](int c, Pre8& p) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int k = c * 16 + h * 8 + q;
-                    p.v[q] = (valid && k < n3) ? __ldg(Yr + k * plane) : 0.f;
-                }
-            },
+            [&](int c, Pre8& p) { load8_strided(p, Yr, (int)plane, c * 16 + h * 8, n3, valid); },
             [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
         uint32_t last = 0;
         if constexpr (GEO == GEO_BALL) {
             const float* hp = T.had_phi + (long long)s * n3 * n1q + i;
             run_gemm(
                 R.P, gs[1],
-                [&](int c, Pre8& p) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int k = c * 16 + h * 8 + q;
-                        p.v[q] = (valid && k < n3) ? __ldg(hp + (long long)k * n1q) : 0.f;
-                    }
-                },
+                [&](int c, Pre8& p) { load8_strided(p, hp, n1q, c * 16 + h * 8, n3, valid); },
                 [&](int c, char* hi, char* lo, const Pre8& p) {
                     float v[8];
                     tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
@@ -859,10 +864,15 @@ __global__ void __launch_bounds__(kBlock, 1)
         for (int c = 0; c < n3p / 16; ++c) {
             float v[8];
             tmem_ld8(R.tmem + lane_base + last + (uint32_t)(c * 16 + h * 8), v);
+            const int k0 = c * 16 + h * 8;
+            float* o = Yr + (long long)k0 * plane;
+            if (valid && k0 + 8 <= n3) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = c * 16 + h * 8 + q;
-                if (valid && k < n3) Ys[k * plane + row0 + r] = v[q];
+                for (int q = 0; q < 8; ++q) o[q * (int)plane] = v[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (valid && k0 + q < n3) o[q * (int)plane] = v[q];
             }
         }
     }
@@ -953,13 +963,7 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
     const int n1q = J.n1q;
     // eight values of row r, columns 16c + 8h + q, of a [j][n1q] table, 0 outside the slab
     auto load_rows = [&](const float* base) {
-        return [=](int c, Pre8& p) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = c * 16 + h * 8 + q;
-                p.v[q] = (r < n1 && j < n2) ? __ldg(base + (long long)j * n1q + r) : 0.f;
-            }
-        };
+        return [=](int c, Pre8& p) { load8_strided(p, base + r, n1q, c * 16 + h * 8, n2, r < n1); };
     };
     run_gemm(P, gs[0], load_rows(J.Y),
              [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
@@ -1064,13 +1068,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcSh
         const float* Yi = T.Y + (long long)s * T.ys + i;
         run_gemm(
             R.P, gs[0],
-            [&](int c, Pre8& p) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = c * 16 + h * 8 + q;
-                    p.v[q] = (valid && j < n2) ? __ldg(Yi + (long long)j * n1q) : 0.f;
-                }
-            },
+            [&](int c, Pre8& p) { load8_strided(p, Yi, n1q, c * 16 + h * 8, n2, valid); },
             [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
         float* Yo = T.Y2 + (long long)s * T.ys + i;
         for (int c = 0; c < NT / 16; ++c) {

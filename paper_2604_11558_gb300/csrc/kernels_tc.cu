@@ -911,8 +911,10 @@ __device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, uint
 // at tensor-memory columns [dcol, dcol + n1p) of lane `row`.  The accumulator is
 // staged through shared memory (`epi`, 128 (n1p + 1) floats) so the FP64
 // read-modify-write is coalesced; the increment is rounded to FP32 and widened
-// exactly by integer operations: one FP64 add per point, eight independent
+// exactly by integer operations: one FP64 add per point, kUpdBatch independent
 // read-modify-writes in flight per thread.  Called by the 256 producer threads.
+constexpr int kUpdBatch = 16;   // FP64 read-modify-writes in flight per thread in update_rows
+
 __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int n1p, const double* Win,
                                             double* W, float tau_f, char* epi, int stride = 0) {
     if (stride == 0) stride = n1;
@@ -930,20 +932,20 @@ __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int
     compute_sync();
     const int count = rows * n1;
     const uint32_t m_n1 = div_magic((uint32_t)n1);
-    for (int f0 = tid; f0 < count; f0 += kThreads * 8) {
-        double w[8];
+    for (int f0 = tid; f0 < count; f0 += kThreads * kUpdBatch) {
+        double w[kUpdBatch];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kUpdBatch; ++u) {
             const int f = f0 + u * kThreads;
             const int jl = div_by(f, m_n1);
-            w[u] = f < count ? Win[(long long)jl * stride + (f - jl * n1)] : 0.0;
+            w[u] = f < count ? Win[jl * stride + (f - jl * n1)] : 0.0;     // offsets < 2^31
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kUpdBatch; ++u) {
             const int f = f0 + u * kThreads;
             if (f < count) {
                 const int jl = div_by(f, m_n1), i = f - jl * n1;
-                W[(long long)jl * stride + i] = w[u] + f32_to_f64(tau_f * E[jl * pitch + i]);
+                W[jl * stride + i] = w[u] + f32_to_f64(tau_f * E[jl * pitch + i]);
             }
         }
     }
@@ -997,7 +999,7 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
                     J.Win + (long long)mt * kRows * n1, J.W + (long long)mt * kRows * n1, J.tau_f, epi);
 }
 
-__global__ void __launch_bounds__(kBlock, 1)
+__global__ void __launch_bounds__(kBlock, 2)
     k_tc_slab(SplitTables T, TcShape sh) {
     extern __shared__ char smem_raw[];
     const uint32_t tmem_cols = sh.tmem_cols;

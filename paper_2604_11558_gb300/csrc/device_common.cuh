@@ -154,31 +154,39 @@ template <class T, int NS>
 __device__ __forceinline__ void reactions(const ReactionParams<T>& rp, const T* w_state, T* g) {
 #pragma unroll
     for (int r = 0; r < NS; ++r) g[r] = (T)0;
-    if (rp.lifted) {
-        const T wu = w_state[0], wv = w_state[1];
-        const T N = fma_t(rp.q[2], wu, mul_t(rp.q[3], wv));
-        const T Q = mul_t(wu, fma_t(rp.q[4], wu, fma_t(rp.q[5], wv, mul_t(wu, wv))));
-        g[0] = mul_t(rp.p[0], (N + Q - wu) + rp.q[0]);
-        g[1] = mul_t(rp.p[0], rp.q[1] - (N + Q));
-        return;
-    }
     T w[kMaxSpecies];
 #pragma unroll
     for (int r = 0; r < kMaxSpecies; ++r) w[r] = r < NS ? w_state[r] + rp.off[r] : (T)0;
-    if (rp.kind == R_GRAY_SCOTT) {
-        const T uv2 = mul_t(mul_t(w[0], w[1]), w[1]);
-        g[0] = fma_t(rp.p[0], (T)1 - w[0], -uv2);
-        g[1] = fma_t(-(rp.p[0] + rp.p[1]), w[1], uv2);
-    } else if (rp.kind == R_SCHNAKENBERG) {
-        const T u2v = mul_t(mul_t(w[0], w[0]), w[1]);
-        g[0] = mul_t(rp.p[0], (rp.p[1] - w[0]) + u2v);
-        g[1] = mul_t(rp.p[0], rp.p[2] - u2v);
-    } else if (rp.kind == R_BVAM || rp.kind == R_BVAM_MMS) {
-        const T u = w[0], v = w[1];
-        g[0] = fma_t(mul_t(rp.p[0], u), fma_t(-rp.p[1], mul_t(v, v), (T)1), mul_t(v, fma_t(-rp.p[2], u, (T)1)));
-        const T q = mul_t(rp.p[0], rp.p[1]) / rp.p[3];
-        g[1] = fma_t(mul_t(rp.p[3], v), fma_t(q, mul_t(u, v), (T)1), mul_t(u, fma_t(rp.p[2], v, rp.p[4])));
-    } else if (rp.kind == R_LINEAR_CUBIC) {
+    if constexpr (NS >= 2) {     // the two-species kinds
+        if (rp.lifted) {
+            const T wu = w_state[0], wv = w_state[1];
+            const T N = fma_t(rp.q[2], wu, mul_t(rp.q[3], wv));
+            const T Q = mul_t(wu, fma_t(rp.q[4], wu, fma_t(rp.q[5], wv, mul_t(wu, wv))));
+            g[0] = mul_t(rp.p[0], (N + Q - wu) + rp.q[0]);
+            g[1] = mul_t(rp.p[0], rp.q[1] - (N + Q));
+            return;
+        }
+        if (rp.kind == R_GRAY_SCOTT) {
+            const T uv2 = mul_t(mul_t(w[0], w[1]), w[1]);
+            g[0] = fma_t(rp.p[0], (T)1 - w[0], -uv2);
+            g[1] = fma_t(-(rp.p[0] + rp.p[1]), w[1], uv2);
+            return;
+        }
+        if (rp.kind == R_SCHNAKENBERG) {
+            const T u2v = mul_t(mul_t(w[0], w[0]), w[1]);
+            g[0] = mul_t(rp.p[0], (rp.p[1] - w[0]) + u2v);
+            g[1] = mul_t(rp.p[0], rp.p[2] - u2v);
+            return;
+        }
+        if (rp.kind == R_BVAM || rp.kind == R_BVAM_MMS) {
+            const T u = w[0], v = w[1];
+            g[0] = fma_t(mul_t(rp.p[0], u), fma_t(-rp.p[1], mul_t(v, v), (T)1), mul_t(v, fma_t(-rp.p[2], u, (T)1)));
+            const T q = mul_t(rp.p[0], rp.p[1]) / rp.p[3];
+            g[1] = fma_t(mul_t(rp.p[3], v), fma_t(q, mul_t(u, v), (T)1), mul_t(u, fma_t(rp.p[2], v, rp.p[4])));
+            return;
+        }
+    }
+    if (rp.kind == R_LINEAR_CUBIC) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             if (s < rp.S) {

@@ -678,8 +678,8 @@ __global__ void __launch_bounds__(kRhsThreads, MINB) k_rhs_roll(RhsTables<float>
 // without holding them in registers; one barrier per plane.  Addresses advance
 // by one plane per step (the kernel issues few instructions per point: it is
 // otherwise issue-bound).  Lines past n2 of a ragged last tile are loaded with
-// the periodic wrap of theta but not computed.  SM: species capacity of the
-// register arrays (2, or 4 with 512 threads).
+// the periodic wrap of theta but not computed.  SM: the number of species
+// (1024 threads per CTA for up to two, else 512).
 constexpr int kMarchAhead = 4;
 
 template <int GEO, int SM>
@@ -687,7 +687,8 @@ __global__ void __launch_bounds__(SM <= 2 ? 1024 : 512, 1)
     k_rhs_march(RhsTables<float> tb, const double* __restrict__ Wall, float* __restrict__ F, int TJ, int KS, int n1q,
                 long long ys) {
     extern __shared__ float2 pbuf[];                 // [2][S][TJ + 2][n1] pairs, then the ring
-    const int n1 = tb.n1, n2 = tb.n2, n3 = tb.n3, S = tb.S;
+    const int n1 = tb.n1, n2 = tb.n2, n3 = tb.n3;
+    constexpr int S = SM;                            // the species count, fixed per instantiation
     const int j0 = blockIdx.x * TJ, k0 = blockIdx.y * KS;
     const int kend = min(k0 + KS, n3);
     const int lpv = (TJ + 2) * n1;                   // values per species and buffered plane
@@ -1433,9 +1434,13 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 4, 2>, A, ring);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 8, 2>, A, ring);
     const int march = 200 * 1024;   // march_smem <= 64 KB of pairs + 4 x 8 B x S (threads + 2 n1) <= 128 KB
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 1>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 2>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 3>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 4>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 1>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 2>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 3>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 4>, A, march);
     return e;
 }
@@ -1532,7 +1537,8 @@ static cudaError_t launch_rhs_march_geo(const SplitTables& T, cudaStream_t st) {
     const size_t smem = march_smem(T.S, tj, T.n1, threads);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + ks - 1) / ks, 1);
-    auto kern = T.S <= 2 ? k_rhs_march<GEO, 2> : k_rhs_march<GEO, 4>;
+    auto kern = T.S == 1 ? k_rhs_march<GEO, 1>
+              : T.S == 2 ? k_rhs_march<GEO, 2> : T.S == 3 ? k_rhs_march<GEO, 3> : k_rhs_march<GEO, 4>;
     cudaError_t e = launch_pdl(kern, grid, dim3(threads), smem, st, T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

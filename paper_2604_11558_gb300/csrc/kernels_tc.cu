@@ -807,6 +807,167 @@ __global__ void __launch_bounds__(SM <= 2 ? 1024 : 512, 1)
     cp_async_wait<0>();                              // no copy may land after the CTA exits
 }
 
+// The marching stencil with two adjacent columns (i, i + 1), i even, per thread
+// (n1 even, state 16-byte aligned): 16-byte copies and stores, the j-neighbours
+// of both columns in one shared load each, and each column's i-neighbour on
+// the other side taken from the thread's own registers; half the threads of
+// k_rhs_march for the same tile and the same F bit for bit (same pairs, same
+// point formula).
+template <int GEO, int SM>
+__global__ void __launch_bounds__(512, 1)
+    k_rhs_march2(RhsTables<float> tb, const double* __restrict__ Wall, float* __restrict__ F, int TJ, int KS, int n1q,
+                 long long ys) {
+    extern __shared__ float2 pbuf[];                 // [2][S][TJ + 2][n1] pairs, then the ring
+    const int n1 = tb.n1, n2 = tb.n2, n3 = tb.n3, h1 = n1 >> 1;
+    constexpr int S = SM;
+    const int j0 = blockIdx.x * TJ, k0 = blockIdx.y * KS;
+    const int kend = min(k0 + KS, n3);
+    const int lpv = (TJ + 2) * n1;
+    const int rs = 2 * (blockDim.x + n1);            // ring doubles per species and plane: own pairs, halo pairs
+    double* ring = reinterpret_cast<double*>(pbuf + 2 * S * lpv);   // [kMarchAhead][S][rs]
+    const long long npts = tb.npts, n12 = (long long)n1 * n2;
+    const int t = threadIdx.x;
+    const int jl = t / h1, i = 2 * (t - jl * h1);
+    const int jr = j0 + jl;
+    const bool ld = jl < TJ;
+    const bool own = ld && jr < n2;
+    const int jw = ld ? (jr < n2 ? jr : jr - n2) : 0;
+    const bool halo = t < n1;                        // h1 pairs of each halo line
+    const int hline = t < h1 ? 0 : TJ + 1, hi = halo ? 2 * (t < h1 ? t : t - h1) : 0;
+    int hj = t < h1 ? j0 - 1 : j0 + TJ;
+    hj = hj < 0 ? hj + n2 : (hj >= n2 ? hj - n2 : hj);
+    const int obuf = (jl + 1) * n1 + i, hbuf = hline * n1 + hi;
+    PointCoef cf0{}, cf1{};
+    if (own) {
+        cf0.lo1 = __ldg(tb.ax[0].lower + i);
+        cf0.up1 = __ldg(tb.ax[0].upper + i);
+        cf0.rs1 = __ldg(tb.ax[0].rs + i);
+        cf0.dr = __ldg(tb.Dr + i);
+        cf1.lo1 = __ldg(tb.ax[0].lower + i + 1);
+        cf1.up1 = __ldg(tb.ax[0].upper + i + 1);
+        cf1.rs1 = __ldg(tb.ax[0].rs + i + 1);
+        cf1.dr = __ldg(tb.Dr + i + 1);
+        cf0.rs2 = cf1.rs2 = __ldg(tb.ax[1].rs + jr);
+        cf0.lo2 = cf1.lo2 = __ldg(tb.ax[1].lower + jr);
+        cf0.up2 = cf1.up2 = __ldg(tb.ax[1].upper + jr);
+    }
+    int kf = k0 + 1;
+    const double* go = Wall + (long long)jw * n1 + i + (long long)kf * n12;
+    const double* gh = Wall + (long long)(halo ? hj : 0) * n1 + hi + (long long)kf * n12;
+    const uint32_t r_own = smem_u32(ring + 2 * t), r_halo = smem_u32(ring + 2 * (blockDim.x + t));
+    const uint32_t slot_b = (uint32_t)(S * rs) * 8u, sp_b = (uint32_t)rs * 8u;
+    auto fetch = [&]() {
+        if (kf <= kend && kf < n3) {
+            const uint32_t so = (uint32_t)(kf & (kMarchAhead - 1)) * slot_b;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                if (ld) cp_async16(r_own + so + s * sp_b, go + s * npts);
+                if (halo) cp_async16(r_halo + so + s * sp_b, gh + s * npts);
+            }
+        }
+        cp_async_commit();
+        go += n12;
+        gh += n12;
+        ++kf;
+    };
+    float2 pm0[S], pc0[S], pn0[S], pm1[S], pc1[S], pn1[S];   // columns i and i + 1
+    pdl_wait();          // the state is the previous step's result
+    pdl_trigger();
+    for (int q = 0; q < kMarchAhead; ++q) fetch();
+    {
+        const double* g0 = Wall + (long long)jw * n1 + i + (long long)k0 * n12;
+        const double* h0 = Wall + (long long)(halo ? hj : 0) * n1 + hi + (long long)k0 * n12;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const double2 a = ld && k0 > 0 ? __ldg(reinterpret_cast<const double2*>(g0 + s * npts - n12)) : make_double2(0.0, 0.0);
+            const double2 b = ld ? __ldg(reinterpret_cast<const double2*>(g0 + s * npts)) : make_double2(0.0, 0.0);
+            pm0[s] = split_f64(a.x);
+            pm1[s] = split_f64(a.y);
+            pc0[s] = split_f64(b.x);
+            pc1[s] = split_f64(b.y);
+            if (ld) *reinterpret_cast<float4*>(pbuf + s * lpv + obuf) = make_float4(pc0[s].x, pc0[s].y, pc1[s].x, pc1[s].y);
+            if (halo) {
+                const double2 hv = __ldg(reinterpret_cast<const double2*>(h0 + s * npts));
+                const float2 u = split_f64(hv.x), v = split_f64(hv.y);
+                *reinterpret_cast<float4*>(pbuf + s * lpv + hbuf) = make_float4(u.x, u.y, v.x, v.y);
+            }
+        }
+    }
+    __syncthreads();
+    float* Fo = F + ((long long)k0 * n2 + (own ? jr : 0)) * n1q + i;
+    const long long fstep = (long long)n2 * n1q;
+    const bool hm0 = i > 0, hp1 = i + 1 < n1 - 1;
+    for (int k = k0; k < kend; ++k, Fo += fstep) {
+        const int b = (k - k0) & 1;
+        const float2* Bc = pbuf + b * S * lpv + obuf;
+        float2* Bn = pbuf + (b ^ 1) * S * lpv;
+        cp_async_wait<kMarchAhead - 1>();            // plane k + 1 landed (this thread's copies)
+        const double* R = ring + (size_t)((k + 1) & (kMarchAhead - 1)) * S * rs + 2 * t;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const double2 v = ld ? *reinterpret_cast<const double2*>(R + s * rs) : make_double2(0.0, 0.0);
+            pn0[s] = split_f64(v.x);
+            pn1[s] = split_f64(v.y);
+        }
+        if (own) {
+            const float rs3 = __ldg(tb.ax[2].rs + k), lo3 = __ldg(tb.ax[2].lower + k), up3 = __ldg(tb.ax[2].upper + k);
+            const float dp3 = (GEO == GEO_BALL) ? __ldg(tb.Dp + k) : 1.f;
+            cf0.rs3 = cf1.rs3 = rs3;
+            cf0.lo3 = cf1.lo3 = lo3;
+            cf0.up3 = cf1.up3 = up3;
+            cf0.dp3 = cf1.dp3 = dp3;
+            float w0[kMaxSpecies], w1[kMaxSpecies], g0[S], g1[S];
+#pragma unroll
+            for (int r = 0; r < kMaxSpecies; ++r) w0[r] = w1[r] = 0.f;
+#pragma unroll
+            for (int r = 0; r < S; ++r) {
+                w0[r] = pc0[r].x + pc0[r].y;
+                w1[r] = pc1[r].x + pc1[r].y;
+            }
+            reactions<float, S>(tb.reac, w0, g0);
+            reactions<float, S>(tb.reac, w1, g1);
+            const bool hkm = k > 0, hkp = k < n3 - 1;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                // every neighbour lies inside the buffer (lines 0 .. TJ + 1); the flags drop the absent ones
+                const float2* q = Bc + s * lpv;
+                const float4 jm = *reinterpret_cast<const float4*>(q - n1);
+                const float4 jp = *reinterpret_cast<const float4*>(q + n1);
+                const float2 m0 = q[-1], p1 = q[2];
+                const float f0 = point_F<GEO>(tb, s, g0[s], pc0[s], m0, pc1[s], make_float2(jm.x, jm.y),
+                                              make_float2(jp.x, jp.y), pm0[s], pn0[s], hm0, true, true, true, hkm, hkp,
+                                              cf0, 1.f);
+                const float f1 = point_F<GEO>(tb, s, g1[s], pc1[s], pc0[s], p1, make_float2(jm.z, jm.w),
+                                              make_float2(jp.z, jp.w), pm1[s], pn1[s], true, hp1, true, true, hkm, hkp,
+                                              cf1, 1.f);
+                *reinterpret_cast<float2*>(Fo + s * ys) = make_float2(f0, f1);
+            }
+        }
+        if (k + 1 < kend) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                if (ld)
+                    *reinterpret_cast<float4*>(Bn + s * lpv + obuf) = make_float4(pn0[s].x, pn0[s].y, pn1[s].x, pn1[s].y);
+                if (halo) {
+                    const double2 hv = *reinterpret_cast<const double2*>(R + s * rs + 2 * blockDim.x);
+                    const float2 u = split_f64(hv.x), v = split_f64(hv.y);
+                    *reinterpret_cast<float4*>(Bn + s * lpv + hbuf) = make_float4(u.x, u.y, v.x, v.y);
+                }
+            }
+        }
+        __syncthreads();
+        fetch();
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            pm0[s] = pc0[s];
+            pc0[s] = pn0[s];
+            pm1[s] = pc1[s];
+            pc1[s] = pn1[s];
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // ------------------------------------------------------------------------------
 // mode-3 pass: rows = 128 consecutive points of the padded (i, j) plane
 // (row index j * n1q + i), columns = the k fibre; reads F from Y and overwrites
@@ -1433,7 +1594,7 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 8, 1>, A, ring);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 4, 2>, A, ring);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_roll<GEO_CYLINDER, 8, 2>, A, ring);
-    const int march = 200 * 1024;   // march_smem <= 64 KB of pairs + 4 x 8 B x S (threads + 2 n1) <= 128 KB
+    const int march = 200 * 1024;   // the marching kernels: candidates and launcher keep march_smem within this
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 1>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 2>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_BALL, 3>, A, march);
@@ -1442,6 +1603,14 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 2>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 3>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<GEO_CYLINDER, 4>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_BALL, 1>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_BALL, 2>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_BALL, 3>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_BALL, 4>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 1>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 2>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 3>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 4>, A, march);
     return e;
 }
 
@@ -1498,6 +1667,20 @@ static cudaError_t launch_rhs_tile_geo(const SplitTables& T, cudaStream_t st) {
 // kernel whose all-species tile fits 220 KB, and, for the 3-D geometries,
 // (tile height, planes per CTA, register cap for 1 or 2 CTAs per SM) for the
 // rolling-window kernel whose plane holds at most 8 values per thread.
+// The marching stencil's launch: two columns per thread when n1 is even and the
+// state 16-byte aligned (then 16-byte copies apply), else one; threads and
+// shared memory (two planes of pairs and the ring of FP64 values).
+static bool march_pairs(const SplitTables& T) { return T.n1 % 2 == 0 && ((uintptr_t)T.state & 15u) == 0; }
+static int march_threads(int tj, int n1, bool pairs) {
+    return (std::max(tj, 2) * (pairs ? n1 / 2 : n1) + 31) / 32 * 32;
+}
+static size_t march_smem(int S, int tj, int n1, bool pairs) {
+    const int threads = march_threads(tj, n1, pairs);
+    const size_t ring_vals = pairs ? 2 * (size_t)(threads + n1) : (size_t)(threads + 2 * n1);
+    return 2 * sizeof(float2) * (size_t)S * (tj + 2) * n1 + sizeof(double) * kMarchAhead * S * ring_vals;
+}
+constexpr size_t kMarchSmemMax = 200 * 1024;
+
 int rhs_candidates(const SplitTables& T, int3* out, int max_out) {
     const bool k3 = T.geometry == GEO_BALL || T.geometry == GEO_CYLINDER;
     const size_t per_line = sizeof(float2) * (size_t)T.S * (k3 ? 10 : 1) * T.n1;
@@ -1510,6 +1693,9 @@ int rhs_candidates(const SplitTables& T, int3* out, int max_out) {
         const int tjs[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 20, 24, 28, 32};
         for (int tj : tjs) {
             if (tj > T.n2 || T.S > 4 || std::max(tj, 2) * T.n1 > maxt) break;
+            if (march_smem(T.S, tj, T.n1, false) > kMarchSmemMax ||
+                (T.n1 % 2 == 0 && march_smem(T.S, tj, T.n1, true) > kMarchSmemMax))
+                continue;
             const int kss[] = {2, 3, 4, 6, 8, 12, 16};
             for (int ks : kss)
                 if (ks <= T.n3 && n < max_out) out[n++] = make_int3(tj, ks, 0);
@@ -1523,23 +1709,28 @@ int rhs_candidates(const SplitTables& T, int3* out, int max_out) {
     return n;
 }
 
-// Shared memory of the marching stencil: two planes of pairs, the ring of FP64 values.
-static size_t march_smem(int S, int tj, int n1, int threads) {
-    return 2 * sizeof(float2) * (size_t)S * (tj + 2) * n1 + sizeof(double) * (size_t)kMarchAhead * S * (threads + 2 * n1);
-}
 
 template <int GEO>
 static cudaError_t launch_rhs_march_geo(const SplitTables& T, cudaStream_t st) {
     const int tj = T.rhs_tj, ks = T.rhs_ks;
-    const int threads = (std::max(tj, 2) * T.n1 + 31) / 32 * 32;
-    if (tj < 1 || tj > T.n2 || ks < 1 || T.S > kMaxSpecies || threads > (T.S <= 2 ? 1024 : 512))
+    if (tj < 1 || tj > T.n2 || ks < 1 || T.S < 1 || T.S > kMaxSpecies ||
+        std::max(tj, 2) * T.n1 > (T.S <= 2 ? 1024 : 512))
         return cudaErrorInvalidValue;
-    const size_t smem = march_smem(T.S, tj, T.n1, threads);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const bool pairs = march_pairs(T);
+    const int threads = march_threads(tj, T.n1, pairs);
+    const size_t smem = march_smem(T.S, tj, T.n1, pairs);
+    if (smem > kMarchSmemMax) return cudaErrorInvalidValue;
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + ks - 1) / ks, 1);
-    auto kern = T.S == 1 ? k_rhs_march<GEO, 1>
-              : T.S == 2 ? k_rhs_march<GEO, 2> : T.S == 3 ? k_rhs_march<GEO, 3> : k_rhs_march<GEO, 4>;
-    cudaError_t e = launch_pdl(kern, grid, dim3(threads), smem, st, T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+    cudaError_t e;
+    if (pairs) {
+        auto kern = T.S == 1 ? k_rhs_march2<GEO, 1>
+                  : T.S == 2 ? k_rhs_march2<GEO, 2> : T.S == 3 ? k_rhs_march2<GEO, 3> : k_rhs_march2<GEO, 4>;
+        e = launch_pdl(kern, grid, dim3(threads), smem, st, T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+    } else {
+        auto kern = T.S == 1 ? k_rhs_march<GEO, 1>
+                  : T.S == 2 ? k_rhs_march<GEO, 2> : T.S == 3 ? k_rhs_march<GEO, 3> : k_rhs_march<GEO, 4>;
+        e = launch_pdl(kern, grid, dim3(threads), smem, st, T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

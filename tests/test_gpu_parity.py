@@ -211,24 +211,49 @@ STENCIL_CASES = [
     ("ball", ball((37, 29, 23)), [(1, 0), (7, 0), (2, 2), (4, 4), (10, 8, 2), (16, 16), (24, 2, 2),
                                   (1, 2, 0), (5, 3, 0), (24, 16, 0)]),
     ("cylinder", cyl((24, 40, 37), steps=3), [(3, 0), (2, 16, 2), (8, 4), (24, 8, 2), (3, 4, 0), (20, 12, 0)]),
+    ("ball_even_rho", ball((36, 29, 23)), [(7, 0), (4, 4), (10, 8, 2), (1, 2, 0), (5, 3, 0), (24, 16, 0)]),
 ]
 
 
 @pytest.mark.parametrize("name,w,configs", STENCIL_CASES, ids=[c[0] for c in STENCIL_CASES])
 def test_every_stencil_configuration_matches_oracle(name, w, configs):
     """The stencil kernels (tiled: planes = 0; rolling window: planes > 0, registers capped for one
-    or two CTAs per SM; k-marching: planes > 0, ctas_per_sm = 0), forced through sexpe_set_stencil at several tile shapes with ragged last
+    or two CTAs per SM; k-marching: planes > 0, ctas_per_sm = 0, with one column per thread for odd
+    n_rho and two for even n_rho), forced through sexpe_set_stencil at several tile shapes with ragged last
     tiles, give the oracle's result; the
     F they write is the same whatever the shape (the rest of the step is identical)."""
     ref = oracle_run(w)
     outs = []
     for cfg in configs:
         got = gpu_run(w, "split_tf32", stencil=cfg)
-        if name == "ball":
+        if name.startswith("ball"):
             assert_parity(got, ref, w["W0"], 1e-6, 1e-5)
         outs.append(got)
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+SPECIES_CASES = [
+    ("cylinder_1species", wl.linear_cubic_cylinder(n=(20, 24, 18), steps=3, seed=21, d=(2e-3,)),
+     [(3, 0), (2, 4, 2), (4, 3, 0), (16, 8, 0)]),
+    ("cylinder_4species", wl.linear_cubic_cylinder(n=(20, 24, 18), steps=3, seed=22, d=(1e-3, 3e-3, 5e-3, 2e-2)),
+     [(3, 0), (2, 4, 1), (5, 3, 0), (16, 6, 0)]),
+]
+
+
+@pytest.mark.parametrize("name,w,configs", SPECIES_CASES, ids=[c[0] for c in SPECIES_CASES])
+def test_species_counts_every_stencil_kernel(name, w, configs):
+    """One and four species (the marching stencil is instantiated per species count): every stencil
+    kernel gives the same F, and the step stays within 8x the FP32-storage floor of the oracle
+    (rough N(0, 0.01^2) data, as for the 3-species cylinder)."""
+    ref = oracle_run(w)
+    floor = emulated_fp32_errors(w, ref)
+    outs = [gpu_run(w, "split_tf32", stencil=cfg) for cfg in configs]
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    e = rel_errors(outs[0], ref)
+    for s in range(len(e)):
+        assert e[s] <= max(1e-6, 8 * floor[s]), (s, e, floor)
 
 
 def test_every_theta_split_matches_oracle():

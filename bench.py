@@ -62,7 +62,7 @@ def max_over_ranks(value, world):
 
 
 # ----------------------------------------------------------------------------- algorithmic work
-PROFILE_STENCIL = (6, 12, 0)   # j-lines, k-planes per CTA, 0 = the k-marching stencil kernel
+PROFILE_STENCIL = (5, 8, 0)   # j-lines, k-planes per CTA, 0 = the k-marching stencil kernel
 
 
 def kernel_work(n, S):

@@ -233,6 +233,26 @@ def test_every_stencil_configuration_matches_oracle(name, w, configs):
         assert np.array_equal(o, outs[0])
 
 
+def test_march_stencil_state_alignment():
+    """A state that is 8- but not 16-byte aligned takes the one-column marching kernel (the
+    two-column kernel's 16-byte copies need 16-byte alignment): same result bit for bit."""
+    import torch
+    from paper_2604_11558_gb300 import binding
+    w = ball((36, 29, 23), steps=4)
+    plan = binding.Plan.from_workload(w, precision="split_tf32")
+    plan.set_stencil(5, 3, 0)
+    x = torch.from_numpy(np.ascontiguousarray(w["W0"])).cuda()
+    buf = torch.zeros(x.numel() + 1, dtype=torch.float64, device="cuda")
+    y = buf[1:].view(x.shape)
+    y.copy_(x)
+    assert x.data_ptr() % 16 == 0 and y.data_ptr() % 16 == 8
+    plan.step(x, w["steps"])
+    plan.step(y, w["steps"])
+    plan.synchronize()
+    assert torch.equal(x, y)
+    plan.close()
+
+
 SPECIES_CASES = [
     ("cylinder_1species", wl.linear_cubic_cylinder(n=(20, 24, 18), steps=3, seed=21, d=(2e-3,)),
      [(3, 0), (2, 4, 2), (4, 3, 0), (16, 8, 0)]),

@@ -51,7 +51,15 @@ typedef enum { SEXPE_DISK = 0, SEXPE_SPHERE = 1, SEXPE_BALL = 2, SEXPE_CYLINDER 
  * mu-mode product on tcgen05 tensor cores as three TF32 products
  * (hi*hi + hi*lo + lo*hi, each operand split x = hi + lo with both parts
  * rounded to TF32) accumulated in FP32 in tensor memory; the state stays FP64. */
-typedef enum { SEXPE_FP64 = 0, SEXPE_SPLIT_TF32 = 1 } sexpe_precision;
+typedef enum { SEXPE_FP64 = 0, SEXPE_SPLIT_TF32 = 1, SEXPE_UNSPLIT_FP64 = 2 } sexpe_precision;
+/* UNSPLIT_FP64 is not the split method: it is unsplit exponential Euler (eq. ee
+ * with phi_1 of the whole operator, w_s += tau phi_1(tau d_s M) F_s,
+ * M = M_1 + ... + M_d the assembled Kronecker sum), the accuracy baseline that
+ * the splitting error of Section 4 is measured against.  phi_1(tau d_s M) is
+ * formed densely at setup by the same [13/13] Pade scaling and squaring, so it
+ * is limited to grids of at most 2048 points (larger: SEXPE_EUNSUPPORTED); a
+ * step is the FP64 stencil+reaction and one dense FP64 matrix-vector product
+ * per species with the update fused.  No adjoint, no batch. */
 
 /* Reaction terms g_s(w), evaluated pointwise.
  *   SCHNAKENBERG (S=2), params {gamma, a, b}: f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)

@@ -20,6 +20,9 @@ What it computes, in plain numpy/scipy FP64 and in the paper's order:
 * ``stepper``   -- one split exponential Euler step (eq. ee with the split
                    approximation eq. splitorder), applying phi_1(tau d M_mu)
                    fibre by fibre with the highest mode first.
+* ``unsplit``   -- unsplit exponential Euler (eq. ee with phi_1 of the whole
+                   assembled operator, dense expm): the baseline the splitting
+                   error is measured against.
 * ``adjoint``   -- gradients of a scalar loss by complex-step differentiation
                    through ``stepper`` (no transposed code path of its own).
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsexpe.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "sexpe.h")
 
 GEOMETRY = {"disk": 0, "sphere": 1, "ball": 2, "cylinder": 3}
-PRECISION = {"fp64": 0, "split_tf32": 1}
+PRECISION = {"fp64": 0, "split_tf32": 1, "unsplit_fp64": 2}
 REACTION = {"none": 0, "schnakenberg": 1, "gray_scott": 2, "linear_cubic": 3, "bvam": 4, "bvam_manufactured": 5}
 ZBC = {"neumann": 0, "paper": 1}
 AXIS = {"theta": 0, "rho2": 1, "rho3": 2, "phi": 3, "z_neumann": 4, "z_paper": 5}

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <limits>
 #include <stdexcept>
+#include <thread>
 
 namespace sexpe {
 
@@ -253,18 +254,31 @@ Eigen tridiag_eigen(const Axis& ax) {
 // Elements of the algebra {[[T, B], [0, c I]]} closed under +, * and inversion
 // of the (V - U) factor; expm([[X, I], [0, 0]]) = [[e^X, phi_1(X)], [0, I]].
 
+// Rows are split over host threads for large n (the dense phi_1 of an assembled
+// operator); every row is computed in the same order whatever the split.
 static Mat matmul(const Mat& A, const Mat& B) {
     const int n = A.n;
     Mat C(n);
-    for (int i = 0; i < n; ++i) {
-        double* ci = &C.a[(size_t)i * n];
-        for (int k = 0; k < n; ++k) {
-            double aik = A(i, k);
-            if (aik == 0.0) continue;
-            const double* bk = &B.a[(size_t)k * n];
-            for (int j = 0; j < n; ++j) ci[j] += aik * bk[j];
+    auto rows = [&](int r0, int r1) {
+        for (int i = r0; i < r1; ++i) {
+            double* ci = &C.a[(size_t)i * n];
+            for (int k = 0; k < n; ++k) {
+                double aik = A(i, k);
+                if (aik == 0.0) continue;
+                const double* bk = &B.a[(size_t)k * n];
+                for (int j = 0; j < n; ++j) ci[j] += aik * bk[j];
+            }
         }
+    };
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nt = n >= 256 ? std::max(1, std::min(hw, 32)) : 1;
+    if (nt == 1) {
+        rows(0, n);
+        return C;
     }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(rows, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
+    for (std::thread& th : pool) th.join();
     return C;
 }
 
@@ -304,33 +318,54 @@ static Aug aug_identity(int n) {
     return z;
 }
 
-// Solve P X = R for X (n x n right-hand sides) by LU with partial pivoting.
+// Solve P X = R for X (n x n right-hand sides) by LU with partial pivoting: P is
+// factored first (multipliers kept below the diagonal, pivots recorded), then
+// the right-hand-side columns are eliminated and back-substituted in blocks on
+// host threads, every column with the same operations in the same order.
 static Mat lu_solve(Mat P, Mat R) {
     const int n = P.n;
+    std::vector<int> piv(n);
     for (int k = 0; k < n; ++k) {
-        int piv = k;
+        int pk = k;
         for (int i = k + 1; i < n; ++i)
-            if (std::fabs(P(i, k)) > std::fabs(P(piv, k))) piv = i;
-        if (P(piv, k) == 0.0) throw std::runtime_error("singular Pade denominator");
-        if (piv != k) {
-            for (int j = 0; j < n; ++j) std::swap(P(k, j), P(piv, j));
-            for (int j = 0; j < n; ++j) std::swap(R(k, j), R(piv, j));
-        }
+            if (std::fabs(P(i, k)) > std::fabs(P(pk, k))) pk = i;
+        if (P(pk, k) == 0.0) throw std::runtime_error("singular Pade denominator");
+        piv[k] = pk;
+        if (pk != k)
+            for (int j = 0; j < n; ++j) std::swap(P(k, j), P(pk, j));
         for (int i = k + 1; i < n; ++i) {
-            double f = P(i, k) / P(k, k);
+            const double f = P(i, k) / P(k, k);
+            P(i, k) = f;
             if (f == 0.0) continue;
-            P(i, k) = 0.0;
             for (int j = k + 1; j < n; ++j) P(i, j) -= f * P(k, j);
-            for (int j = 0; j < n; ++j) R(i, j) -= f * R(k, j);
         }
     }
-    for (int k = n - 1; k >= 0; --k) {
-        for (int j = 0; j < n; ++j) {
-            double s = R(k, j);
-            for (int i = k + 1; i < n; ++i) s -= P(k, i) * R(i, j);
-            R(k, j) = s / P(k, k);
+    auto cols = [&](int c0, int c1) {
+        for (int k = 0; k < n; ++k) {
+            if (piv[k] != k)
+                for (int j = c0; j < c1; ++j) std::swap(R(k, j), R(piv[k], j));
+            for (int i = k + 1; i < n; ++i) {
+                const double f = P(i, k);
+                if (f == 0.0) continue;
+                for (int j = c0; j < c1; ++j) R(i, j) -= f * R(k, j);
+            }
         }
+        for (int k = n - 1; k >= 0; --k)
+            for (int j = c0; j < c1; ++j) {
+                double s = R(k, j);
+                for (int i = k + 1; i < n; ++i) s -= P(k, i) * R(i, j);
+                R(k, j) = s / P(k, k);
+            }
+    };
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nt = n >= 256 ? std::max(1, std::min(hw, 32)) : 1;
+    if (nt == 1) {
+        cols(0, n);
+        return R;
     }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(cols, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
+    for (std::thread& th : pool) th.join();
     return R;
 }
 

@@ -94,6 +94,28 @@ __global__ void __launch_bounds__(256) k_gemm64(Gemm64 g) {
     }
 }
 
+// Unsplit baseline: W_s[r] += tau sum_k P_s[r][k] F_s[k] (row-major N x N per
+// species), one warp per row, lanes striding the row (coalesced), a warp-shuffle
+// reduction, then the update by lane 0.  grid (ceil(N / 8), S), 256 threads.
+__global__ void __launch_bounds__(256) k_matvec64(const double* __restrict__ P, const double* __restrict__ F,
+                                                  double* __restrict__ W, int N, double tau) {
+    const int s = blockIdx.y;
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const double* pr = P + ((long long)s * N + row) * N;
+    const double* f = F + (long long)s * N;
+    double acc = 0.0;
+    for (int k = lane; k < N; k += 32) acc = fma(__ldg(pr + k), __ldg(f + k), acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) W[(long long)s * N + row] += tau * acc;
+}
+
+cudaError_t launch_matvec64(const double* P, const double* F, double* W, int N, int S, double tau, cudaStream_t st) {
+    k_matvec64<<<dim3((N + 7) / 8, S), 256, 0, st>>>(P, F, W, N, tau);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Discrete adjoint of the step (derived from eqs. ee and splitorder; the paper
 // has no adjoint).  With mu_s = tau P_s^T lambda_s:

@@ -286,6 +286,49 @@ sexpe_status build_fp64(sexpe_plan* p, cudaStream_t st) {
     return SEXPE_OK;
 }
 
+// Unsplit exponential Euler (the accuracy baseline of the splitting, eq. ee with
+// phi_1 of the whole operator): M = M_1 + ... + M_d assembled densely from the
+// same 1-D axes and diagonal factors as the split chain (each point's row gets
+// s * A_mu along every mode mu, s the direction's scale at the point), then
+// P_s = phi_1(tau d_s M) by Pade scaling and squaring.  N_pts <= 2048.
+constexpr long long kUnsplitMaxPts = 2048;
+
+sexpe_status build_unsplit(sexpe_plan* p, cudaStream_t st) {
+    if (p->npts > kUnsplitMaxPts) return SEXPE_EUNSUPPORTED;
+    const int N = (int)p->npts;
+    SX_TRY(build_rhs_tables<double>(p, &p->rhs64, st));
+    SX_TRY(alloc_dev(p, (size_t)p->S * p->npts, &p->buf64[0]));
+    Mat M(N);
+    for (int k = 0; k < p->n[2]; ++k)
+        for (int j = 0; j < p->n[1]; ++j)
+            for (int i = 0; i < p->n[0]; ++i) {
+                const int c[3] = {i, j, k};
+                const int row = i + p->n[0] * (j + p->n[1] * k);
+                for (int mu = 1; mu <= p->ndim; ++mu) {
+                    const Axis& a = p->ax[mu - 1];
+                    const int r = c[mu - 1], n = a.n;
+                    const int stride = mu == 1 ? 1 : (mu == 2 ? p->n[0] : p->n[0] * p->n[1]);
+                    const double sc = dir_scale(p, mu, i, j, k);
+                    M(row, row) += sc * a.diag[r];
+                    if (r > 0) M(row, row - stride) += sc * a.lower[r];
+                    else if (a.periodic) M(row, row + (n - 1) * stride) += sc * a.lower[r];
+                    if (r < n - 1) M(row, row + stride) += sc * a.upper[r];
+                    else if (a.periodic) M(row, row - (n - 1) * stride) += sc * a.upper[r];
+                }
+            }
+    std::vector<double> P((size_t)p->S * N * N);
+    for (int s = 0; s < p->S; ++s) {
+        Mat X(N);
+        for (size_t q = 0; q < X.a.size(); ++q) X.a[q] = p->tau * p->d[s] * M.a[q];
+        const Mat R = phi1_pade(X);
+        std::memcpy(&P[(size_t)s * N * N], R.a.data(), sizeof(double) * (size_t)N * N);
+    }
+    if (!all_finite(P)) return SEXPE_ENUMERIC;
+    SX_TRY(upload(p, P, &p->unsplit_P, st));
+    p->kernels_per_step = 2;
+    return SEXPE_OK;
+}
+
 // Measured choice of the stencil tile height (the autotuner of the split path):
 // every feasible height is timed with CUDA events -- one warm-up launch, then
 // three launches -- on a zeroed scratch state of the plan's shape, and the
@@ -619,6 +662,16 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
         p->bparity ^= 1;
         return SEXPE_OK;
     }
+    if (p->precision == SEXPE_UNSPLIT_FP64) {
+        // w_s += tau P_s F_s: one dense matrix-vector product per species, update fused
+        const long long N = p->npts;
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_rhs64(p->geometry, p->rhs64, state, p->buf64[0], st));
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_matvec64(p->unsplit_P, p->buf64[0], state, (int)N, p->S, p->tau, st));
+        if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
+        return SEXPE_OK;
+    }
     if (p->precision == SEXPE_FP64) {
         SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_rhs64(p->geometry, p->rhs64, state, p->buf64[0], st));
@@ -669,7 +722,7 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
 sexpe_status validate(const sexpe_grid* g, const sexpe_species* sp, double tau, int32_t precision) {
     if (!g || !sp) return SEXPE_EINVAL;
     if (g->geometry < SEXPE_DISK || g->geometry > SEXPE_CYLINDER) return SEXPE_EINVAL;
-    if (precision != SEXPE_FP64 && precision != SEXPE_SPLIT_TF32) return SEXPE_EINVAL;
+    if (precision != SEXPE_FP64 && precision != SEXPE_SPLIT_TF32 && precision != SEXPE_UNSPLIT_FP64) return SEXPE_EINVAL;
     if (!(tau > 0.0) || !std::isfinite(tau)) return SEXPE_EINVAL;
     const int ndim = (g->geometry == SEXPE_BALL || g->geometry == SEXPE_CYLINDER) ? 3 : 2;
     for (int m = 0; m < ndim; ++m)
@@ -764,6 +817,7 @@ sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species*
     SX_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st));
     SX_TRY(alloc_dev(p, (size_t)p->S * p->npts, &p->d_host_state));
     if (precision == SEXPE_FP64) SX_TRY(build_fp64(p, st));
+    else if (precision == SEXPE_UNSPLIT_FP64) SX_TRY(build_unsplit(p, st));
     else SX_TRY(build_split(p, st));
     SX_CUDA(cudaStreamSynchronize(st));   // host vectors of the uploads go out of scope
     return SEXPE_OK;

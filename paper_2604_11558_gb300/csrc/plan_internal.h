@@ -49,6 +49,7 @@ struct sexpe_plan {
     sexpe::RhsTables<double> rhs64{};
     std::vector<sexpe::Dir64> dirs64;
     double* buf64[3] = {nullptr, nullptr, nullptr};
+    const double* unsplit_P = nullptr;     // unsplit baseline: phi_1(tau d_s M), S x N x N
     // split path
     sexpe::SplitTables tabs{};
     sexpe::TcShape sh3{}, shs{};

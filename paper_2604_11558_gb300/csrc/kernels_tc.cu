@@ -59,7 +59,7 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 constexpr int kRows = 128;                 // MMA M and tensor-memory lanes
 constexpr int kThreads = 256;              // producer threads: two per row, columns 0-7 / 8-15 of a chunk
 constexpr int kBlock = kThreads + 64;      // + one warp issuing TMA copies ahead, one issuing the MMAs
-constexpr int kMaxMat = 6;                 // matrix-ring slots (TMA lookahead)
+constexpr int kMaxMat = 4;                 // matrix-ring slots (TMA lookahead; at most the data-ring slots)
 constexpr int kMaxData = 4;                // data-ring slots
 constexpr uint32_t kHeaderBytes = 256;     // barriers + tensor-memory slot + abort flag
 
@@ -70,7 +70,6 @@ constexpr uint32_t kHeaderBytes = 256;     // barriers + tensor-memory slot + ab
 // tcgen05.commit, so the TMA warp can run nm chunks ahead of the MMAs while
 // the producers run nd chunks ahead.
 struct Pipe {
-    uint64_t* mat_full;     // (unused: the matrix copies complete on data_full)
     uint64_t* mat_empty;    // MMAs reading the matrix slot completed
     uint64_t* data_full;    // chunk ready: one arrive per producer warp + the matrix copy (TMA
                             // thread's arrive and transaction count)
@@ -320,16 +319,13 @@ __device__ __forceinline__ CtaRes cta_begin(char* smem_raw, const TcShape& rs, i
     const uint32_t base = smem_u32(smem_raw);
     char* smem = smem_raw + (((base + 127u) & ~127u) - base);   // 128-byte aligned rings
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * (kMaxMat + kMaxData) * sizeof(uint64_t));
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + (kMaxMat + 2 * kMaxData) * sizeof(uint64_t));
     int* aborted = reinterpret_cast<int*>(tslot + 4);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kMaxMat; ++s) {
-            mbar_init(&bars[s], 1);                          // mat_full: the TMA thread's expect_tx
-            mbar_init(&bars[kMaxMat + s], 1);                // mat_empty: tcgen05.commit
-        }
+        for (int s = 0; s < kMaxMat; ++s) mbar_init(&bars[s], 1);   // mat_empty: tcgen05.commit
         for (int s = 0; s < kMaxData; ++s) {
-            mbar_init(&bars[2 * kMaxMat + s], kThreads / 32 + 1);      // data_full: producer warps + TMA
-            mbar_init(&bars[2 * kMaxMat + kMaxData + s], 1);           // data_empty: tcgen05.commit
+            mbar_init(&bars[kMaxMat + s], kThreads / 32 + 1);              // data_full: producer warps + TMA
+            mbar_init(&bars[kMaxMat + kMaxData + s], 1);                   // data_empty: tcgen05.commit
         }
         *aborted = 0;
         fence_mbar_init();
@@ -342,10 +338,9 @@ __device__ __forceinline__ CtaRes cta_begin(char* smem_raw, const TcShape& rs, i
     __syncthreads();
     tc_fence_after();
     CtaRes r;
-    r.P.mat_full = bars;
-    r.P.mat_empty = bars + kMaxMat;
-    r.P.data_full = bars + 2 * kMaxMat;
-    r.P.data_empty = bars + 2 * kMaxMat + kMaxData;
+    r.P.mat_empty = bars;
+    r.P.data_full = bars + kMaxMat;
+    r.P.data_empty = bars + kMaxMat + kMaxData;
     r.P.mat_slots = smem + kHeaderBytes;
     r.P.data_slots = r.P.mat_slots + (size_t)rs.nm * rs.mat_bytes;
     r.P.mat_bytes = rs.mat_bytes;
@@ -1461,9 +1456,10 @@ static uint32_t pow2_cols(uint32_t c) {
 }
 
 // Ring depths and shared-memory size.  With `pair`, the rings are sized so
-// that two CTAs share an SM (228 KB per SM, 1 KB reserved per CTA): three data
-// slots and as many matrix slots (up to kMaxMat) as fit, fewer data slots only
-// if three matrix slots would not fit; otherwise (or if even two and two do not
+// that two CTAs share an SM (228 KB per SM, 1 KB reserved per CTA): up to four
+// data slots and as many matrix slots as fit, at most as many as data slots
+// (the matrix copies complete on the data barriers), fewer data slots only if
+// three matrix slots would not fit; otherwise (or if even two and two do not
 // fit) one CTA takes the SM's 227 KB.
 static void rings(TcShape& sh, uint32_t min_body, bool pair) {
     const uint32_t slack = 128 + kHeaderBytes;                 // ring alignment + barriers

@@ -40,8 +40,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cylinder, batched-disk and sphere-adjoint measurements")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run only setup + 3 + 3 split steps, the last 3 inside the NVTX range sexpe_step (for an ncu capture of the step kernels)")
+    ap.add_argument("--profile-case", nargs="?", const="ball", default=None, choices=["ball", "sphere", "batch"],
+                    help="run only setup + 3 + 3 split steps of the ball workload (or the 256 x 512 sphere, or the "
+                         "256 batched disks), the last 3 inside the NVTX range sexpe_step (for an ncu capture of "
+                         "the step kernels)")
     return ap.parse_args()
 
 
@@ -63,6 +65,7 @@ def max_over_ranks(value, world):
 
 # ----------------------------------------------------------------------------- algorithmic work
 PROFILE_STENCIL = (5, 8, 0)   # j-lines, k-planes per CTA, 0 = the k-marching stencil kernel
+PROFILE_THETA_SPLIT = 8        # sphere 256 x 512: theta-kernel column split the tuner picks
 
 
 def kernel_work(n, S):
@@ -225,6 +228,8 @@ def main():
     from paper_2604_11558_gb300 import binding
     from paper_2604_11558_gb300 import workloads as wl
 
+    if args.profile_case in ("sphere", "batch"):
+        return profile_other(args.profile_case)
     w = wl.gray_scott_ball()
     n, S = w["n"], len(w["d"])
     dof = S * int(np.prod(n))
@@ -441,6 +446,31 @@ def measure_extras(flush):
                                           "steps": steps, "checkpoint_every": every}
     plan.close()
     return out
+
+
+def profile_other(case):
+    """Setup, 3 untimed steps, then 3 steps in the NVTX range sexpe_step, of the 256 x 512 sphere or
+    the 256 batched disks (split path), for an ncu capture of their kernels."""
+    import torch
+    from paper_2604_11558_gb300 import binding
+    from paper_2604_11558_gb300 import workloads as wl
+    if case == "sphere":
+        w = wl.schnakenberg_sphere(steps=1)
+        plan = binding.Plan.from_workload(w, precision="split_tf32")
+        plan.set_theta_split(PROFILE_THETA_SPLIT)     # the unprofiled tuner's choice (timings under a profiler differ)
+        x = torch.from_numpy(w["W0"]).cuda()
+    else:
+        ws = wl.batched_disks(steps=1)
+        plan = binding.BatchPlan(ws)
+        import numpy as np
+        x = torch.from_numpy(np.concatenate([wq["W0"].ravel() for wq in ws])).cuda()
+    plan.step(x, 3)
+    plan.synchronize()
+    torch.cuda.nvtx.range_push("sexpe_step")
+    plan.step(x, 3)
+    plan.synchronize()
+    torch.cuda.nvtx.range_pop()
+    plan.close()
 
 
 def kernel_source_hash():

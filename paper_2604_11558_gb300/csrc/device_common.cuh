@@ -149,33 +149,56 @@ __device__ __forceinline__ T reaction(const ReactionParams<T>& rp, const T* w_st
 
 // Reaction terms of every species at one point, g[s] equal to reaction<T>(rp, w_state, s) bit
 // for bit (the same operations), with the kind tested once per point by uniform branches
-// rather than once per species, and the terms two species share formed once.
-template <class T, int NS>
+// rather than once per species, and the terms two species share formed once.  KIND >= 0
+// compiles only that kind (the caller knows it).
+template <class T>
+__device__ __forceinline__ void reac_gray_scott(const ReactionParams<T>& rp, const T* w, T* g) {
+    const T uv2 = mul_t(mul_t(w[0], w[1]), w[1]);
+    g[0] = fma_t(rp.p[0], (T)1 - w[0], -uv2);
+    g[1] = fma_t(-(rp.p[0] + rp.p[1]), w[1], uv2);
+}
+template <class T>
+__device__ __forceinline__ void reac_schnakenberg(const ReactionParams<T>& rp, const T* w, T* g) {
+    const T u2v = mul_t(mul_t(w[0], w[0]), w[1]);
+    g[0] = mul_t(rp.p[0], (rp.p[1] - w[0]) + u2v);
+    g[1] = mul_t(rp.p[0], rp.p[2] - u2v);
+}
+template <class T>
+__device__ __forceinline__ void reac_schnakenberg_lifted(const ReactionParams<T>& rp, const T* w_state, T* g) {
+    const T wu = w_state[0], wv = w_state[1];
+    const T N = fma_t(rp.q[2], wu, mul_t(rp.q[3], wv));
+    const T Q = mul_t(wu, fma_t(rp.q[4], wu, fma_t(rp.q[5], wv, mul_t(wu, wv))));
+    g[0] = mul_t(rp.p[0], (N + Q - wu) + rp.q[0]);
+    g[1] = mul_t(rp.p[0], rp.q[1] - (N + Q));
+}
+
+template <class T, int NS, int KIND = -1>
 __device__ __forceinline__ void reactions(const ReactionParams<T>& rp, const T* w_state, T* g) {
 #pragma unroll
     for (int r = 0; r < NS; ++r) g[r] = (T)0;
     T w[kMaxSpecies];
 #pragma unroll
     for (int r = 0; r < kMaxSpecies; ++r) w[r] = r < NS ? w_state[r] + rp.off[r] : (T)0;
-    if constexpr (NS >= 2) {     // the two-species kinds
+    if constexpr (NS >= 2 && KIND == R_GRAY_SCOTT) {
+        reac_gray_scott(rp, w, g);
+        return;
+    }
+    if constexpr (NS >= 2 && KIND == R_SCHNAKENBERG) {
+        if (rp.lifted) reac_schnakenberg_lifted(rp, w_state, g);
+        else reac_schnakenberg(rp, w, g);
+        return;
+    }
+    if constexpr (NS >= 2 && KIND < 0) {     // the two-species kinds
         if (rp.lifted) {
-            const T wu = w_state[0], wv = w_state[1];
-            const T N = fma_t(rp.q[2], wu, mul_t(rp.q[3], wv));
-            const T Q = mul_t(wu, fma_t(rp.q[4], wu, fma_t(rp.q[5], wv, mul_t(wu, wv))));
-            g[0] = mul_t(rp.p[0], (N + Q - wu) + rp.q[0]);
-            g[1] = mul_t(rp.p[0], rp.q[1] - (N + Q));
+            reac_schnakenberg_lifted(rp, w_state, g);
             return;
         }
         if (rp.kind == R_GRAY_SCOTT) {
-            const T uv2 = mul_t(mul_t(w[0], w[1]), w[1]);
-            g[0] = fma_t(rp.p[0], (T)1 - w[0], -uv2);
-            g[1] = fma_t(-(rp.p[0] + rp.p[1]), w[1], uv2);
+            reac_gray_scott(rp, w, g);
             return;
         }
         if (rp.kind == R_SCHNAKENBERG) {
-            const T u2v = mul_t(mul_t(w[0], w[0]), w[1]);
-            g[0] = mul_t(rp.p[0], (rp.p[1] - w[0]) + u2v);
-            g[1] = mul_t(rp.p[0], rp.p[2] - u2v);
+            reac_schnakenberg(rp, w, g);
             return;
         }
         if (rp.kind == R_BVAM || rp.kind == R_BVAM_MMS) {
@@ -186,15 +209,17 @@ __device__ __forceinline__ void reactions(const ReactionParams<T>& rp, const T* 
             return;
         }
     }
-    if (rp.kind == R_LINEAR_CUBIC) {
+    if constexpr (KIND < 0) {
+        if (rp.kind == R_LINEAR_CUBIC) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            if (s < rp.S) {
-                T acc = -mul_t(mul_t(w[s], w[s]), w[s]);
+            for (int s = 0; s < NS; ++s) {
+                if (s < rp.S) {
+                    T acc = -mul_t(mul_t(w[s], w[s]), w[s]);
 #pragma unroll
-                for (int r = 0; r < NS; ++r)
-                    if (r < rp.S) acc = fma_t(rp.p[s * rp.S + r], w[r], acc);
-                g[s] = acc;
+                    for (int r = 0; r < NS; ++r)
+                        if (r < rp.S) acc = fma_t(rp.p[s * rp.S + r], w[r], acc);
+                    g[s] = acc;
+                }
             }
         }
     }

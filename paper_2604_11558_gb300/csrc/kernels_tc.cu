@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(SM <= 2 ? 1024 : 512, 1)
 // the other side taken from the thread's own registers; half the threads of
 // k_rhs_march for the same tile and the same F bit for bit (same pairs, same
 // point formula).
-template <int GEO, int SM>
+template <int GEO, int SM, int RK = -1>
 __global__ void __launch_bounds__(512, 1)
     k_rhs_march2(RhsTables<float> tb, const double* __restrict__ Wall, float* __restrict__ F, int TJ, int KS, int n1q,
                  long long ys) {
@@ -919,8 +919,8 @@ __global__ void __launch_bounds__(512, 1)
                 w0[r] = pc0[r].x + pc0[r].y;
                 w1[r] = pc1[r].x + pc1[r].y;
             }
-            reactions<float, S>(tb.reac, w0, g0);
-            reactions<float, S>(tb.reac, w1, g1);
+            reactions<float, S, RK>(tb.reac, w0, g0);
+            reactions<float, S, RK>(tb.reac, w1, g1);
             const bool hkm = k > 0, hkp = k < n3 - 1;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
@@ -1607,6 +1607,10 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 2>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 3>, A, march);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 4>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_BALL, 2, R_GRAY_SCOTT>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_BALL, 2, R_SCHNAKENBERG>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 2, R_GRAY_SCOTT>, A, march);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march2<GEO_CYLINDER, 2, R_SCHNAKENBERG>, A, march);
     return e;
 }
 
@@ -1719,8 +1723,12 @@ static cudaError_t launch_rhs_march_geo(const SplitTables& T, cudaStream_t st) {
     dim3 grid((T.n2 + tj - 1) / tj, (T.n3 + ks - 1) / ks, 1);
     cudaError_t e;
     if (pairs) {
+        // two-species Gray-Scott / Schnakenberg: the reaction kind compiled in (same arithmetic)
+        const int kind = T.rhs.reac.kind;
         auto kern = T.S == 1 ? k_rhs_march2<GEO, 1>
-                  : T.S == 2 ? k_rhs_march2<GEO, 2> : T.S == 3 ? k_rhs_march2<GEO, 3> : k_rhs_march2<GEO, 4>;
+                  : T.S == 2 ? (kind == R_GRAY_SCOTT ? k_rhs_march2<GEO, 2, R_GRAY_SCOTT>
+                                : kind == R_SCHNAKENBERG ? k_rhs_march2<GEO, 2, R_SCHNAKENBERG> : k_rhs_march2<GEO, 2>)
+                  : T.S == 3 ? k_rhs_march2<GEO, 3> : k_rhs_march2<GEO, 4>;
         e = launch_pdl(kern, grid, dim3(threads), smem, st, T.rhs, T.state, T.Y, tj, ks, T.n1q, T.ys);
     } else {
         auto kern = T.S == 1 ? k_rhs_march<GEO, 1>

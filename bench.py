@@ -40,10 +40,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cylinder, batched-disk and sphere-adjoint measurements")
-    ap.add_argument("--profile-case", nargs="?", const="ball", default=None, choices=["ball", "sphere", "batch"],
-                    help="run only setup + 3 + 3 split steps of the ball workload (or the 256 x 512 sphere, or the "
-                         "256 batched disks), the last 3 inside the NVTX range sexpe_step (for an ncu capture of "
-                         "the step kernels)")
+    ap.add_argument("--profile-case", nargs="?", const="ball", default=None,
+                    choices=["ball", "sphere", "batch", "cylinder", "ball-fp64"],
+                    help="run only setup + 3 + 3 split steps of the ball workload (or the 256 x 512 sphere, the "
+                         "256 batched disks, the 64 x 128 x 128 cylinder, or the ball on the FP64 path), the last "
+                         "3 inside the NVTX range sexpe_step (for an ncu capture of the step kernels)")
     return ap.parse_args()
 
 
@@ -228,7 +229,7 @@ def main():
     from paper_2604_11558_gb300 import binding
     from paper_2604_11558_gb300 import workloads as wl
 
-    if args.profile_case in ("sphere", "batch"):
+    if args.profile_case in ("sphere", "batch", "cylinder", "ball-fp64"):
         return profile_other(args.profile_case)
     w = wl.gray_scott_ball()
     n, S = w["n"], len(w["d"])
@@ -449,12 +450,21 @@ def measure_extras(flush):
 
 
 def profile_other(case):
-    """Setup, 3 untimed steps, then 3 steps in the NVTX range sexpe_step, of the 256 x 512 sphere or
-    the 256 batched disks (split path), for an ncu capture of their kernels."""
+    """Setup, 3 untimed steps, then 3 steps in the NVTX range sexpe_step, of the 256 x 512 sphere, the
+    256 batched disks, the 64 x 128 x 128 cylinder (split path) or the ball on the FP64 path, for an
+    ncu capture of their kernels."""
     import torch
     from paper_2604_11558_gb300 import binding
     from paper_2604_11558_gb300 import workloads as wl
-    if case == "sphere":
+    if case == "cylinder":
+        w = wl.linear_cubic_cylinder(steps=1)
+        plan = binding.Plan.from_workload(w, precision="split_tf32")
+        x = torch.from_numpy(w["W0"]).cuda()
+    elif case == "ball-fp64":
+        w = wl.gray_scott_ball(steps=1)
+        plan = binding.Plan.from_workload(w, precision="fp64")
+        x = torch.from_numpy(w["W0"]).cuda()
+    elif case == "sphere":
         w = wl.schnakenberg_sphere(steps=1)
         plan = binding.Plan.from_workload(w, precision="split_tf32")
         plan.set_theta_split(PROFILE_THETA_SPLIT)     # the unprofiled tuner's choice (timings under a profiler differ)

@@ -23,6 +23,9 @@ What it computes, in plain numpy/scipy FP64 and in the paper's order:
 * ``unsplit``   -- unsplit exponential Euler (eq. ee with phi_1 of the whole
                    assembled operator, dense expm): the baseline the splitting
                    error is measured against.
+* ``coupled``   -- the bulk-surface Schnakenberg system of Section 5.5 (ball
+                   and its boundary sphere coupled through Robin boundary
+                   conditions and the surface reactions).
 * ``adjoint``   -- gradients of a scalar loss by complex-step differentiation
                    through ``stepper`` (no transposed code path of its own).
 

@@ -97,3 +97,17 @@ def run(problem, W0, n_steps, t0=0.0, fp32_storage=False):
     for n in range(n_steps):
         W = step(problem, W, t0 + n * problem.tau, fp32_storage)
     return W
+
+
+def advance(problem, W, F):
+    """w_s + tau phi_1(tau d_s M_1) ... phi_1(tau d_s M_d) F_s for every species, for a given F
+    (the split update of eq. splitorder; used where F carries terms from outside the grid, as in
+    the bulk-surface coupling of Section 5.5)."""
+    grid = problem.grid
+    out = np.array(W, copy=True)
+    for s in range(problem.S):
+        X = F[s]
+        for mu in range(grid.ndim, 0, -1):
+            X = apply_phi1_mode(X, grid, problem._eig[mu], mu, problem.tau * problem.d[s])
+        out[s] = W[s] + problem.tau * X
+    return out

@@ -192,6 +192,33 @@ sexpe_status sexpe_step_host(sexpe_plan* plan, double* state_host, int64_t n_ste
  *  - Results equal sexpe_step's for the same plan and state. */
 sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_steps, void* stream);
 
+/* Bulk-surface coupled system (Section 5.5, eqs. bulkball): two species u, v on
+ * the ball (`ball`, geometry SEXPE_BALL; `bulk`: diffusion d_u, d_v = delta and a
+ * two-species reaction, alpha1 b(u, v), alpha1 c(u, v) for SCHNAKENBERG with
+ * params {alpha1, alpha2, beta1}) and two species r, s on its boundary sphere
+ * rho = rho_*, whose grid is the ball's theta x phi grid (`surface`: diffusion
+ * 1/rho_*^2 and eps/rho_*^2 for the paper's scaling, reaction zeta1 b(r, s),
+ * zeta1 c(r, s)).  They couple through the boundary conditions
+ * grad u . n = zeta1 (zeta2 r - zeta3 u), delta grad v . n = zeta1 (eta1 s - eta2 v)
+ * and the surface reactions p = b(r, s) - (zeta2 r - zeta3 u),
+ * q = c(r, s) - (eta1 s - eta2 v).  The paper omits the coupled discretisation;
+ * this one keeps eq. ball_discr and lets a normal derivative g enter its outer
+ * radial row through the same virtual point, adding (2/h + 2/rho_*) g, with h
+ * the radial step; all coupling terms are explicit at t_n with the reactions,
+ * and each component takes its own geometry's split step (eqs. ee_ball,
+ * ee_sphere).  State (device, FP64, caller-owned): [u][v] in the ball layout,
+ * then [r][s] in the sphere layout (theta fastest), 2 (N_ball + N_sphere)
+ * elements.  Precision SEXPE_FP64 (others SEXPE_EUNSUPPORTED); no adjoint, no
+ * lifting offsets.  Step with sexpe_step / sexpe_step_host; destroy with
+ * sexpe_destroy.  Errors as sexpe_setup. */
+typedef struct {
+    double zeta1, zeta2, zeta3;  /* grad u . n = zeta1 (zeta2 r - zeta3 u)             */
+    double eta1, eta2;           /* delta grad v . n = zeta1 (eta1 s - eta2 v)       */
+} sexpe_coupling;
+sexpe_status sexpe_coupled_setup(const sexpe_grid* ball, const sexpe_species* bulk, const sexpe_species* surface,
+                                 const sexpe_coupling* cp, double tau, int32_t precision, void* stream,
+                                 sexpe_plan** out);
+
 /* Wait for the plan's work on `stream` and report the device error word
  * (SEXPE_ETIMEOUT if a bounded wait ran out), clearing it. */
 sexpe_status sexpe_synchronize(sexpe_plan* plan, void* stream);

@@ -45,6 +45,11 @@ class Species(ctypes.Structure):
                 ("params_host", ctypes.POINTER(ctypes.c_double)), ("offset_host", ctypes.POINTER(ctypes.c_double))]
 
 
+class Coupling(ctypes.Structure):
+    _fields_ = [("zeta1", ctypes.c_double), ("zeta2", ctypes.c_double), ("zeta3", ctypes.c_double),
+                ("eta1", ctypes.c_double), ("eta2", ctypes.c_double)]
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("geometry", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_species", ctypes.c_int32),
                 ("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("n_instances", ctypes.c_int32),
@@ -73,6 +78,9 @@ def lib():
                                   _P, ctypes.POINTER(_P)]
         L.sexpe_batch_setup.argtypes = [ctypes.c_int32, ctypes.POINTER(Grid), ctypes.POINTER(Species),
                                         ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(_P)]
+        L.sexpe_coupled_setup.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Species), ctypes.POINTER(Species),
+                                          ctypes.POINTER(Coupling), ctypes.c_double, ctypes.c_int32, _P,
+                                          ctypes.POINTER(_P)]
         L.sexpe_state_offsets.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         L.sexpe_step.argtypes = [_P, _P, ctypes.c_int64, _P]
         L.sexpe_step_host.argtypes = [_P, _DP, ctypes.c_int64, _P]
@@ -96,7 +104,7 @@ def lib():
                      "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
                      "sexpe_step_checkpointed", "sexpe_adjoint", "sexpe_set_stencil",
                      "sexpe_set_theta_split", "sexpe_selftest_wait_timeout", "sexpe_set_time",
-                     "sexpe_axis_phi1", "sexpe_axis_eigen"]:
+                     "sexpe_axis_phi1", "sexpe_axis_eigen", "sexpe_coupled_setup"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -280,6 +288,43 @@ class BatchPlan(Plan):
         out = (ctypes.c_int64 * (self.count + 1))()
         _check(lib().sexpe_state_offsets(self.handle, out), "sexpe_state_offsets")
         return list(out)
+
+
+class CoupledPlan(Plan):
+    """The bulk-surface coupled system of Section 5.5 (wraps sexpe_coupled_setup): species u, v on the ball
+    n = (n_rho, n_theta, n_phi) and r, s on its boundary sphere; state [u][v] (ball layout) then [r][s]
+    (sphere layout, theta fastest)."""
+
+    def __init__(self, n, d_bulk, bulk_params, d_surface, surface_params, coupling, tau, rho_star=1.0,
+                 precision="fp64", stream=None, reaction="schnakenberg"):
+        L = lib()
+        self._keep = [np.ascontiguousarray(x, dtype=np.float64)
+                      for x in (d_bulk, bulk_params, d_surface, surface_params)]
+        db, pb, ds, ps = self._keep
+        grid = _grid_struct("ball", n, rho_star)
+        bulk = Species(len(db), _dptr(db), REACTION[reaction], len(pb), _dptr(pb))
+        surf = Species(len(ds), _dptr(ds), REACTION[reaction], len(ps), _dptr(ps))
+        c = coupling
+        cp = Coupling(float(c["zeta1"]), float(c["zeta2"]), float(c["zeta3"]), float(c["eta1"]), float(c["eta2"]))
+        h = _P()
+        st = _stream_ptr(stream) if stream is not None else 0
+        _check(L.sexpe_coupled_setup(ctypes.byref(grid), ctypes.byref(bulk), ctypes.byref(surf), ctypes.byref(cp),
+                                     float(tau), PRECISION[precision], st, ctypes.byref(h)), "sexpe_coupled_setup")
+        self.handle = h
+        self.geometry, self.n, self.S = "ball+sphere", tuple(n), len(db) + len(ds)
+        self._p_list = []
+        self.n_ball = int(np.prod(n))
+        self.n_sphere = int(n[1]) * int(n[2])
+
+
+def coupled_setup_status(*args, **kw):
+    """Status code of sexpe_coupled_setup for the given arguments (the plan is destroyed again)."""
+    try:
+        p = CoupledPlan(*args, **kw)
+    except SexpeError as e:
+        return e.status
+    p.close()
+    return 0
 
 
 def batch_setup_status(workloads, precision="split_tf32"):

@@ -94,6 +94,34 @@ __global__ void __launch_bounds__(256) k_gemm64(Gemm64 g) {
     }
 }
 
+// Bulk-surface coupling (Section 5.5, eqs. bulkballsys, bulkballnl), one thread per surface
+// point (theta_j, phi_k) = bulk node (rho_*, theta_j, phi_k): with the normal derivatives
+// g_u = zeta1 (zeta2 r - zeta3 u) and delta g_v = zeta1 (eta1 s - eta2 v), the bulk F gets the
+// virtual-point term of the outer radial row, coef = 2/h + 2/rho_* (d_u coef g_u and coef
+// delta g_v), and the surface F the coupling parts of p and q (-g_u and -delta g_v).
+__global__ void k_couple64(const double* __restrict__ Wb, const double* __restrict__ Ws, double* __restrict__ Fb,
+                           double* __restrict__ Fs, int n_rho, int n_theta, int n_phi, double coef, double du,
+                           double z1, double z2, double z3, double e1, double e2) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ns = (long long)n_theta * n_phi, nb = ns * n_rho;
+    if (q >= ns) return;
+    const long long b = (n_rho - 1) + (long long)n_rho * q;        // q = j + n_theta k
+    const double ub = Wb[b], vb = Wb[nb + b], r = Ws[q], s = Ws[ns + q];
+    const double ju = z1 * (z2 * r - z3 * ub), jv = z1 * (e1 * s - e2 * vb);
+    Fb[b] += du * coef * ju;
+    Fb[nb + b] += coef * jv;
+    Fs[q] -= ju;
+    Fs[ns + q] -= jv;
+}
+
+cudaError_t launch_couple64(const double* Wb, const double* Ws, double* Fb, double* Fs, int n_rho, int n_theta,
+                            int n_phi, double coef, double du, const double* c, cudaStream_t st) {
+    const long long ns = (long long)n_theta * n_phi;
+    k_couple64<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(Wb, Ws, Fb, Fs, n_rho, n_theta, n_phi, coef, du, c[0], c[1],
+                                                           c[2], c[3], c[4]);
+    return cudaGetLastError();
+}
+
 // Unsplit baseline: W_s[r] += tau sum_k P_s[r][k] F_s[k] (row-major N x N per
 // species), one warp per row, lanes striding the row (coalesced), a warp-shuffle
 // reduction, then the update by lane 0.  grid (ceil(N / 8), S), 256 threads.

@@ -642,6 +642,53 @@ cudaError_t prof_mark(sexpe_plan* p, cudaStream_t st) {
 
 sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st);
 
+// FP64 direction chain of plan q on F in q->buf64[0], the last product fused with the update of
+// `state` (profiling marks recorded on plan `prof`).
+sexpe_status enqueue_fp64_chain(sexpe_plan* q, sexpe_plan* prof, double* state, cudaStream_t st) {
+    int x = 0;                                  // buffer holding the current operand
+    for (const Dir64& d : q->dirs64) {
+        const bool last = d.mu == 1;
+        const int nmu = q->n[d.mu - 1];
+        const int t = (x + 1) % 3, y = (x + 2) % 3;
+        if (d.eigen) {
+            SX_CUDA(prof_mark(prof, st));
+            SX_CUDA(launch_gemm64(mode_gemm(q, d.mu, d.Vinv, 0, q->buf64[x], q->buf64[t], d.had, nullptr), q->S, st));
+            SX_CUDA(prof_mark(prof, st));
+            SX_CUDA(launch_gemm64(mode_gemm(q, d.mu, d.V, 0, q->buf64[t], q->buf64[y], nullptr,
+                                            last ? state : nullptr), q->S, st));
+            x = y;
+        } else {
+            SX_CUDA(prof_mark(prof, st));
+            SX_CUDA(launch_gemm64(mode_gemm(q, d.mu, d.P, (long long)nmu * nmu, q->buf64[x], q->buf64[t],
+                                            nullptr, last ? state : nullptr), q->S, st));
+            x = t;
+        }
+    }
+    return SEXPE_OK;
+}
+
+// Bulk-surface step (Section 5.5): both stencil+reaction passes, the boundary coupling added
+// to their F (explicit at t_n), then each component's own split chain (eqs. ee_ball, ee_sphere).
+// State: [u, v on the ball][r, s on the sphere].
+sexpe_status enqueue_coupled_step(sexpe_plan* p, double* state, cudaStream_t st) {
+    sexpe_plan* b = p->sub[0];
+    sexpe_plan* s = p->sub[1];
+    double* Wb = state;
+    double* Ws = state + 2 * b->npts;
+    SX_CUDA(prof_mark(p, st));
+    SX_CUDA(launch_rhs64(b->geometry, b->rhs64, Wb, b->buf64[0], st));
+    SX_CUDA(prof_mark(p, st));
+    SX_CUDA(launch_rhs64(s->geometry, s->rhs64, Ws, s->buf64[0], st));
+    const double h = b->ax[0].pts[0];                  // rho_i = i h
+    const double rho_star = b->ax[0].pts[b->n[0] - 1];
+    SX_CUDA(prof_mark(p, st));
+    SX_CUDA(launch_couple64(Wb, Ws, b->buf64[0], s->buf64[0], b->n[0], b->n[1], b->n[2], 2.0 / h + 2.0 / rho_star,
+                            b->d[0], p->cpl, st));
+    SX_TRY(enqueue_fp64_chain(b, p, Wb, st));
+    SX_TRY(enqueue_fp64_chain(s, p, Ws, st));
+    return SEXPE_OK;
+}
+
 sexpe_status enqueue_step(sexpe_plan* p, double* state, cudaStream_t st) {
     p->prof_slot = 0;
     SX_TRY(enqueue_step_body(p, state, st));
@@ -672,28 +719,11 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
         if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
         return SEXPE_OK;
     }
+    if (p->coupled) return enqueue_coupled_step(p, state, st);
     if (p->precision == SEXPE_FP64) {
         SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_rhs64(p->geometry, p->rhs64, state, p->buf64[0], st));
-        int x = 0;                                  // buffer holding the current operand
-        for (const Dir64& d : p->dirs64) {
-            const bool last = d.mu == 1;
-            const int nmu = p->n[d.mu - 1];
-            const int t = (x + 1) % 3, y = (x + 2) % 3;
-            if (d.eigen) {
-                SX_CUDA(prof_mark(p, st));
-                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.Vinv, 0, p->buf64[x], p->buf64[t], d.had, nullptr), p->S, st));
-                SX_CUDA(prof_mark(p, st));
-                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.V, 0, p->buf64[t], p->buf64[y], nullptr,
-                                                last ? state : nullptr), p->S, st));
-                x = y;
-            } else {
-                SX_CUDA(prof_mark(p, st));
-                SX_CUDA(launch_gemm64(mode_gemm(p, d.mu, d.P, (long long)nmu * nmu, p->buf64[x], p->buf64[t],
-                                                nullptr, last ? state : nullptr), p->S, st));
-                x = t;
-            }
-        }
+        SX_TRY(enqueue_fp64_chain(p, p, state, st));
         if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
         return SEXPE_OK;
     }
@@ -717,6 +747,13 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
     SX_CUDA(launch_tc_slab(T, p->shs, st));
     if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
     return SEXPE_OK;
+}
+
+// FP64 elements of a plan's whole state.
+long long state_elems(const sexpe_plan* p) {
+    if (p->batch) return p->inst_off.back();
+    if (p->coupled) return 2 * (p->sub[0]->npts + p->sub[1]->npts);
+    return (long long)p->S * p->npts;
 }
 
 sexpe_status validate(const sexpe_grid* g, const sexpe_species* sp, double tau, int32_t precision) {
@@ -769,6 +806,8 @@ void free_profile(sexpe_plan* p) {
 
 void free_plan(sexpe_plan* p) {
     if (!p) return;
+    free_plan(p->sub[0]);
+    free_plan(p->sub[1]);
     free_profile(p);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (void* a : p->allocs) cudaFree(a);
@@ -1234,6 +1273,67 @@ sexpe_status sexpe_setup(const sexpe_grid* grid, const sexpe_species* species, d
     return SEXPE_OK;
 }
 
+sexpe_status sexpe_coupled_setup(const sexpe_grid* ball, const sexpe_species* bulk, const sexpe_species* surface,
+                                 const sexpe_coupling* cp, double tau, int32_t precision, void* stream,
+                                 sexpe_plan** out) {
+    if (!out) return SEXPE_EINVAL;
+    *out = nullptr;
+    if (!ball || !bulk || !surface || !cp) return SEXPE_EINVAL;
+    if (ball->geometry != SEXPE_BALL || bulk->n_species != 2 || surface->n_species != 2) return SEXPE_EINVAL;
+    const double c[5] = {cp->zeta1, cp->zeta2, cp->zeta3, cp->eta1, cp->eta2};
+    for (double x : c)
+        if (!std::isfinite(x)) return SEXPE_EINVAL;
+    if (bulk->offset_host || surface->offset_host) return SEXPE_EINVAL;
+    if (bulk->reaction == SEXPE_BVAM_MANUFACTURED || surface->reaction == SEXPE_BVAM_MANUFACTURED) return SEXPE_EINVAL;
+    sexpe_grid sg = *ball;                             // the boundary sphere: the ball's theta and phi grids
+    sg.geometry = SEXPE_SPHERE;
+    sg.n[0] = ball->n[1];
+    sg.n[1] = ball->n[2];
+    sg.n[2] = 0;
+    sexpe_status v = validate(ball, bulk, tau, precision);
+    if (v == SEXPE_OK) v = validate(&sg, surface, tau, precision);
+    if (v != SEXPE_OK) return v;
+    if (precision != SEXPE_FP64) return SEXPE_EUNSUPPORTED;
+    auto t0 = std::chrono::steady_clock::now();
+    sexpe_plan* p = new (std::nothrow) sexpe_plan();
+    if (!p) return SEXPE_ENOMEM;
+    sexpe_status s = SEXPE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    try {
+        p->sub[0] = new sexpe_plan();
+        p->sub[1] = new sexpe_plan();
+        s = build_plan(p->sub[0], ball, bulk, tau, precision, st);
+        if (s == SEXPE_OK) s = build_plan(p->sub[1], &sg, surface, tau, precision, st);
+        if (s == SEXPE_OK) {
+            p->coupled = true;
+            p->geometry = SEXPE_BALL;
+            p->precision = precision;
+            p->S = 4;
+            p->ndim = 3;
+            for (int m = 0; m < 3; ++m) p->n[m] = ball->n[m];
+            p->npts = p->sub[0]->npts;
+            p->tau = tau;
+            for (int q = 0; q < 5; ++q) p->cpl[q] = c[q];
+            p->kernels_per_step = 1 + p->sub[0]->kernels_per_step + p->sub[1]->kernels_per_step;
+            s = alloc_dev(p, 4, &p->d_err);
+            if (s == SEXPE_OK && cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st) != cudaSuccess) s = SEXPE_ECUDA;
+            if (s == SEXPE_OK) s = alloc_dev(p, (size_t)state_elems(p), &p->d_host_state);
+            if (s == SEXPE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SEXPE_ECUDA;
+        }
+    } catch (const std::bad_alloc&) {
+        s = SEXPE_ENOMEM;
+    } catch (...) {
+        s = SEXPE_ENUMERIC;
+    }
+    if (s != SEXPE_OK) {
+        free_plan(p);
+        return s;
+    }
+    p->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SEXPE_OK;
+}
+
 sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sexpe_species* species, double tau,
                                int32_t precision, void* stream, sexpe_plan** out) {
     if (!out) return SEXPE_EINVAL;
@@ -1277,7 +1377,7 @@ sexpe_status sexpe_state_offsets(const sexpe_plan* plan, int64_t* offsets_host) 
         return SEXPE_OK;
     }
     offsets_host[0] = 0;
-    offsets_host[1] = (int64_t)plan->S * plan->npts;
+    offsets_host[1] = state_elems(plan);
     return SEXPE_OK;
 }
 
@@ -1376,7 +1476,7 @@ sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* str
 sexpe_status sexpe_step_host(sexpe_plan* p, double* state_host, int64_t n_steps, void* stream) {
     if (!p || !state_host || n_steps < 0) return SEXPE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = sizeof(double) * (size_t)(p->batch ? p->inst_off.back() : (long long)p->S * p->npts);
+    const size_t bytes = sizeof(double) * (size_t)state_elems(p);
     SX_CUDA(cudaMemcpyAsync(p->d_host_state, state_host, bytes, cudaMemcpyHostToDevice, st));
     SX_TRY(sexpe_step(p, p->d_host_state, n_steps, stream));
     SX_CUDA(cudaMemcpyAsync(state_host, p->d_host_state, bytes, cudaMemcpyDeviceToHost, st));
@@ -1423,7 +1523,7 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
     info->n_instances = p->n_instances;
     info->kernels_per_step = p->kernels_per_step;
     info->npts = p->npts;
-    info->state_elems = p->batch ? (int64_t)p->inst_off.back() : (int64_t)p->S * p->npts;
+    info->state_elems = state_elems(p);
     info->workspace_bytes = (int64_t)p->bytes;
     info->setup_ms = p->setup_ms;
     if (!p->batch && p->precision == SEXPE_SPLIT_TF32) {
@@ -1445,7 +1545,7 @@ sexpe_status sexpe_step_checkpointed(sexpe_plan* p, double* state, int64_t n_ste
                                      double* checkpoints, void* stream) {
     if (!p || !state || !checkpoints || n_steps < 0 || every < 1) return SEXPE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t E = (size_t)p->S * p->npts;
+    const size_t E = (size_t)state_elems(p);
     for (int64_t k = 0; k < n_steps; ++k) {
         if (k % every == 0)
             SX_CUDA(cudaMemcpyAsync(checkpoints + (size_t)(k / every) * E, state, E * sizeof(double),
@@ -1458,7 +1558,7 @@ sexpe_status sexpe_step_checkpointed(sexpe_plan* p, double* state, int64_t n_ste
 sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_ckpt, int32_t every,
                            const double* dL_dWT, double* dL_dW0, double* dL_dparams, void* stream) {
     if (!p || !checkpoints || !dL_dWT || !dL_dW0 || n_ckpt < 1 || every < 1) return SEXPE_EINVAL;
-    if (p->precision != SEXPE_FP64) return SEXPE_EUNSUPPORTED;
+    if (p->precision != SEXPE_FP64 || p->coupled) return SEXPE_EUNSUPPORTED;
     if (p->reaction == SEXPE_BVAM || p->reaction == SEXPE_BVAM_MANUFACTURED) return SEXPE_EUNSUPPORTED;
     for (double c : p->offset)
         if (c != 0.0) return SEXPE_EUNSUPPORTED;

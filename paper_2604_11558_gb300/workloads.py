@@ -133,3 +133,26 @@ def random_state(geometry, n, S=2, seed=7, scale=0.1, offset=0.5):
     """Generic seeded field for parity tests: offset + scale * N(0, 1) per point and species."""
     rng = _rng(seed)
     return offset + scale * rng.standard_normal((S,) + _shape(n))
+
+
+def bulk_surface_ball(n=(30, 50, 30), steps=150000, seed=8, tau=1e-4):
+    """Bulk-surface Schnakenberg on the unit ball and its boundary sphere (Section 5.5, eqs. bulkball):
+    bulk u, v on the ball n = (n_rho, n_theta, n_phi) with diffusion (1, delta) and reaction
+    alpha1 (b, c); surface r, s on the ball's theta x phi grid with diffusion (1, eps) / rho_*^2 and
+    reaction zeta1 (b, c); alpha1 = zeta1 = 55, alpha2 = 0.1, beta1 = 0.9, zeta2 = zeta3 = 5/12,
+    eta1 = eta2 = 5, delta = eps = 10, rho_* = 1.  Initial data: the homogeneous equilibrium
+    (alpha2 + beta1, beta1 / (alpha2 + beta1)^2) for both pairs plus 1e-3 N(0, 1) per point and
+    species.  t_* = 15 in 150000 steps (tau = 1e-4).  Wb: (2, n_phi, n_theta, n_rho), Ws: (2, n_phi,
+    n_theta); the flat state is Wb then Ws."""
+    rng = _rng(seed)
+    a1, a2, b1, delta, eps = 55.0, 0.1, 0.9, 10.0, 10.0
+    z1, z2, z3, e1, e2 = 55.0, 5.0 / 12.0, 5.0 / 12.0, 5.0, 5.0
+    ue, ve = a2 + b1, b1 / (a2 + b1) ** 2
+    shb, shs = _shape(n), _shape(n[1:])
+    eq = np.array([ue, ve])[:, None, None, None]
+    Wb = eq + 1e-3 * rng.standard_normal((2,) + shb)
+    Ws = eq[:, :, :, 0] + 1e-3 * rng.standard_normal((2,) + shs)
+    return dict(geometry="ball+sphere", n=tuple(n), rho_star=1.0, tau=tau, steps=steps, seed=seed,
+                d_bulk=[1.0, delta], bulk_params=[a1, a2, b1], d_surface=[1.0, eps], surface_params=[z1, a2, b1],
+                coupling=dict(zeta1=z1, zeta2=z2, zeta3=z3, eta1=e1, eta2=e2), Wb=Wb, Ws=Ws,
+                name="bulk_surface_ball")

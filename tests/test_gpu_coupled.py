@@ -115,14 +115,17 @@ def test_coupled_step_host_equals_device():
 
 
 def test_coupled_equilibrium_stays_fixed():
-    """The homogeneous equilibrium is a fixed point of the coupled step (up to rounding)."""
+    """The homogeneous equilibrium is a fixed point of the coupled step up to rounding.  With
+    zeta2 = zeta3 and eta1 = eta2 the coupling terms vanish exactly there; what remains is the FP64
+    rounding of the operators' row sums (ball entries up to ~1e4 near the axis on this grid, times
+    tau, over 10 steps), of order 1e-12."""
     w = case((8, 10, 12), 10, 1e-3, 66)
     ue, ve = 0.1 + 0.9, 0.9 / (0.1 + 0.9) ** 2
     w["Wb"] = np.stack([np.full_like(w["Wb"][0], ue), np.full_like(w["Wb"][1], ve)])
     w["Ws"] = np.stack([np.full_like(w["Ws"][0], ue), np.full_like(w["Ws"][1], ve)])
     got = gpu_coupled(w, 10)
-    assert np.max(np.abs(got[0] - w["Wb"])) < 1e-12
-    assert np.max(np.abs(got[1] - w["Ws"])) < 1e-12
+    assert np.max(np.abs(got[0] - w["Wb"])) < 1e-10
+    assert np.max(np.abs(got[1] - w["Ws"])) < 1e-10
 
 
 def test_coupled_setup_errors():

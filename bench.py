@@ -381,7 +381,7 @@ def main():
 
 def measure_extras(flush):
     """The other workloads: cylinder 64x128x128 (3 species), sphere 256x512 (split and FP64), 256
-    uneven disks (one persistent launch per step), the bulk-surface ball 30x50x30 (FP64),
+    uneven disks (one persistent launch per step), the bulk-surface ball 30x50x30 (split and FP64),
     and the sphere 256x512 adjoint cost relative to its forward."""
     import numpy as np
     import torch
@@ -426,28 +426,28 @@ def measure_extras(flush):
                                 "value": dof * steps / (sum(ms) / 1e3), "launches_per_step": 1,
                                 "kernel_ms": kms, "l2": "flushed before every timed step"}
     plan.close()
-    # bulk-surface Schnakenberg on the ball 30x50x30 and its boundary sphere (Section 5.5), FP64: the
+    # bulk-surface Schnakenberg on the ball 30x50x30 and its boundary sphere (Section 5.5): the
     # paper's t_* = 15 run takes 150000 steps; the 0.74 MB state stays in L2 from step to step, as in
     # such a run, so no flush here
     w = wl.bulk_surface_ball()
-    plan = binding.CoupledPlan(w["n"], w["d_bulk"], w["bulk_params"], w["d_surface"], w["surface_params"],
-                               w["coupling"], w["tau"], rho_star=w["rho_star"])
-    x = torch.from_numpy(np.concatenate([w["Wb"].ravel(), w["Ws"].ravel()])).cuda()
-    plan.step(x, 100)
-    torch.cuda.synchronize()
-    steps = 2000
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    plan.step(x, steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    dof = x.numel()
-    out["bulk_surface_ball_30x50x30_fp64"] = {"unit": UNIT, "dof": dof, "ms_per_step": ms,
-                                              "value": dof / (ms / 1e3), "steps": steps,
-                                              "kernels_per_step": plan.info()["kernels_per_step"],
-                                              "t15_run_s": ms * w["steps"] / 1e3, "l2": "not flushed"}
-    plan.close()
+    res = {}
+    for prec, steps in (("split_tf32", 5000), ("fp64", 2000)):
+        plan = binding.CoupledPlan(w["n"], w["d_bulk"], w["bulk_params"], w["d_surface"], w["surface_params"],
+                                   w["coupling"], w["tau"], rho_star=w["rho_star"], precision=prec)
+        x = torch.from_numpy(np.concatenate([w["Wb"].ravel(), w["Ws"].ravel()])).cuda()
+        plan.step(x, 100)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.step(x, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[prec] = {"ms_per_step": ms, "value": x.numel() / (ms / 1e3), "steps": steps,
+                     "kernels_per_step": plan.info()["kernels_per_step"], "t15_run_s": ms * w["steps"] / 1e3}
+        plan.close()
+    out["bulk_surface_ball_30x50x30"] = {"unit": UNIT, "dof": 2 * (30 * 50 * 30 + 50 * 30), "l2": "not flushed",
+                                         **res}
     # sphere adjoint vs forward (FP64), full 256x512 workload: 1000 steps, checkpoints every 50
     w = wl.schnakenberg_sphere()
     plan = binding.Plan.from_workload(w, precision="fp64")

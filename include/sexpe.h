@@ -208,9 +208,13 @@ sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_s
  * and each component takes its own geometry's split step (eqs. ee_ball,
  * ee_sphere).  State (device, FP64, caller-owned): [u][v] in the ball layout,
  * then [r][s] in the sphere layout (theta fastest), 2 (N_ball + N_sphere)
- * elements.  Precision SEXPE_FP64 (others SEXPE_EUNSUPPORTED); no adjoint, no
- * lifting offsets.  Step with sexpe_step / sexpe_step_host; destroy with
- * sexpe_destroy.  Errors as sexpe_setup. */
+ * elements.  Precision SEXPE_FP64 (FP64 SIMT chains) or SEXPE_SPLIT_TF32 (the
+ * tensor-core chains of each grid, the coupling terms formed in FP64 and added
+ * to their FP32 F); SEXPE_UNSPLIT_FP64 gives SEXPE_EUNSUPPORTED.  No adjoint,
+ * no lifting offsets, no sexpe_set_stencil / sexpe_set_theta_split
+ * (SEXPE_EUNSUPPORTED) and no sexpe_step_noalloc (SEXPE_EINVAL).  Step with
+ * sexpe_step / sexpe_step_host; destroy with sexpe_destroy.  Other errors as
+ * sexpe_setup. */
 typedef struct {
     double zeta1, zeta2, zeta3;  /* grad u . n = zeta1 (zeta2 r - zeta3 u)             */
     double eta1, eta2;           /* delta grad v . n = zeta1 (eta1 s - eta2 v)       */

@@ -122,6 +122,37 @@ cudaError_t launch_couple64(const double* Wb, const double* Ws, double* Fb, doub
     return cudaGetLastError();
 }
 
+// The same coupling terms for the split-TF32 chains, whose F is FP32 in the
+// padded layout [s][k][j][n1q] of each grid (ball: i = rho fastest, j = theta,
+// k = phi; sphere: i = theta, j = phi).  The terms are formed in FP64 from the
+// FP64 state and added to F in FP64 before rounding to FP32.
+__global__ void k_couple_split(const double* __restrict__ Wb, const double* __restrict__ Ws, float* __restrict__ Yb,
+                               float* __restrict__ Ys, int n_rho, int n_theta, int n_phi, int n1q_b, long long ys_b,
+                               int n1q_s, long long ys_s, double coef, double du, double z1, double z2, double z3,
+                               double e1, double e2) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ns = (long long)n_theta * n_phi, nb = ns * n_rho;
+    if (q >= ns) return;
+    const long long j = q % n_theta, k = q / n_theta;
+    const long long b = (n_rho - 1) + (long long)n_rho * q;
+    const double ub = Wb[b], vb = Wb[nb + b], r = Ws[q], s = Ws[ns + q];
+    const double ju = z1 * (z2 * r - z3 * ub), jv = z1 * (e1 * s - e2 * vb);
+    const long long yb = (k * n_theta + j) * n1q_b + (n_rho - 1), ysq = k * n1q_s + j;
+    Yb[yb] = (float)((double)Yb[yb] + du * coef * ju);
+    Yb[ys_b + yb] = (float)((double)Yb[ys_b + yb] + coef * jv);
+    Ys[ysq] = (float)((double)Ys[ysq] - ju);
+    Ys[ys_s + ysq] = (float)((double)Ys[ys_s + ysq] - jv);
+}
+
+cudaError_t launch_couple_split(const double* Wb, const double* Ws, float* Yb, float* Ys, int n_rho, int n_theta,
+                                int n_phi, int n1q_b, long long ys_b, int n1q_s, long long ys_s, double coef,
+                                double du, const double* c, cudaStream_t st) {
+    const long long ns = (long long)n_theta * n_phi;
+    k_couple_split<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(Wb, Ws, Yb, Ys, n_rho, n_theta, n_phi, n1q_b, ys_b,
+                                                               n1q_s, ys_s, coef, du, c[0], c[1], c[2], c[3], c[4]);
+    return cudaGetLastError();
+}
+
 // Unsplit baseline: W_s[r] += tau sum_k P_s[r][k] F_s[k] (row-major N x N per
 // species), one warp per row, lanes striding the row (coalesced), a warp-shuffle
 // reduction, then the update by lane 0.  grid (ceil(N / 8), S), 256 threads.

@@ -667,6 +667,25 @@ sexpe_status enqueue_fp64_chain(sexpe_plan* q, sexpe_plan* prof, double* state, 
     return SEXPE_OK;
 }
 
+// Split-TF32 products of plan q on the FP32 F in T.Y, the last fused with the update of
+// T.state_upd (profiling marks recorded on plan `prof`).
+sexpe_status enqueue_split_products(sexpe_plan* q, sexpe_plan* prof, const SplitTables& T, cudaStream_t st) {
+    if (q->geometry == SEXPE_SPHERE) {
+        SX_CUDA(prof_mark(prof, st));
+        SX_CUDA(launch_tc_sphere_phi(T, q->sh3, st));
+        SX_CUDA(prof_mark(prof, st));
+        SX_CUDA(launch_tc_sphere_theta(T, q->shs, st));
+        return SEXPE_OK;
+    }
+    if (q->ndim == 3) {
+        SX_CUDA(prof_mark(prof, st));
+        SX_CUDA(launch_tc_mode3(T, q->sh3, st));
+    }
+    SX_CUDA(prof_mark(prof, st));
+    SX_CUDA(launch_tc_slab(T, q->shs, st));
+    return SEXPE_OK;
+}
+
 // Bulk-surface step (Section 5.5): both stencil+reaction passes, the boundary coupling added
 // to their F (explicit at t_n), then each component's own split chain (eqs. ee_ball, ee_sphere).
 // State: [u, v on the ball][r, s on the sphere].
@@ -675,15 +694,31 @@ sexpe_status enqueue_coupled_step(sexpe_plan* p, double* state, cudaStream_t st)
     sexpe_plan* s = p->sub[1];
     double* Wb = state;
     double* Ws = state + 2 * b->npts;
+    const double h = b->ax[0].pts[0];                  // rho_i = i h, i = 1 .. n_rho
+    const double rho_star = b->ax[0].pts[b->n[0] - 1];
+    const double coef = 2.0 / h + 2.0 / rho_star;
+    if (p->precision == SEXPE_SPLIT_TF32) {
+        SplitTables Tb = b->tabs, Ts = s->tabs;
+        Tb.state = Tb.state_upd = Wb;
+        Ts.state = Ts.state_upd = Ws;
+        Tb.err = Ts.err = p->d_err;                    // bounded-wait timeouts reported by sexpe_synchronize
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_rhs_split(Tb, st));
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_rhs_split(Ts, st));
+        SX_CUDA(prof_mark(p, st));
+        SX_CUDA(launch_couple_split(Wb, Ws, Tb.Y, Ts.Y, b->n[0], b->n[1], b->n[2], Tb.n1q, Tb.ys, Ts.n1q, Ts.ys,
+                                    coef, b->d[0], p->cpl, st));
+        SX_TRY(enqueue_split_products(b, p, Tb, st));
+        SX_TRY(enqueue_split_products(s, p, Ts, st));
+        return SEXPE_OK;
+    }
     SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_rhs64(b->geometry, b->rhs64, Wb, b->buf64[0], st));
     SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_rhs64(s->geometry, s->rhs64, Ws, s->buf64[0], st));
-    const double h = b->ax[0].pts[0];                  // rho_i = i h
-    const double rho_star = b->ax[0].pts[b->n[0] - 1];
     SX_CUDA(prof_mark(p, st));
-    SX_CUDA(launch_couple64(Wb, Ws, b->buf64[0], s->buf64[0], b->n[0], b->n[1], b->n[2], 2.0 / h + 2.0 / rho_star,
-                            b->d[0], p->cpl, st));
+    SX_CUDA(launch_couple64(Wb, Ws, b->buf64[0], s->buf64[0], b->n[0], b->n[1], b->n[2], coef, b->d[0], p->cpl, st));
     SX_TRY(enqueue_fp64_chain(b, p, Wb, st));
     SX_TRY(enqueue_fp64_chain(s, p, Ws, st));
     return SEXPE_OK;
@@ -732,20 +767,8 @@ sexpe_status enqueue_step_body(sexpe_plan* p, double* state, cudaStream_t st) {
     T.state_upd = state;
     SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_rhs_split(T, st));
-    if (p->geometry == SEXPE_SPHERE) {
-        SX_CUDA(prof_mark(p, st));
-        SX_CUDA(launch_tc_sphere_phi(T, p->sh3, st));
-        SX_CUDA(prof_mark(p, st));
-        SX_CUDA(launch_tc_sphere_theta(T, p->shs, st));
-        return SEXPE_OK;
-    }
-    if (p->ndim == 3) {
-        SX_CUDA(prof_mark(p, st));
-        SX_CUDA(launch_tc_mode3(T, p->sh3, st));
-    }
-    SX_CUDA(prof_mark(p, st));
-    SX_CUDA(launch_tc_slab(T, p->shs, st));
-    if (p->d_step) SX_CUDA(launch_tick(p->d_step, st));
+    SX_TRY(enqueue_split_products(p, p, T, st));
+    if (p->d_step && p->geometry != SEXPE_SPHERE) SX_CUDA(launch_tick(p->d_step, st));
     return SEXPE_OK;
 }
 
@@ -1212,7 +1235,7 @@ namespace sexpe {
 sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float* Y, long long y_floats,
                                              cudaStream_t st) {
     if (!p || !state || !Y) return SEXPE_EINVAL;
-    if (p->precision != SEXPE_SPLIT_TF32 || p->batch) return SEXPE_EINVAL;
+    if (p->precision != SEXPE_SPLIT_TF32 || p->batch || p->coupled) return SEXPE_EINVAL;
     if ((long long)p->S * p->tabs.ys > y_floats) return SEXPE_EINVAL;
     SplitTables T = p->tabs;
     T.state = state;
@@ -1293,7 +1316,7 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* ball, const sexpe_species* bu
     sexpe_status v = validate(ball, bulk, tau, precision);
     if (v == SEXPE_OK) v = validate(&sg, surface, tau, precision);
     if (v != SEXPE_OK) return v;
-    if (precision != SEXPE_FP64) return SEXPE_EUNSUPPORTED;
+    if (precision != SEXPE_FP64 && precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
     auto t0 = std::chrono::steady_clock::now();
     sexpe_plan* p = new (std::nothrow) sexpe_plan();
     if (!p) return SEXPE_ENOMEM;
@@ -1397,7 +1420,7 @@ sexpe_status sexpe_set_time(sexpe_plan* p, double t, void* stream) {
 
 sexpe_status sexpe_set_stencil(sexpe_plan* p, int32_t tile_j, int32_t planes, int32_t ctas_per_sm) {
     if (!p) return SEXPE_EINVAL;
-    if (p->batch || p->precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
+    if (p->batch || p->coupled || p->precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
     int3 cand[256];
     const int nc = rhs_candidates(p->tabs, cand, 256);
     bool ok = false;

@@ -5,7 +5,10 @@ Species u, v on the ball and r, s on its boundary sphere, coupled through the fl
 conditions (entering the ball's outer radial row through the virtual point of eq. ball_discr) and
 the surface reactions, explicit at t_n; each component then takes its own split step (eqs. ee_ball,
 ee_sphere).  FP64 on both sides: the state within 1e-12 relative, and the increment W_n - W_0
-(of size ~tau |F|, far below the state near the equilibrium) within 1e-9 relative.
+(of size ~tau |F|, far below the state near the equilibrium) within 1e-9 relative.  Split-TF32
+chains (FP32 F, TF32 hi/lo products): the state within 1e-6 relative; the increment within 1e-5
+over a few steps and 1e-4 over 200, on data 5e-2 away from the equilibrium (nearer to it the FP32
+reaction, alpha1 b(u, v) with |b| ~ 1e-3 formed from O(1) terms, loses digits to cancellation).
 """
 import numpy as np
 import pytest
@@ -33,9 +36,9 @@ def split_state(x, n):
     return x[:2 * nb].reshape((2,) + tuple(reversed(n))), x[2 * nb:2 * nb + 2 * ns].reshape((2, n[2], n[1]))
 
 
-def gpu_coupled(w, steps, single_calls=False):
+def gpu_coupled(w, steps, single_calls=False, precision="fp64"):
     import torch
-    plan = plan_for(w)
+    plan = plan_for(w, precision)
     x = torch.from_numpy(flat(w["Wb"], w["Ws"])).cuda()
     info = plan.info()
     assert info["state_elems"] == x.numel()
@@ -61,13 +64,17 @@ def oracle_coupled(w, steps):
 
 
 def check(got, ref, W0, tol_state=1e-12, tol_incr=1e-9):
+    errs = []
     for g, r, w0 in zip(got, ref, W0):
         assert np.all(np.isfinite(g))
         for s in range(2):
             err = np.max(np.abs(g[s] - r[s])) / np.max(np.abs(r[s]))
-            assert err <= tol_state, (s, err)
             inc = np.linalg.norm((g[s] - w0[s]) - (r[s] - w0[s])) / max(np.linalg.norm(r[s] - w0[s]), 1e-300)
-            assert inc <= tol_incr, (s, inc)
+            errs.append((float(err), float(inc)))
+    print("state / increment errors (u, v, r, s):", errs)
+    for err, inc in errs:
+        assert err <= tol_state, errs
+        assert inc <= tol_incr, errs
 
 
 def case(n, steps, tau, seed, rho_star=1.0, noise=1e-3):
@@ -94,10 +101,26 @@ def test_coupled_matches_oracle(name, w):
     check(got, ref, (w["Wb"], w["Ws"]))
 
 
-def test_coupled_single_calls_equal_one_call():
-    w = case((7, 10, 9), 6, 1e-3, 64, noise=2e-2)
-    a = gpu_coupled(w, 6)
-    b = gpu_coupled(w, 6, single_calls=True)
+SPLIT_CASES = [
+    ("small", case((5, 6, 7), 4, 1e-3, 71, noise=5e-2), 1e-5),
+    ("rho_star_0p7", case((9, 8, 6), 5, 1e-3, 72, rho_star=0.7, noise=5e-2), 1e-5),
+    ("ragged_tiles", case((33, 40, 37), 3, 2e-4, 73, noise=5e-2), 1e-5),
+    ("paper_30x50x30", case((30, 50, 30), 200, 1e-4, 74, noise=5e-2), 1e-4),
+]
+
+
+@pytest.mark.parametrize("name,w,tol_incr", SPLIT_CASES, ids=[c[0] for c in SPLIT_CASES])
+def test_coupled_split_tf32_matches_oracle(name, w, tol_incr):
+    got = gpu_coupled(w, w["steps"], precision="split_tf32")
+    ref = oracle_coupled(w, w["steps"])
+    check(got, ref, (w["Wb"], w["Ws"]), tol_state=1e-6, tol_incr=tol_incr)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_tf32"])
+def test_coupled_single_calls_equal_one_call(precision):
+    w = case((7, 10, 9), 12, 1e-3, 64, noise=2e-2)       # one call: a 10-step graph, then 2 steps
+    a = gpu_coupled(w, 12, precision=precision)
+    b = gpu_coupled(w, 12, single_calls=True, precision=precision)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
 
@@ -135,11 +158,19 @@ def test_coupled_setup_errors():
                 surface_params=w["surface_params"], coupling=w["coupling"], tau=w["tau"])
     st = binding.coupled_setup_status
     assert st(**base) == 0
-    assert st(**dict(base, precision="split_tf32")) == 5         # SEXPE_EUNSUPPORTED
+    assert st(**dict(base, precision="split_tf32")) == 0
+    assert st(**dict(base, precision="unsplit_fp64")) == 5       # SEXPE_EUNSUPPORTED
     assert st(**dict(base, d_bulk=[1.0, 10.0, 3.0])) == 1        # SEXPE_EINVAL: three bulk species
     assert st(**dict(base, coupling=dict(w["coupling"], zeta2=float("nan")))) == 1
     assert st(**dict(base, tau=-1.0)) == 1
     assert st(**dict(base, n=(2, 6, 7))) == 1
+    plan = plan_for(w, "split_tf32")
+    with pytest.raises(RuntimeError):                            # the stencil belongs to the sub-grids
+        plan.set_stencil(4, 0)
+    import torch
+    with pytest.raises(RuntimeError):                            # no static-scratch variant
+        plan.step_noalloc(torch.zeros(plan.info()["state_elems"], dtype=torch.float64, device="cuda"), 1)
+    plan.close()
     plan = plan_for(w)
     with pytest.raises(RuntimeError):                            # no adjoint for the coupled system
         import torch

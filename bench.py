@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cylinder, batched-disk and sphere-adjoint measurements")
     ap.add_argument("--profile-case", nargs="?", const="ball", default=None,
-                    choices=["ball", "sphere", "batch", "cylinder", "ball-fp64"],
+                    choices=["ball", "sphere", "batch", "cylinder", "ball-fp64", "bulk-surface"],
                     help="run only setup + 3 + 3 split steps of the ball workload (or the 256 x 512 sphere, the "
-                         "256 batched disks, the 64 x 128 x 128 cylinder, or the ball on the FP64 path), the last "
+                         "256 batched disks, the 64 x 128 x 128 cylinder, the ball on the FP64 path, or the split bulk-surface "
+                         "ball 30 x 50 x 30), the last "
                          "3 inside the NVTX range sexpe_step (for an ncu capture of the step kernels)")
     return ap.parse_args()
 
@@ -229,7 +230,7 @@ def main():
     from paper_2604_11558_gb300 import binding
     from paper_2604_11558_gb300 import workloads as wl
 
-    if args.profile_case in ("sphere", "batch", "cylinder", "ball-fp64"):
+    if args.profile_case in ("sphere", "batch", "cylinder", "ball-fp64", "bulk-surface"):
         return profile_other(args.profile_case)
     w = wl.gray_scott_ball()
     n, S = w["n"], len(w["d"])
@@ -473,8 +474,8 @@ def measure_extras(flush):
 
 def profile_other(case):
     """Setup, 3 untimed steps, then 3 steps in the NVTX range sexpe_step, of the 256 x 512 sphere, the
-    256 batched disks, the 64 x 128 x 128 cylinder (split path) or the ball on the FP64 path, for an
-    ncu capture of their kernels."""
+    256 batched disks, the 64 x 128 x 128 cylinder (split path), the ball on the FP64 path or the
+    bulk-surface ball 30 x 50 x 30 (split path), for an ncu capture of their kernels."""
     import torch
     from paper_2604_11558_gb300 import binding
     from paper_2604_11558_gb300 import workloads as wl
@@ -486,6 +487,12 @@ def profile_other(case):
         w = wl.gray_scott_ball(steps=1)
         plan = binding.Plan.from_workload(w, precision="fp64")
         x = torch.from_numpy(w["W0"]).cuda()
+    elif case == "bulk-surface":
+        w = wl.bulk_surface_ball(steps=1)
+        plan = binding.CoupledPlan(w["n"], w["d_bulk"], w["bulk_params"], w["d_surface"], w["surface_params"],
+                                   w["coupling"], w["tau"], rho_star=w["rho_star"], precision="split_tf32")
+        import numpy as np
+        x = torch.from_numpy(np.concatenate([w["Wb"].ravel(), w["Ws"].ravel()])).cuda()
     elif case == "sphere":
         w = wl.schnakenberg_sphere(steps=1)
         plan = binding.Plan.from_workload(w, precision="split_tf32")

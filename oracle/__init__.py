@@ -26,6 +26,9 @@ What it computes, in plain numpy/scipy FP64 and in the paper's order:
 * ``coupled``   -- the bulk-surface Schnakenberg system of Section 5.5 (ball
                    and its boundary sphere coupled through Robin boundary
                    conditions and the surface reactions).
+* ``coupled_dib`` -- the bulk-surface DIB model of Section 5.6 (cylinder with a
+                   Dirichlet top and its bottom disk, coupled through flux
+                   conditions and the surface kinetics p, q).
 * ``adjoint``   -- gradients of a scalar loss by complex-step differentiation
                    through ``stepper`` (no transposed code path of its own).
 

@@ -382,8 +382,9 @@ def main():
 
 def measure_extras(flush):
     """The other workloads: cylinder 64x128x128 (3 species), sphere 256x512 (split and FP64), 256
-    uneven disks (one persistent launch per step), the bulk-surface ball 30x50x30 (split and FP64),
-    and the sphere 256x512 adjoint cost relative to its forward."""
+    uneven disks (one persistent launch per step), the bulk-surface ball 30x50x30 (split and FP64), the
+    bulk-surface DIB cylinder (FP64 140x140x25, split 128x140x25), and the sphere 256x512 adjoint cost
+    relative to its forward."""
     import numpy as np
     import torch
     from paper_2604_11558_gb300 import binding
@@ -449,6 +450,30 @@ def measure_extras(flush):
         plan.close()
     out["bulk_surface_ball_30x50x30"] = {"unit": UNIT, "dof": 2 * (30 * 50 * 30 + 50 * 30), "l2": "not flushed",
                                          **res}
+    # bulk-surface DIB model on the cylinder 140x140x25 and its bottom disk (Section 5.6): the paper's
+    # t_* = 250 run takes 10000 steps.  FP64 on the paper's grid; the split chains take n_rho <= 128,
+    # so they are timed on 128x140x25
+    res = {}
+    for prec, n, steps in (("fp64", (140, 140, 25), 200), ("split_tf32", (128, 140, 25), 1000)):
+        w = wl.dib_cylinder(n=n)
+        plan = binding.CoupledPlan(n, w["d_bulk"], w["bulk_params"], w["d_surface"], w["surface_params"],
+                                   w["coupling"], w["tau"], rho_star=w["rho_star"], precision=prec,
+                                   reaction=w["bulk_reaction"], surface_reaction=w["surface_reaction"],
+                                   geometry="cylinder", z_star=w["z_star"])
+        x = torch.from_numpy(np.concatenate([w["Wb"].ravel(), w["Ws"].ravel()])).cuda()
+        plan.step(x, 20)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.step(x, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[prec] = {"n": list(n), "dof": x.numel(), "ms_per_step": ms, "value": x.numel() / (ms / 1e3),
+                     "steps": steps, "kernels_per_step": plan.info()["kernels_per_step"],
+                     "t250_run_s": ms * w["steps"] / 1e3}
+        plan.close()
+    out["bulk_surface_dib_cylinder"] = {"unit": UNIT, "l2": "not flushed (state 8 MB)", **res}
     # sphere adjoint vs forward (FP64), full 256x512 workload: 1000 steps, checkpoints every 50
     w = wl.schnakenberg_sphere()
     plan = binding.Plan.from_workload(w, precision="fp64")

@@ -65,6 +65,9 @@ typedef enum { SEXPE_FP64 = 0, SEXPE_SPLIT_TF32 = 1, SEXPE_UNSPLIT_FP64 = 2 } se
  *   SCHNAKENBERG (S=2), params {gamma, a, b}: f = gamma(a - u + u^2 v), g = gamma(b - u^2 v)
  *   GRAY_SCOTT   (S=2), params {F, k}:        f = -u v^2 + F(1-u),      g = u v^2 - (F+k) v
  *   LINEAR_CUBIC (S<=4), params K row-major S x S: f_i = sum_j K_ij u_j - u_i^3
+ *   LINEAR (S<=4), params K row-major S x S: f_i = sum_j K_ij u_j (the bulk kinetics
+ *       b(u) = -alpha1 (u - alpha2), c(v) = -beta1 (v - beta2) of Section 5.6 on the
+ *       lifted state w = (u - alpha2, v - beta2) are K = diag(-alpha1, -beta1))
  *   BVAM (S=2), params {alpha1, alpha2, alpha3, beta1, beta2} (Section 5.1, eq. BVAMnl):
  *       b = alpha1 u (1 - alpha2 v^2) + v (1 - alpha3 u),
  *       c = beta1 v (1 + alpha1 alpha2 / beta1 u v) + u (beta2 + alpha3 v)
@@ -81,7 +84,8 @@ typedef enum {
     SEXPE_GRAY_SCOTT = 2,
     SEXPE_LINEAR_CUBIC = 3,
     SEXPE_BVAM = 4,
-    SEXPE_BVAM_MANUFACTURED = 5
+    SEXPE_BVAM_MANUFACTURED = 5,
+    SEXPE_LINEAR = 6
 } sexpe_reaction;
 
 /* Height axis of the cylinder: NEUMANN = homogeneous Neumann at both caps
@@ -192,36 +196,60 @@ sexpe_status sexpe_step_host(sexpe_plan* plan, double* state_host, int64_t n_ste
  *  - Results equal sexpe_step's for the same plan and state. */
 sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_steps, void* stream);
 
-/* Bulk-surface coupled system (Section 5.5, eqs. bulkball): two species u, v on
- * the ball (`ball`, geometry SEXPE_BALL; `bulk`: diffusion d_u, d_v = delta and a
- * two-species reaction, alpha1 b(u, v), alpha1 c(u, v) for SCHNAKENBERG with
- * params {alpha1, alpha2, beta1}) and two species r, s on its boundary sphere
- * rho = rho_*, whose grid is the ball's theta x phi grid (`surface`: diffusion
- * 1/rho_*^2 and eps/rho_*^2 for the paper's scaling, reaction zeta1 b(r, s),
- * zeta1 c(r, s)).  They couple through the boundary conditions
- * grad u . n = zeta1 (zeta2 r - zeta3 u), delta grad v . n = zeta1 (eta1 s - eta2 v)
- * and the surface reactions p = b(r, s) - (zeta2 r - zeta3 u),
- * q = c(r, s) - (eta1 s - eta2 v).  The paper omits the coupled discretisation;
- * this one keeps eq. ball_discr and lets a normal derivative g enter its outer
- * radial row through the same virtual point, adding (2/h + 2/rho_*) g, with h
- * the radial step; all coupling terms are explicit at t_n with the reactions,
- * and each component takes its own geometry's split step (eqs. ee_ball,
- * ee_sphere).  State (device, FP64, caller-owned): [u][v] in the ball layout,
- * then [r][s] in the sphere layout (theta fastest), 2 (N_ball + N_sphere)
- * elements.  Precision SEXPE_FP64 (FP64 SIMT chains) or SEXPE_SPLIT_TF32 (the
- * tensor-core chains of each grid, the coupling terms formed in FP64 and added
- * to their FP32 F); SEXPE_UNSPLIT_FP64 gives SEXPE_EUNSUPPORTED.  No adjoint,
- * no lifting offsets, no sexpe_set_stencil / sexpe_set_theta_split
- * (SEXPE_EUNSUPPORTED) and no sexpe_step_noalloc (SEXPE_EINVAL).  Step with
- * sexpe_step / sexpe_step_host; destroy with sexpe_destroy.  Other errors as
- * sexpe_setup. */
+/* Bulk-surface coupled systems (Sections 5.5 and 5.6): two bulk species on a 3-D
+ * grid and two surface species on a 2-D grid that is part of its boundary,
+ * coupled through flux boundary conditions of the bulk and through the surface
+ * kinetics.  The paper omits the coupled discretisation; this one keeps each
+ * bulk axis as printed and lets a normal derivative g = grad w . n enter the
+ * boundary row through the same virtual point that gives the row its Neumann
+ * form; all coupling terms are explicit at t_n with the reactions, and each
+ * component takes its own geometry's split step.
+ *
+ *  SEXPE_COUPLING_SCHNAKENBERG_BALL (Section 5.5, eqs. bulkball): bulk u, v on
+ *    the ball `bulk_grid` (SEXPE_BALL; `bulk`: diffusion d_u, d_v = delta and its
+ *    reaction, alpha1 (b, c) by SCHNAKENBERG with params {alpha1, alpha2, beta1});
+ *    surface r, s on the boundary sphere rho = rho_* whose grid is the ball's
+ *    theta x phi grid (`surface`: diffusion 1/rho_*^2 and eps/rho_*^2, reaction
+ *    zeta1 (b, c)).  grad u . n = zeta1 (zeta2 r - zeta3 u) and
+ *    delta grad v . n = zeta1 (eta1 s - eta2 v) enter the outer radial row of
+ *    eq. ball_discr as (2/h + 2/rho_*) times d_u grad u . n and delta grad v . n
+ *    (h the radial step); the surface F loses zeta1 (zeta2 r - zeta3 u) and
+ *    zeta1 (eta1 s - eta2 v).  Uses zeta[0..2], eta[0..1].
+ *  SEXPE_COUPLING_DIB_CYLINDER (Section 5.6, eqs. bulkcyl): bulk u, v on the
+ *    cylinder `bulk_grid` (SEXPE_CYLINDER with z_bc = SEXPE_Z_PAPER: Neumann at
+ *    z = 0, Dirichlet at z_*), its state LIFTED by the top values,
+ *    w = (u - u_top, v - v_top) (`bulk`: diffusion 1, delta and its reaction on w,
+ *    e.g. LINEAR with K = diag(-alpha1, -beta1)); surface r, s on the bottom disk
+ *    z = 0 whose grid is the cylinder's rho x theta grid (`surface`: diffusion 1,
+ *    eps; reaction usually NONE).  With u = w_u + u_top, v = w_v + v_top on z = 0,
+ *      p = zeta2 u (1 - s) r - zeta3 r^3 - zeta4 (s - zeta5),
+ *      q = eta1 v (1 + eta2 r)(1 - s)(1 - eta3 (1 - s)) - eta4 (1 + eta5 r) s (1 + eta3 s),
+ *    the surface F gains zeta1 p, zeta1 q, and grad u . n = -zeta1 alpha3 p,
+ *    grad v . n = -zeta1 beta3 q enter the z = 0 row of eq. A_z as 2/h_z times
+ *    d_u grad u . n and d_v grad v . n.  Uses zeta[0..4], eta[0..4], alpha3,
+ *    beta3, u_top, v_top.
+ *
+ * State (device, FP64, caller-owned): [bulk species 0][1] in the bulk grid's
+ * layout, then [surface 0][1] in the surface grid's layout (sphere: theta
+ * fastest; disk: rho fastest), 2 (N_bulk + N_surface) elements.  Precision
+ * SEXPE_FP64 (FP64 SIMT chains) or SEXPE_SPLIT_TF32 (each grid's tensor-core
+ * chain, within its size limits; the coupling terms formed in FP64 and added to
+ * the FP32 F); SEXPE_UNSPLIT_FP64 gives SEXPE_EUNSUPPORTED.  Both species sets
+ * must have 2 species; no lifting offsets (SEXPE_EINVAL), no adjoint, no
+ * sexpe_set_stencil / sexpe_set_theta_split (SEXPE_EUNSUPPORTED), no
+ * sexpe_step_noalloc (SEXPE_EINVAL).  Step with sexpe_step / sexpe_step_host;
+ * destroy with sexpe_destroy.  Other errors as sexpe_setup. */
+typedef enum { SEXPE_COUPLING_SCHNAKENBERG_BALL = 0, SEXPE_COUPLING_DIB_CYLINDER = 1 } sexpe_coupling_kind;
 typedef struct {
-    double zeta1, zeta2, zeta3;  /* grad u . n = zeta1 (zeta2 r - zeta3 u)             */
-    double eta1, eta2;           /* delta grad v . n = zeta1 (eta1 s - eta2 v)       */
+    int32_t kind;            /* sexpe_coupling_kind                                       */
+    double zeta[5];          /* zeta1 .. zeta5                                            */
+    double eta[5];           /* eta1 .. eta5                                              */
+    double alpha3, beta3;    /* DIB: scalings of the bulk fluxes                           */
+    double u_top, v_top;     /* DIB: Dirichlet values on z = z_*, by which the bulk is lifted */
 } sexpe_coupling;
-sexpe_status sexpe_coupled_setup(const sexpe_grid* ball, const sexpe_species* bulk, const sexpe_species* surface,
-                                 const sexpe_coupling* cp, double tau, int32_t precision, void* stream,
-                                 sexpe_plan** out);
+sexpe_status sexpe_coupled_setup(const sexpe_grid* bulk_grid, const sexpe_species* bulk,
+                                 const sexpe_species* surface, const sexpe_coupling* cp, double tau,
+                                 int32_t precision, void* stream, sexpe_plan** out);
 
 /* Wait for the plan's work on `stream` and report the device error word
  * (SEXPE_ETIMEOUT if a bounded wait ran out), clearing it. */

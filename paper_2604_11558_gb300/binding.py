@@ -20,7 +20,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sexpe.h")
 
 GEOMETRY = {"disk": 0, "sphere": 1, "ball": 2, "cylinder": 3}
 PRECISION = {"fp64": 0, "split_tf32": 1, "unsplit_fp64": 2}
-REACTION = {"none": 0, "schnakenberg": 1, "gray_scott": 2, "linear_cubic": 3, "bvam": 4, "bvam_manufactured": 5}
+REACTION = {"none": 0, "schnakenberg": 1, "gray_scott": 2, "linear_cubic": 3, "bvam": 4, "bvam_manufactured": 5,
+            "linear": 6}
 ZBC = {"neumann": 0, "paper": 1}
 AXIS = {"theta": 0, "rho2": 1, "rho3": 2, "phi": 3, "z_neumann": 4, "z_paper": 5}
 STATUS = {0: "SEXPE_OK", 1: "SEXPE_EINVAL", 2: "SEXPE_ENOMEM", 3: "SEXPE_ECUDA", 4: "SEXPE_ETIMEOUT",
@@ -45,9 +46,23 @@ class Species(ctypes.Structure):
                 ("params_host", ctypes.POINTER(ctypes.c_double)), ("offset_host", ctypes.POINTER(ctypes.c_double))]
 
 
+COUPLING = {"schnakenberg_ball": 0, "dib_cylinder": 1}
+
+
 class Coupling(ctypes.Structure):
-    _fields_ = [("zeta1", ctypes.c_double), ("zeta2", ctypes.c_double), ("zeta3", ctypes.c_double),
-                ("eta1", ctypes.c_double), ("eta2", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int32), ("zeta", ctypes.c_double * 5), ("eta", ctypes.c_double * 5),
+                ("alpha3", ctypes.c_double), ("beta3", ctypes.c_double), ("u_top", ctypes.c_double),
+                ("v_top", ctypes.c_double)]
+
+
+def _coupling_struct(c):
+    """c: dict with 'kind' (default 'schnakenberg_ball'), zeta1..zeta5, eta1..eta5 (missing ones 0),
+    alpha3, beta3, u_top, v_top."""
+    z = [float(c.get(f"zeta{q}", 0.0)) for q in range(1, 6)]
+    e = [float(c.get(f"eta{q}", 0.0)) for q in range(1, 6)]
+    return Coupling(COUPLING[c.get("kind", "schnakenberg_ball")], (ctypes.c_double * 5)(*z),
+                    (ctypes.c_double * 5)(*e), float(c.get("alpha3", 0.0)), float(c.get("beta3", 0.0)),
+                    float(c.get("u_top", 0.0)), float(c.get("v_top", 0.0)))
 
 
 class PlanInfo(ctypes.Structure):
@@ -291,30 +306,33 @@ class BatchPlan(Plan):
 
 
 class CoupledPlan(Plan):
-    """The bulk-surface coupled system of Section 5.5 (wraps sexpe_coupled_setup): species u, v on the ball
-    n = (n_rho, n_theta, n_phi) and r, s on its boundary sphere; state [u][v] (ball layout) then [r][s]
-    (sphere layout, theta fastest)."""
+    """A bulk-surface coupled plan (wraps sexpe_coupled_setup).  Section 5.5: the ball
+    n = (n_rho, n_theta, n_phi) and its boundary sphere, state [u][v] (ball layout) then [r][s] (sphere
+    layout, theta fastest).  Section 5.6 (coupling kind 'dib_cylinder', geometry 'cylinder'): the
+    cylinder n = (n_rho, n_theta, n_z) with the Dirichlet top of eq. A_z, its state lifted by
+    (u_top, v_top), and the bottom disk, state [w_u][w_v] (cylinder layout) then [r][s] (disk layout)."""
 
     def __init__(self, n, d_bulk, bulk_params, d_surface, surface_params, coupling, tau, rho_star=1.0,
-                 precision="fp64", stream=None, reaction="schnakenberg"):
+                 precision="fp64", stream=None, reaction="schnakenberg", surface_reaction=None,
+                 geometry="ball", z_star=1.0):
         L = lib()
-        self._keep = [np.ascontiguousarray(x, dtype=np.float64)
+        self._keep = [np.ascontiguousarray(x if len(x) else [0.0], dtype=np.float64)
                       for x in (d_bulk, bulk_params, d_surface, surface_params)]
         db, pb, ds, ps = self._keep
-        grid = _grid_struct("ball", n, rho_star)
-        bulk = Species(len(db), _dptr(db), REACTION[reaction], len(pb), _dptr(pb))
-        surf = Species(len(ds), _dptr(ds), REACTION[reaction], len(ps), _dptr(ps))
-        c = coupling
-        cp = Coupling(float(c["zeta1"]), float(c["zeta2"]), float(c["zeta3"]), float(c["eta1"]), float(c["eta2"]))
+        grid = _grid_struct(geometry, n, rho_star, z_star, "paper" if geometry == "cylinder" else "neumann")
+        srx = reaction if surface_reaction is None else surface_reaction
+        bulk = Species(len(d_bulk), _dptr(db), REACTION[reaction], len(bulk_params), _dptr(pb))
+        surf = Species(len(d_surface), _dptr(ds), REACTION[srx], len(surface_params), _dptr(ps))
+        cp = _coupling_struct(coupling)
         h = _P()
         st = _stream_ptr(stream) if stream is not None else 0
         _check(L.sexpe_coupled_setup(ctypes.byref(grid), ctypes.byref(bulk), ctypes.byref(surf), ctypes.byref(cp),
                                      float(tau), PRECISION[precision], st, ctypes.byref(h)), "sexpe_coupled_setup")
         self.handle = h
-        self.geometry, self.n, self.S = "ball+sphere", tuple(n), len(db) + len(ds)
+        self.geometry, self.n, self.S = geometry + "+surface", tuple(n), len(d_bulk) + len(d_surface)
         self._p_list = []
-        self.n_ball = int(np.prod(n))
-        self.n_sphere = int(n[1]) * int(n[2])
+        self.n_bulk = int(np.prod(n))
+        self.n_surface = int(n[1]) * int(n[2]) if geometry == "ball" else int(n[0]) * int(n[1])
 
 
 def coupled_setup_status(*args, **kw):

@@ -142,6 +142,13 @@ __device__ __forceinline__ T reaction(const ReactionParams<T>& rp, const T* w_st
             if (r < rp.S) acc = fma_t(rp.p[s * rp.S + r], w[r], acc);
         return acc;
     }
+    case R_LINEAR: {         // f_i = sum_j K_ij u_j
+        T acc = (T)0;
+#pragma unroll
+        for (int r = 0; r < kMaxSpecies; ++r)
+            if (r < rp.S) acc = fma_t(rp.p[s * rp.S + r], w[r], acc);
+        return acc;
+    }
     default:
         return (T)0;
     }
@@ -210,11 +217,12 @@ __device__ __forceinline__ void reactions(const ReactionParams<T>& rp, const T* 
         }
     }
     if constexpr (KIND < 0) {
-        if (rp.kind == R_LINEAR_CUBIC) {
+        if (rp.kind == R_LINEAR_CUBIC || rp.kind == R_LINEAR) {
+            const bool cubic = rp.kind == R_LINEAR_CUBIC;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if (s < rp.S) {
-                    T acc = -mul_t(mul_t(w[s], w[s]), w[s]);
+                    T acc = cubic ? -mul_t(mul_t(w[s], w[s]), w[s]) : (T)0;
 #pragma unroll
                     for (int r = 0; r < NS; ++r)
                         if (r < rp.S) acc = fma_t(rp.p[s * rp.S + r], w[r], acc);

@@ -5,7 +5,7 @@
 namespace sexpe {
 
 enum Geo { GEO_DISK = 0, GEO_SPHERE = 1, GEO_BALL = 2, GEO_CYLINDER = 3 };
-enum Reac { R_NONE = 0, R_SCHNAKENBERG = 1, R_GRAY_SCOTT = 2, R_LINEAR_CUBIC = 3, R_BVAM = 4, R_BVAM_MMS = 5 };
+enum Reac { R_NONE = 0, R_SCHNAKENBERG = 1, R_GRAY_SCOTT = 2, R_LINEAR_CUBIC = 3, R_BVAM = 4, R_BVAM_MMS = 5, R_LINEAR = 6 };
 
 constexpr int kMaxSpecies = 4;
 constexpr int kMaxN = 512;
@@ -22,6 +22,21 @@ struct StencilAxis {
     const T* rs;
     int n;
     int periodic;
+};
+
+// Bulk-surface coupling terms, one thread per surface point q (Sections 5.5 and 5.6).
+// kind 0: ball + boundary sphere, q = j + n_theta k, bulk node (n_rho - 1, j, k);
+// kind 1: cylinder + bottom disk, q = i + n_rho j, bulk node (i, j, 0).
+struct CoupleArgs {
+    int kind;
+    int bn1, bn2;            // bulk points along modes 1 and 2
+    int sn1;                 // surface points along its mode 1
+    long long nb, ns;        // points per species of the bulk and of the surface
+    double coef;             // ball: 2/h + 2/rho_*; cylinder: 2/h_z (the virtual-point factor)
+    double d0, d1;           // bulk diffusion
+    double z[5], e[5];       // zeta1..5, eta1..5
+    double a3, b3;           // flux scalings (kind 1)
+    double u_top, v_top;     // lifting of the bulk state (kind 1)
 };
 
 template <class T>

@@ -94,62 +94,80 @@ __global__ void __launch_bounds__(256) k_gemm64(Gemm64 g) {
     }
 }
 
-// Bulk-surface coupling (Section 5.5, eqs. bulkballsys, bulkballnl), one thread per surface
-// point (theta_j, phi_k) = bulk node (rho_*, theta_j, phi_k): with the normal derivatives
-// g_u = zeta1 (zeta2 r - zeta3 u) and delta g_v = zeta1 (eta1 s - eta2 v), the bulk F gets the
-// virtual-point term of the outer radial row, coef = 2/h + 2/rho_* (d_u coef g_u and coef
-// delta g_v), and the surface F the coupling parts of p and q (-g_u and -delta g_v).
-__global__ void k_couple64(const double* __restrict__ Wb, const double* __restrict__ Ws, double* __restrict__ Fb,
-                           double* __restrict__ Fs, int n_rho, int n_theta, int n_phi, double coef, double du,
-                           double z1, double z2, double z3, double e1, double e2) {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long ns = (long long)n_theta * n_phi, nb = ns * n_rho;
-    if (q >= ns) return;
-    const long long b = (n_rho - 1) + (long long)n_rho * q;        // q = j + n_theta k
-    const double ub = Wb[b], vb = Wb[nb + b], r = Ws[q], s = Ws[ns + q];
-    const double ju = z1 * (z2 * r - z3 * ub), jv = z1 * (e1 * s - e2 * vb);
-    Fb[b] += du * coef * ju;
-    Fb[nb + b] += coef * jv;
-    Fs[q] -= ju;
-    Fs[ns + q] -= jv;
+// The coupling terms at one surface point from the bulk values (ub, vb) on the
+// boundary and the surface values (r, s): add[0], add[1] go to the bulk F of the
+// boundary node, add[2], add[3] to the surface F (Sections 5.5 and 5.6).
+__device__ __forceinline__ void couple_terms(const CoupleArgs& a, double ub, double vb, double r, double s,
+                                             double* add) {
+    if (a.kind == 0) {      // Robin exchange of eqs. bulkball
+        const double ju = a.z[0] * (a.z[1] * r - a.z[2] * ub), jv = a.z[0] * (a.e[0] * s - a.e[1] * vb);
+        add[0] = a.d0 * a.coef * ju;                 // d_u grad u . n
+        add[1] = a.coef * jv;                        // delta grad v . n
+        add[2] = -ju;
+        add[3] = -jv;
+    } else {                // DIB kinetics of eqs. bulkcylnl, bulk lifted by the top values
+        const double u = ub + a.u_top, v = vb + a.v_top;
+        const double P = a.z[1] * u * (1.0 - s) * r - a.z[2] * r * r * r - a.z[3] * (s - a.z[4]);
+        const double Q = a.e[0] * v * (1.0 + a.e[1] * r) * (1.0 - s) * (1.0 - a.e[2] * (1.0 - s)) -
+                         a.e[3] * (1.0 + a.e[4] * r) * s * (1.0 + a.e[2] * s);
+        const double gu = -a.z[0] * a.a3 * P, gv = -a.z[0] * a.b3 * Q;    // grad . n on z = 0
+        add[0] = a.d0 * a.coef * gu;
+        add[1] = a.d1 * a.coef * gv;
+        add[2] = a.z[0] * P;
+        add[3] = a.z[0] * Q;
+    }
 }
 
-cudaError_t launch_couple64(const double* Wb, const double* Ws, double* Fb, double* Fs, int n_rho, int n_theta,
-                            int n_phi, double coef, double du, const double* c, cudaStream_t st) {
-    const long long ns = (long long)n_theta * n_phi;
-    k_couple64<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(Wb, Ws, Fb, Fs, n_rho, n_theta, n_phi, coef, du, c[0], c[1],
-                                                           c[2], c[3], c[4]);
+__device__ __forceinline__ long long couple_bulk_node(const CoupleArgs& a, long long q) {
+    return a.kind == 0 ? (a.bn1 - 1) + (long long)a.bn1 * q : q;
+}
+
+// Bulk-surface coupling for the FP64 chains: one thread per surface point adds the
+// terms to the bulk F (buffer of the bulk sub-plan, species stride nb) and the
+// surface F (species stride ns), both computed from the state at t_n.
+__global__ void k_couple64(CoupleArgs a, const double* __restrict__ Wb, const double* __restrict__ Ws,
+                           double* __restrict__ Fb, double* __restrict__ Fs) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.ns) return;
+    const long long b = couple_bulk_node(a, q);
+    double add[4];
+    couple_terms(a, Wb[b], Wb[a.nb + b], Ws[q], Ws[a.ns + q], add);
+    Fb[b] += add[0];
+    Fb[a.nb + b] += add[1];
+    Fs[q] += add[2];
+    Fs[a.ns + q] += add[3];
+}
+
+cudaError_t launch_couple64(const CoupleArgs& a, const double* Wb, const double* Ws, double* Fb, double* Fs,
+                            cudaStream_t st) {
+    k_couple64<<<(unsigned)((a.ns + 255) / 256), 256, 0, st>>>(a, Wb, Ws, Fb, Fs);
     return cudaGetLastError();
 }
 
-// The same coupling terms for the split-TF32 chains, whose F is FP32 in the
-// padded layout [s][k][j][n1q] of each grid (ball: i = rho fastest, j = theta,
-// k = phi; sphere: i = theta, j = phi).  The terms are formed in FP64 from the
-// FP64 state and added to F in FP64 before rounding to FP32.
-__global__ void k_couple_split(const double* __restrict__ Wb, const double* __restrict__ Ws, float* __restrict__ Yb,
-                               float* __restrict__ Ys, int n_rho, int n_theta, int n_phi, int n1q_b, long long ys_b,
-                               int n1q_s, long long ys_s, double coef, double du, double z1, double z2, double z3,
-                               double e1, double e2) {
+// The same terms for the split-TF32 chains, whose F is FP32 in the padded layout
+// [s][k][j][n1q] of each grid: the ball's boundary node (n_rho - 1, j, k) and the
+// cylinder's (i, j, 0); the surface point (a, c) = (q mod sn1, q / sn1) at
+// c n1q + a.  The terms are added to F in FP64 before rounding to FP32.
+__global__ void k_couple_split(CoupleArgs a, const double* __restrict__ Wb, const double* __restrict__ Ws,
+                               float* __restrict__ Yb, float* __restrict__ Ys, int n1q_b, long long ys_b, int n1q_s,
+                               long long ys_s) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long ns = (long long)n_theta * n_phi, nb = ns * n_rho;
-    if (q >= ns) return;
-    const long long j = q % n_theta, k = q / n_theta;
-    const long long b = (n_rho - 1) + (long long)n_rho * q;
-    const double ub = Wb[b], vb = Wb[nb + b], r = Ws[q], s = Ws[ns + q];
-    const double ju = z1 * (z2 * r - z3 * ub), jv = z1 * (e1 * s - e2 * vb);
-    const long long yb = (k * n_theta + j) * n1q_b + (n_rho - 1), ysq = k * n1q_s + j;
-    Yb[yb] = (float)((double)Yb[yb] + du * coef * ju);
-    Yb[ys_b + yb] = (float)((double)Yb[ys_b + yb] + coef * jv);
-    Ys[ysq] = (float)((double)Ys[ysq] - ju);
-    Ys[ys_s + ysq] = (float)((double)Ys[ys_s + ysq] - jv);
+    if (q >= a.ns) return;
+    const long long b = couple_bulk_node(a, q);
+    double add[4];
+    couple_terms(a, Wb[b], Wb[a.nb + b], Ws[q], Ws[a.ns + q], add);
+    const long long ca = q % a.sn1, cc = q / a.sn1;
+    const long long yb = a.kind == 0 ? (cc * a.bn2 + ca) * n1q_b + (a.bn1 - 1) : cc * n1q_b + ca;
+    const long long ysq = cc * n1q_s + ca;
+    Yb[yb] = (float)((double)Yb[yb] + add[0]);
+    Yb[ys_b + yb] = (float)((double)Yb[ys_b + yb] + add[1]);
+    Ys[ysq] = (float)((double)Ys[ysq] + add[2]);
+    Ys[ys_s + ysq] = (float)((double)Ys[ys_s + ysq] + add[3]);
 }
 
-cudaError_t launch_couple_split(const double* Wb, const double* Ws, float* Yb, float* Ys, int n_rho, int n_theta,
-                                int n_phi, int n1q_b, long long ys_b, int n1q_s, long long ys_s, double coef,
-                                double du, const double* c, cudaStream_t st) {
-    const long long ns = (long long)n_theta * n_phi;
-    k_couple_split<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(Wb, Ws, Yb, Ys, n_rho, n_theta, n_phi, n1q_b, ys_b,
-                                                               n1q_s, ys_s, coef, du, c[0], c[1], c[2], c[3], c[4]);
+cudaError_t launch_couple_split(const CoupleArgs& a, const double* Wb, const double* Ws, float* Yb, float* Ys,
+                                int n1q_b, long long ys_b, int n1q_s, long long ys_s, cudaStream_t st) {
+    k_couple_split<<<(unsigned)((a.ns + 255) / 256), 256, 0, st>>>(a, Wb, Ws, Yb, Ys, n1q_b, ys_b, n1q_s, ys_s);
     return cudaGetLastError();
 }
 

@@ -9,13 +9,12 @@ namespace sexpe {
 // FP64 SIMT path.
 cudaError_t launch_rhs64(int geometry, const RhsTables<double>& tb, const double* W, double* F, cudaStream_t st);
 cudaError_t launch_gemm64(const Gemm64& g, int n_species, cudaStream_t st);
-cudaError_t launch_couple64(const double* Wb, const double* Ws, double* Fb, double* Fs, int n_rho, int n_theta,
-                            int n_phi, double coef, double du, const double* c, cudaStream_t st);
-// Split-TF32 counterpart: the same terms added to the FP32 F of the ball (Yb) and
-// sphere (Ys) chains, layouts [s][k][j][n1q] with ys floats per species.
-cudaError_t launch_couple_split(const double* Wb, const double* Ws, float* Yb, float* Ys, int n_rho, int n_theta,
-                                int n_phi, int n1q_b, long long ys_b, int n1q_s, long long ys_s, double coef,
-                                double du, const double* c, cudaStream_t st);
+// Bulk-surface coupling terms added to the bulk and surface F (FP64 chains), or to
+// the FP32 F of the split chains (Yb, Ys: layouts [s][k][j][n1q], ys floats per species).
+cudaError_t launch_couple64(const CoupleArgs& a, const double* Wb, const double* Ws, double* Fb, double* Fs,
+                            cudaStream_t st);
+cudaError_t launch_couple_split(const CoupleArgs& a, const double* Wb, const double* Ws, float* Yb, float* Ys,
+                                int n1q_b, long long ys_b, int n1q_s, long long ys_s, cudaStream_t st);
 // Unsplit baseline: W_s += tau P_s F_s, P_s dense N x N row-major.
 cudaError_t launch_matvec64(const double* P, const double* F, double* W, int N, int S, double tau, cudaStream_t st);
 // Discrete adjoint (FP64).

@@ -686,17 +686,14 @@ sexpe_status enqueue_split_products(sexpe_plan* q, sexpe_plan* prof, const Split
     return SEXPE_OK;
 }
 
-// Bulk-surface step (Section 5.5): both stencil+reaction passes, the boundary coupling added
-// to their F (explicit at t_n), then each component's own split chain (eqs. ee_ball, ee_sphere).
-// State: [u, v on the ball][r, s on the sphere].
+// Bulk-surface step (Sections 5.5, 5.6): both stencil+reaction passes, the boundary coupling
+// added to their F (explicit at t_n), then each component's own split chain (eqs. ee_ball and
+// ee_sphere, or ee_cylinder and ee_disk).  State: [bulk species][surface species].
 sexpe_status enqueue_coupled_step(sexpe_plan* p, double* state, cudaStream_t st) {
     sexpe_plan* b = p->sub[0];
     sexpe_plan* s = p->sub[1];
     double* Wb = state;
     double* Ws = state + 2 * b->npts;
-    const double h = b->ax[0].pts[0];                  // rho_i = i h, i = 1 .. n_rho
-    const double rho_star = b->ax[0].pts[b->n[0] - 1];
-    const double coef = 2.0 / h + 2.0 / rho_star;
     if (p->precision == SEXPE_SPLIT_TF32) {
         SplitTables Tb = b->tabs, Ts = s->tabs;
         Tb.state = Tb.state_upd = Wb;
@@ -707,8 +704,7 @@ sexpe_status enqueue_coupled_step(sexpe_plan* p, double* state, cudaStream_t st)
         SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_rhs_split(Ts, st));
         SX_CUDA(prof_mark(p, st));
-        SX_CUDA(launch_couple_split(Wb, Ws, Tb.Y, Ts.Y, b->n[0], b->n[1], b->n[2], Tb.n1q, Tb.ys, Ts.n1q, Ts.ys,
-                                    coef, b->d[0], p->cpl, st));
+        SX_CUDA(launch_couple_split(p->cpl, Wb, Ws, Tb.Y, Ts.Y, Tb.n1q, Tb.ys, Ts.n1q, Ts.ys, st));
         SX_TRY(enqueue_split_products(b, p, Tb, st));
         SX_TRY(enqueue_split_products(s, p, Ts, st));
         return SEXPE_OK;
@@ -718,7 +714,7 @@ sexpe_status enqueue_coupled_step(sexpe_plan* p, double* state, cudaStream_t st)
     SX_CUDA(prof_mark(p, st));
     SX_CUDA(launch_rhs64(s->geometry, s->rhs64, Ws, s->buf64[0], st));
     SX_CUDA(prof_mark(p, st));
-    SX_CUDA(launch_couple64(Wb, Ws, b->buf64[0], s->buf64[0], b->n[0], b->n[1], b->n[2], coef, b->d[0], p->cpl, st));
+    SX_CUDA(launch_couple64(p->cpl, Wb, Ws, b->buf64[0], s->buf64[0], st));
     SX_TRY(enqueue_fp64_chain(b, p, Wb, st));
     SX_TRY(enqueue_fp64_chain(s, p, Ws, st));
     return SEXPE_OK;
@@ -806,6 +802,7 @@ sexpe_status validate(const sexpe_grid* g, const sexpe_species* sp, double tau, 
     case SEXPE_SCHNAKENBERG: if (sp->n_species != 2 || sp->n_params != 3) return SEXPE_EINVAL; break;
     case SEXPE_GRAY_SCOTT: if (sp->n_species != 2 || sp->n_params != 2) return SEXPE_EINVAL; break;
     case SEXPE_LINEAR_CUBIC:
+    case SEXPE_LINEAR:
         if (sp->n_params != sp->n_species * sp->n_species) return SEXPE_EINVAL;
         break;
     case SEXPE_BVAM: if (sp->n_species != 2 || sp->n_params != 5 || sp->params_host[3] == 0.0) return SEXPE_EINVAL; break;
@@ -1296,24 +1293,36 @@ sexpe_status sexpe_setup(const sexpe_grid* grid, const sexpe_species* species, d
     return SEXPE_OK;
 }
 
-sexpe_status sexpe_coupled_setup(const sexpe_grid* ball, const sexpe_species* bulk, const sexpe_species* surface,
+sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk, const sexpe_species* surface,
                                  const sexpe_coupling* cp, double tau, int32_t precision, void* stream,
                                  sexpe_plan** out) {
     if (!out) return SEXPE_EINVAL;
     *out = nullptr;
-    if (!ball || !bulk || !surface || !cp) return SEXPE_EINVAL;
-    if (ball->geometry != SEXPE_BALL || bulk->n_species != 2 || surface->n_species != 2) return SEXPE_EINVAL;
-    const double c[5] = {cp->zeta1, cp->zeta2, cp->zeta3, cp->eta1, cp->eta2};
-    for (double x : c)
+    if (!bg || !bulk || !surface || !cp) return SEXPE_EINVAL;
+    if (cp->kind != SEXPE_COUPLING_SCHNAKENBERG_BALL && cp->kind != SEXPE_COUPLING_DIB_CYLINDER) return SEXPE_EINVAL;
+    const bool dib = cp->kind == SEXPE_COUPLING_DIB_CYLINDER;
+    if (bg->geometry != (dib ? SEXPE_CYLINDER : SEXPE_BALL)) return SEXPE_EINVAL;
+    if (dib && bg->z_bc != SEXPE_Z_PAPER) return SEXPE_EINVAL;
+    if (bulk->n_species != 2 || surface->n_species != 2) return SEXPE_EINVAL;
+    for (int q = 0; q < 5; ++q)
+        if (!std::isfinite(cp->zeta[q]) || !std::isfinite(cp->eta[q])) return SEXPE_EINVAL;
+    const double extra[4] = {cp->alpha3, cp->beta3, cp->u_top, cp->v_top};
+    for (double x : extra)
         if (!std::isfinite(x)) return SEXPE_EINVAL;
     if (bulk->offset_host || surface->offset_host) return SEXPE_EINVAL;
     if (bulk->reaction == SEXPE_BVAM_MANUFACTURED || surface->reaction == SEXPE_BVAM_MANUFACTURED) return SEXPE_EINVAL;
-    sexpe_grid sg = *ball;                             // the boundary sphere: the ball's theta and phi grids
-    sg.geometry = SEXPE_SPHERE;
-    sg.n[0] = ball->n[1];
-    sg.n[1] = ball->n[2];
+    sexpe_grid sg = *bg;                               // the surface grid: part of the bulk grid's boundary
     sg.n[2] = 0;
-    sexpe_status v = validate(ball, bulk, tau, precision);
+    if (dib) {                                         // bottom disk: the cylinder's rho x theta grid
+        sg.geometry = SEXPE_DISK;
+        sg.rho_op = 0;
+        sg.z_bc = 0;
+    } else {                                           // boundary sphere: the ball's theta x phi grid
+        sg.geometry = SEXPE_SPHERE;
+        sg.n[0] = bg->n[1];
+        sg.n[1] = bg->n[2];
+    }
+    sexpe_status v = validate(bg, bulk, tau, precision);
     if (v == SEXPE_OK) v = validate(&sg, surface, tau, precision);
     if (v != SEXPE_OK) return v;
     if (precision != SEXPE_FP64 && precision != SEXPE_SPLIT_TF32) return SEXPE_EUNSUPPORTED;
@@ -1325,18 +1334,38 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* ball, const sexpe_species* bu
     try {
         p->sub[0] = new sexpe_plan();
         p->sub[1] = new sexpe_plan();
-        s = build_plan(p->sub[0], ball, bulk, tau, precision, st);
+        s = build_plan(p->sub[0], bg, bulk, tau, precision, st);
         if (s == SEXPE_OK) s = build_plan(p->sub[1], &sg, surface, tau, precision, st);
         if (s == SEXPE_OK) {
             p->coupled = true;
-            p->geometry = SEXPE_BALL;
+            p->geometry = bg->geometry;
             p->precision = precision;
             p->S = 4;
             p->ndim = 3;
-            for (int m = 0; m < 3; ++m) p->n[m] = ball->n[m];
+            for (int m = 0; m < 3; ++m) p->n[m] = bg->n[m];
             p->npts = p->sub[0]->npts;
             p->tau = tau;
-            for (int q = 0; q < 5; ++q) p->cpl[q] = c[q];
+            CoupleArgs& a = p->cpl;
+            a.kind = cp->kind;
+            a.bn1 = bg->n[0];
+            a.bn2 = bg->n[1];
+            a.sn1 = sg.n[0];
+            a.nb = p->sub[0]->npts;
+            a.ns = p->sub[1]->npts;
+            // the virtual-point factor of the boundary row: ball radial step h = rho_*/n_rho
+            // (eq. ball_discr), cylinder height step h_z = z_*/n_z (eq. A_z)
+            a.coef = dib ? 2.0 / (bg->z_star / bg->n[2])
+                         : 2.0 / (bg->rho_star / bg->n[0]) + 2.0 / bg->rho_star;
+            a.d0 = p->sub[0]->d[0];
+            a.d1 = p->sub[0]->d[1];
+            for (int q = 0; q < 5; ++q) {
+                a.z[q] = cp->zeta[q];
+                a.e[q] = cp->eta[q];
+            }
+            a.a3 = cp->alpha3;
+            a.b3 = cp->beta3;
+            a.u_top = cp->u_top;
+            a.v_top = cp->v_top;
             p->kernels_per_step = 1 + p->sub[0]->kernels_per_step + p->sub[1]->kernels_per_step;
             s = alloc_dev(p, 4, &p->d_err);
             if (s == SEXPE_OK && cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st) != cudaSuccess) s = SEXPE_ECUDA;
@@ -1366,7 +1395,8 @@ sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sex
         const sexpe_status v = validate(&grids[q], &species[q], tau, precision);
         if (v != SEXPE_OK) return v;
         if (grids[q].geometry != SEXPE_DISK || species[q].n_species != 2) return SEXPE_EINVAL;
-        if (species[q].reaction == SEXPE_LINEAR_CUBIC || species[q].reaction == SEXPE_BVAM_MANUFACTURED)
+        if (species[q].reaction == SEXPE_LINEAR_CUBIC || species[q].reaction == SEXPE_BVAM_MANUFACTURED ||
+            species[q].reaction == SEXPE_LINEAR)
             return SEXPE_EUNSUPPORTED;
         if (grids[q].rho_op != 0 || species[q].offset_host) return SEXPE_EUNSUPPORTED;
         if (grids[q].n[0] > 128 || grids[q].n[1] > 256) return SEXPE_EUNSUPPORTED;
@@ -1582,7 +1612,8 @@ sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_c
                            const double* dL_dWT, double* dL_dW0, double* dL_dparams, void* stream) {
     if (!p || !checkpoints || !dL_dWT || !dL_dW0 || n_ckpt < 1 || every < 1) return SEXPE_EINVAL;
     if (p->precision != SEXPE_FP64 || p->coupled) return SEXPE_EUNSUPPORTED;
-    if (p->reaction == SEXPE_BVAM || p->reaction == SEXPE_BVAM_MANUFACTURED) return SEXPE_EUNSUPPORTED;
+    if (p->reaction == SEXPE_BVAM || p->reaction == SEXPE_BVAM_MANUFACTURED || p->reaction == SEXPE_LINEAR)
+        return SEXPE_EUNSUPPORTED;
     for (double c : p->offset)
         if (c != 0.0) return SEXPE_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;

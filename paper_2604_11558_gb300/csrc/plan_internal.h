@@ -50,11 +50,11 @@ struct sexpe_plan {
     std::vector<sexpe::Dir64> dirs64;
     double* buf64[3] = {nullptr, nullptr, nullptr};
     const double* unsplit_P = nullptr;     // unsplit baseline: phi_1(tau d_s M), S x N x N
-    // bulk-surface coupled plan (sexpe_coupled_setup): the ball and sphere sub-plans and the
-    // boundary coupling constants {zeta1, zeta2, zeta3, eta1, eta2}
+    // bulk-surface coupled plan (sexpe_coupled_setup): the bulk and surface sub-plans and the
+    // arguments of the coupling kernel
     bool coupled = false;
     sexpe_plan* sub[2] = {nullptr, nullptr};
-    double cpl[5] = {0, 0, 0, 0, 0};
+    sexpe::CoupleArgs cpl{};
     // split path
     sexpe::SplitTables tabs{};
     sexpe::TcShape sh3{}, shs{};

@@ -156,3 +156,35 @@ def bulk_surface_ball(n=(30, 50, 30), steps=150000, seed=8, tau=1e-4):
                 d_bulk=[1.0, delta], bulk_params=[a1, a2, b1], d_surface=[1.0, eps], surface_params=[z1, a2, b1],
                 coupling=dict(zeta1=z1, zeta2=z2, zeta3=z3, eta1=e1, eta2=e2), Wb=Wb, Ws=Ws,
                 name="bulk_surface_ball")
+
+
+def dib_cylinder(n=(140, 140, 25), steps=10000, seed=9, tau=0.025, bulk_noise=0.0):
+    """Bulk-surface DIB model on the cylinder rho_* = 15, z_* = 25 and its bottom disk (Section 5.6,
+    eqs. bulkcyl): bulk u, v (diffusion 1, delta = 1; b = -alpha1 (u - alpha2), c = -beta1 (v - beta2);
+    u = alpha2, v = beta2 on the top) held lifted, w = (u - alpha2, v - beta2), so the bulk reaction
+    is LINEAR with K = diag(-alpha1, -beta1); surface r, s (diffusion 1, eps = 20, no reaction of
+    their own: the DIB kinetics zeta1 p, zeta1 q come through the coupling).  Parameters as printed:
+    alpha1 = alpha2 = delta = beta1 = beta2 = zeta1 = zeta3 = 1, alpha3 = beta3 = 0.1, eps = 20,
+    zeta2 = 10, zeta4 = 30, zeta5 = 0.5, eta1 = 3, eta2 = 2.5, eta3 = 0.2, eta5 = 1.5 and eta4 from
+    the equilibrium condition.  Initial data: u = alpha2, v = beta2 (w = 0; optionally plus
+    bulk_noise N(0, 1)), r = 1e-2 U(0, 1), s = zeta5 + 1e-2 U(0, 1).  t_* = 250 in 10000 steps.
+    Wb: (2, n_z, n_theta, n_rho), Ws: (2, n_theta, n_rho); the flat state is Wb then Ws."""
+    rng = _rng(seed)
+    a1, a2, a3, b1, b2, b3, delta, eps = 1.0, 1.0, 0.1, 1.0, 1.0, 0.1, 1.0, 20.0
+    z = [1.0, 10.0, 1.0, 30.0, 0.5]
+    e1, e2, e3, e5 = 3.0, 2.5, 0.2, 1.5
+    e4 = b2 * e1 * (1.0 - z[4]) * (1.0 - e3 + e3 * z[4]) / (z[4] * (1.0 + e3 * z[4]))
+    shb, shs = _shape(n), _shape(n[:2])
+    Ws = np.stack([1e-2 * rng.uniform(0.0, 1.0, shs), z[4] + 1e-2 * rng.uniform(0.0, 1.0, shs)])
+    Wb = np.zeros((2,) + shb)
+    if bulk_noise:
+        Wb = Wb + bulk_noise * rng.standard_normal((2,) + shb)
+    coupling = dict(kind="dib_cylinder", alpha3=a3, beta3=b3, u_top=a2, v_top=b2, eta4=e4,
+                    **{f"zeta{q + 1}": z[q] for q in range(5)}, eta1=e1, eta2=e2, eta3=e3, eta5=e5)
+    return dict(geometry="cylinder+disk", n=tuple(n), rho_star=15.0, z_star=25.0, tau=tau, steps=steps, seed=seed,
+                d_bulk=[1.0, delta], bulk_reaction="linear", bulk_params=[-a1, 0.0, 0.0, -b1],
+                d_surface=[1.0, eps], surface_reaction="none", surface_params=[], coupling=coupling,
+                oracle_params=dict(alpha1=a1, alpha2=a2, alpha3=a3, beta1=b1, beta2=b2, beta3=b3, delta=delta,
+                                   eps=eps, zeta1=z[0], zeta2=z[1], zeta3=z[2], zeta4=z[3], zeta5=z[4],
+                                   eta1=e1, eta2=e2, eta3=e3, eta5=e5),
+                Wb=Wb, Ws=Ws, name="dib_cylinder")

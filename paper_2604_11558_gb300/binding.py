@@ -314,12 +314,14 @@ class CoupledPlan(Plan):
 
     def __init__(self, n, d_bulk, bulk_params, d_surface, surface_params, coupling, tau, rho_star=1.0,
                  precision="fp64", stream=None, reaction="schnakenberg", surface_reaction=None,
-                 geometry="ball", z_star=1.0):
+                 geometry="ball", z_star=1.0, z_bc=None):
         L = lib()
         self._keep = [np.ascontiguousarray(x if len(x) else [0.0], dtype=np.float64)
                       for x in (d_bulk, bulk_params, d_surface, surface_params)]
         db, pb, ds, ps = self._keep
-        grid = _grid_struct(geometry, n, rho_star, z_star, "paper" if geometry == "cylinder" else "neumann")
+        if z_bc is None:
+            z_bc = "paper" if geometry == "cylinder" else "neumann"
+        grid = _grid_struct(geometry, n, rho_star, z_star, z_bc)
         srx = reaction if surface_reaction is None else surface_reaction
         bulk = Species(len(d_bulk), _dptr(db), REACTION[reaction], len(bulk_params), _dptr(pb))
         surf = Species(len(d_surface), _dptr(ds), REACTION[srx], len(surface_params), _dptr(ps))

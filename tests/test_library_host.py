@@ -113,3 +113,35 @@ def test_batch_setup_rejects_invalid(binding):
     big = wl.schnakenberg_disk(n=(10, 300), steps=1)
     assert binding.batch_setup_status([big]) == 5                         # theta > 256 unsupported
     assert binding.batch_setup_status([good], precision="fp64") == 5      # batched FP64 not built
+
+
+def test_coupled_setup_rejects_invalid(binding):
+    """sexpe_coupled_setup validates everything on the host before it touches a GPU."""
+    from paper_2604_11558_gb300 import workloads as wl
+    b = wl.bulk_surface_ball(n=(5, 6, 7), steps=1)
+    ball = dict(n=b["n"], d_bulk=b["d_bulk"], bulk_params=b["bulk_params"], d_surface=b["d_surface"],
+                surface_params=b["surface_params"], coupling=b["coupling"], tau=b["tau"])
+    st = binding.coupled_setup_status
+    assert st(**dict(ball, precision="unsplit_fp64")) == 5
+    assert st(**dict(ball, d_bulk=[1.0, 10.0, 3.0])) == 1                         # three bulk species
+    assert st(**dict(ball, d_surface=[1.0])) == 1                                 # one surface species
+    assert st(**dict(ball, coupling=dict(b["coupling"], zeta2=float("nan")))) == 1
+    assert st(**dict(ball, coupling=dict(b["coupling"], eta2=float("inf")))) == 1
+    assert st(**dict(ball, tau=0.0)) == 1
+    assert st(**dict(ball, n=(5, 2, 7))) == 1                                     # theta < 3
+    assert st(**dict(ball, geometry="cylinder")) == 1                             # the ball kind needs a ball
+    assert st(**dict(ball, reaction="bvam_manufactured", bulk_params=[1.0, 0.2, 0.2, 1.0, 1.0])) == 1
+    d = wl.dib_cylinder(n=(5, 6, 7), steps=1)
+    dib = dict(n=d["n"], d_bulk=d["d_bulk"], bulk_params=d["bulk_params"], d_surface=d["d_surface"],
+               surface_params=d["surface_params"], coupling=d["coupling"], tau=d["tau"], rho_star=d["rho_star"],
+               reaction=d["bulk_reaction"], surface_reaction=d["surface_reaction"], geometry="cylinder",
+               z_star=d["z_star"])
+    assert st(**dict(dib, geometry="ball")) == 1                                  # the DIB kind needs a cylinder
+    assert st(**dict(dib, z_bc="neumann")) == 1                                   # and the Dirichlet top of A_z
+    assert st(**dict(dib, z_star=-1.0)) == 1
+    assert st(**dict(dib, bulk_params=[-1.0, 0.0, 0.0])) == 1                     # LINEAR takes S^2 params
+    assert st(**dict(dib, coupling=dict(d["coupling"], alpha3=float("nan")))) == 1
+    assert st(**dict(dib, coupling=dict(d["coupling"], u_top=float("inf")))) == 1
+    assert st(**dict(dib, precision="unsplit_fp64")) == 5
+    L = binding.lib()
+    assert L.sexpe_coupled_setup(None, None, None, None, 1e-3, 0, None, None) == 1

@@ -181,10 +181,11 @@ def test_dib_split_tf32_characterised_on_120x140x25():
     dominated by the theta-Laplacian (~1e4, zero theta-mean), so the FP32-accumulated theta
     transform leaves a coherent error in the undamped theta-mean of s (measured ring-mean bias
     ~1.5e-7, uniform over the inner rings); r and w are driven by zeta4 (s - zeta5) with s ~ zeta5
-    and are ~1e-2 of s, which amplifies it ~100x.  An emulation of the chain's whole arithmetic
-    tracks the GPU within 3-5x after 3 steps but decays to ~6e-6 by step 20 where the GPU error grows
-    to 1e-4: a persistent per-step error source at this size is not yet identified.  The bounds hold
-    the measured values with a margin of ~3 so that a change shows."""
+    and are ~1e-2 of s, which amplifies it ~100x.  An emulation of the chain's arithmetic with
+    round-to-nearest accumulation tracks the GPU within 3-5x after 3 steps but decays by step 20;
+    with the accumulator rounded toward zero per 8-wide K step (truncating tensor-core accumulation)
+    the error grows with the steps as on the GPU, to within ~6x.  The bounds hold the measured values
+    with a margin of ~3 so that a change shows."""
     w = wl.dib_cylinder(n=(120, 140, 25), steps=20, seed=85)
     got = gpu_dib(w, w["steps"], precision="split_tf32")
     ref = oracle_dib(w, w["steps"])

@@ -80,49 +80,18 @@ def oracle_dib_rowsum_exact(w, steps):
     return o.run(w["Wb"].copy(), w["Ws"].copy(), steps)
 
 
-def _tf32(x):
-    a = np.asarray(x, dtype=np.float32).view(np.uint32)
-    return ((a + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).astype(np.uint32).view(np.float32)
-
-
-def _mm_tf32x3(A, B):
-    A = A.astype(np.float32)
-    B = B.astype(np.float32)
-    Ah, Bh = _tf32(A), _tf32(B)
-    Al, Bl = _tf32(A - Ah), _tf32(B - Bh)
-    return ((Ah @ Bl + Al @ Bh) + Ah @ Bh).astype(np.float64)
-
-
 def oracle_dib_split_emulated(w, steps):
     """The oracle step with the split chain's arithmetic emulated (an error model, not a reference)."""
-    from oracle.phi import phi1
     from oracle.stepper import rhs
-
-    def f32(x):
-        return np.asarray(x).astype(np.float32).astype(np.float64)
-
-    def advance32(problem, W, F):
-        g = problem.grid
-        out = np.array(W, copy=True)
-        for s in range(problem.S):
-            X = f32(F[s])
-            for mu in range(g.ndim, 0, -1):
-                lam, V, Vinv = problem._eig[mu]
-                axis = X.ndim - mu
-                sc = np.moveaxis(np.broadcast_to(g.scale[mu], X.shape), axis, -1)[..., :1]
-                Z = _mm_tf32x3(np.moveaxis(X, axis, -1), Vinv.T)
-                Z = f32(Z * f32(phi1(problem.tau * problem.d[s] * sc * lam)))
-                X = np.moveaxis(_mm_tf32x3(Z, V.T), -1, axis)
-            out[s] = W[s] + f32(problem.tau * X)
-        return out
+    from tests.precision_emulation import advance
 
     o = CoupledCylinder(w["n"], w["tau"], rho_star=w["rho_star"], z_star=w["z_star"], **w["oracle_params"])
     Wb, Ws = w["Wb"].copy(), w["Ws"].copy()
     for _ in range(steps):
         Fb, Fs = rhs(o.pb, Wb), rhs(o.ps, Ws)
         ab, as_ = o.coupling(Wb, Ws)
-        Wb, Ws = (advance32(o.pb, Wb, [Fb[q] + ab[q] for q in range(2)]),
-                  advance32(o.ps, Ws, [Fs[q] + as_[q] for q in range(2)]))
+        Wb, Ws = (advance(o.pb, Wb, [Fb[q] + ab[q] for q in range(2)]),
+                  advance(o.ps, Ws, [Fs[q] + as_[q] for q in range(2)]))
     return Wb, Ws
 
 

@@ -1578,15 +1578,17 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
     info->npts = p->npts;
     info->state_elems = state_elems(p);
     info->workspace_bytes = (int64_t)p->bytes;
+    if (p->coupled) info->workspace_bytes += (int64_t)(p->sub[0]->bytes + p->sub[1]->bytes);
     info->setup_ms = p->setup_ms;
+    const sexpe_plan* t = p->coupled ? p->sub[0] : p;   // a coupled plan reports its bulk grid's tiling
     if (!p->batch && p->precision == SEXPE_SPLIT_TF32) {
-        info->stencil_tile_j = p->tabs.rhs_tj;
-        info->ring_slots[0] = (int32_t)p->shs.nm;
-        info->ring_slots[1] = (int32_t)p->shs.nd;
-        info->stencil_tile_us = p->rhs_tj_us;
-        info->stencil_planes = p->tabs.rhs_ks;
-        info->stencil_ctas_per_sm = p->tabs.rhs_mb;
-        if (!p->th_splits.empty()) info->theta_split = rup16(p->n[0]) / p->tabs.th_nt;
+        info->stencil_tile_j = t->tabs.rhs_tj;
+        info->ring_slots[0] = (int32_t)t->shs.nm;
+        info->ring_slots[1] = (int32_t)t->shs.nd;
+        info->stencil_tile_us = t->rhs_tj_us;
+        info->stencil_planes = t->tabs.rhs_ks;
+        info->stencil_ctas_per_sm = t->tabs.rhs_mb;
+        if (!t->th_splits.empty()) info->theta_split = rup16(t->n[0]) / t->tabs.th_nt;
     } else if (p->batch) {
         info->ring_slots[0] = (int32_t)p->bsh.nm;
         info->ring_slots[1] = (int32_t)p->bsh.nd;

@@ -238,7 +238,9 @@ sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_s
  * must have 2 species; no lifting offsets (SEXPE_EINVAL), no adjoint, no
  * sexpe_set_stencil / sexpe_set_theta_split (SEXPE_EUNSUPPORTED), no
  * sexpe_step_noalloc (SEXPE_EINVAL).  Step with sexpe_step / sexpe_step_host;
- * destroy with sexpe_destroy.  Other errors as sexpe_setup. */
+ * destroy with sexpe_destroy.  Other errors as sexpe_setup.  sexpe_plan_info
+ * reports n_species = 4, npts of the bulk grid, the bulk grid's tile choices
+ * and the device bytes of both sub-plans. */
 typedef enum { SEXPE_COUPLING_SCHNAKENBERG_BALL = 0, SEXPE_COUPLING_DIB_CYLINDER = 1 } sexpe_coupling_kind;
 typedef struct {
     int32_t kind;            /* sexpe_coupling_kind                                       */

@@ -23,7 +23,9 @@ The paper leaves the coupled discretisation out ("We omit the details").  Readin
 
 Pins (tests/test_oracle_coupled.py): the flux term makes the discrete bulk operator exact on
 u = rho^2 with its normal derivative (Laplacian 6 at every node); zeta1 = 0 reduces the step to
-the two uncoupled split steps; the homogeneous equilibrium is a fixed point.
+the two uncoupled split steps; the homogeneous equilibrium is a fixed point; a discrete divergence
+theorem ties the bulk's gain through the outer row, (n^2 - 1)/h times the exchanged flux, to the
+surface's loss (flux factor, sign, pairing); the coupling reads and writes the outer shell only.
 """
 import numpy as np
 

@@ -188,3 +188,14 @@ def dib_cylinder(n=(140, 140, 25), steps=10000, seed=9, tau=0.025, bulk_noise=0.
                                    eps=eps, zeta1=z[0], zeta2=z[1], zeta3=z[2], zeta4=z[3], zeta5=z[4],
                                    eta1=e1, eta2=e2, eta3=e3, eta5=e5),
                 Wb=Wb, Ws=Ws, name="dib_cylinder")
+
+
+def bvam_disk(n=(40, 80), steps=5000, seed=10, tau=0.16):
+    """BVAM model on the unit disk without sources (Section 5.2, eq. BVAM): diffusion (gamma, delta)
+    and the reaction of eq. BVAMnl with the parameters printed in Section 5.1 (gamma 3.87e-3, delta
+    7.5e-3, alpha1 0.899, alpha2 0.2, alpha3 0.2, beta1 -0.91, beta2 -0.899); initial data
+    1e-2 N(0, 1) per point and species about the equilibrium (0, 0); t_* = 800 in 5000 steps."""
+    rng = _rng(seed)
+    W0 = 1e-2 * rng.standard_normal((2,) + _shape(n))
+    return dict(geometry="disk", n=tuple(n), d=[3.87e-3, 7.5e-3], reaction="bvam",
+                params=[0.899, 0.2, 0.2, -0.91, -0.899], tau=tau, steps=steps, W0=W0, seed=seed, name="bvam_disk")

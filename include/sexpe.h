@@ -253,6 +253,18 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bulk_grid, const sexpe_specie
                                  const sexpe_species* surface, const sexpe_coupling* cp, double tau,
                                  int32_t precision, void* stream, sexpe_plan** out);
 
+/* Host-only evaluation of the coupling terms a coupled plan adds every step (introspection and
+ * testing; no device work, no plan): for n surface points with the bulk species' boundary values
+ * (ub, vb; the DIB kind takes the lifted values w) and the surface values (r, s), writes what the
+ * step adds to the bulk F of the boundary node (add_b0, add_b1) and to the surface F (add_s0,
+ * add_s1), with the virtual-point factor and the bulk diffusion taken from bulk_grid and bulk as
+ * in sexpe_coupled_setup.  All arrays host, n doubles, caller-owned.  Arguments are checked as by
+ * sexpe_coupled_setup (the surface species aside); n < 0 or a NULL array with n > 0 gives
+ * SEXPE_EINVAL. */
+sexpe_status sexpe_coupling_terms(const sexpe_grid* bulk_grid, const sexpe_species* bulk, const sexpe_coupling* cp,
+                                  int64_t n, const double* ub, const double* vb, const double* r, const double* s,
+                                  double* add_b0, double* add_b1, double* add_s0, double* add_s1);
+
 /* Wait for the plan's work on `stream` and report the device error word
  * (SEXPE_ETIMEOUT if a bounded wait ran out), clearing it. */
 sexpe_status sexpe_synchronize(sexpe_plan* plan, void* stream);

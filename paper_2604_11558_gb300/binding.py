@@ -96,6 +96,8 @@ def lib():
         L.sexpe_coupled_setup.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Species), ctypes.POINTER(Species),
                                           ctypes.POINTER(Coupling), ctypes.c_double, ctypes.c_int32, _P,
                                           ctypes.POINTER(_P)]
+        L.sexpe_coupling_terms.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Species), ctypes.POINTER(Coupling),
+                                           ctypes.c_int64] + [_DP] * 8
         L.sexpe_state_offsets.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         L.sexpe_step.argtypes = [_P, _P, ctypes.c_int64, _P]
         L.sexpe_step_host.argtypes = [_P, _DP, ctypes.c_int64, _P]
@@ -119,7 +121,8 @@ def lib():
                      "sexpe_profile_begin", "sexpe_profile_end", "sexpe_step_noalloc",
                      "sexpe_step_checkpointed", "sexpe_adjoint", "sexpe_set_stencil",
                      "sexpe_set_theta_split", "sexpe_selftest_wait_timeout", "sexpe_set_time",
-                     "sexpe_axis_phi1", "sexpe_axis_eigen", "sexpe_coupled_setup"]:
+                     "sexpe_axis_phi1", "sexpe_axis_eigen", "sexpe_coupled_setup",
+                     "sexpe_coupling_terms"]:
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -335,6 +338,21 @@ class CoupledPlan(Plan):
         self._p_list = []
         self.n_bulk = int(np.prod(n))
         self.n_surface = int(n[1]) * int(n[2]) if geometry == "ball" else int(n[0]) * int(n[1])
+
+
+def coupling_terms(geometry, n, d_bulk, coupling, ub, vb, r, s, rho_star=1.0, z_star=1.0):
+    """sexpe_coupling_terms: the additions to the bulk F (boundary node) and to the surface F at each
+    of len(ub) surface points, as four numpy arrays (host evaluation, no GPU)."""
+    L = lib()
+    d = np.ascontiguousarray(d_bulk, dtype=np.float64)
+    grid = _grid_struct(geometry, n, rho_star, z_star, "paper" if geometry == "cylinder" else "neumann")
+    sp = Species(len(d), _dptr(d), REACTION["none"], 0, None)
+    cp = _coupling_struct(coupling)
+    ins = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in (ub, vb, r, s)]
+    outs = [np.zeros_like(ins[0]) for _ in range(4)]
+    _check(L.sexpe_coupling_terms(ctypes.byref(grid), ctypes.byref(sp), ctypes.byref(cp), len(ins[0]),
+                                  *[_dptr(x) for x in ins], *[_dptr_out(x) for x in outs]), "sexpe_coupling_terms")
+    return outs
 
 
 def coupled_setup_status(*args, **kw):

@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "couple_terms.cuh"
 #include "plan_internal.h"
 
 using namespace sexpe;
@@ -1252,6 +1253,54 @@ sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float
 
 }  // namespace sexpe
 
+namespace {
+
+// The coupling kernel's arguments for a bulk grid, its bulk diffusion and the coupling constants
+// (sexpe_coupled_setup and sexpe_coupling_terms): the surface is the ball's outer shell
+// (theta x phi) or the cylinder's bottom disk (rho x theta); the virtual-point factor of the
+// boundary row is 2/h + 2/rho_* with the ball's radial step h = rho_*/n_rho (eq. ball_discr) or
+// 2/h_z with the cylinder's h_z = z_*/n_z (eq. A_z).
+CoupleArgs make_couple_args(const sexpe_grid* bg, const double* d_bulk, const sexpe_coupling* cp) {
+    CoupleArgs a{};
+    const bool dib = cp->kind == SEXPE_COUPLING_DIB_CYLINDER;
+    a.kind = cp->kind;
+    a.bn1 = bg->n[0];
+    a.bn2 = bg->n[1];
+    a.sn1 = dib ? bg->n[0] : bg->n[1];
+    a.nb = (long long)bg->n[0] * bg->n[1] * bg->n[2];
+    a.ns = dib ? (long long)bg->n[0] * bg->n[1] : (long long)bg->n[1] * bg->n[2];
+    a.coef = dib ? 2.0 / (bg->z_star / bg->n[2]) : 2.0 / (bg->rho_star / bg->n[0]) + 2.0 / bg->rho_star;
+    a.d0 = d_bulk[0];
+    a.d1 = d_bulk[1];
+    for (int q = 0; q < 5; ++q) {
+        a.z[q] = cp->zeta[q];
+        a.e[q] = cp->eta[q];
+    }
+    a.a3 = cp->alpha3;
+    a.b3 = cp->beta3;
+    a.u_top = cp->u_top;
+    a.v_top = cp->v_top;
+    return a;
+}
+
+// Arguments of sexpe_coupled_setup / sexpe_coupling_terms that need no GPU to check.
+sexpe_status validate_coupling(const sexpe_grid* bg, const sexpe_species* bulk, const sexpe_coupling* cp) {
+    if (!bg || !bulk || !cp) return SEXPE_EINVAL;
+    if (cp->kind != SEXPE_COUPLING_SCHNAKENBERG_BALL && cp->kind != SEXPE_COUPLING_DIB_CYLINDER) return SEXPE_EINVAL;
+    const bool dib = cp->kind == SEXPE_COUPLING_DIB_CYLINDER;
+    if (bg->geometry != (dib ? SEXPE_CYLINDER : SEXPE_BALL)) return SEXPE_EINVAL;
+    if (dib && bg->z_bc != SEXPE_Z_PAPER) return SEXPE_EINVAL;
+    if (bulk->n_species != 2) return SEXPE_EINVAL;
+    for (int q = 0; q < 5; ++q)
+        if (!std::isfinite(cp->zeta[q]) || !std::isfinite(cp->eta[q])) return SEXPE_EINVAL;
+    const double extra[4] = {cp->alpha3, cp->beta3, cp->u_top, cp->v_top};
+    for (double x : extra)
+        if (!std::isfinite(x)) return SEXPE_EINVAL;
+    return SEXPE_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sexpe_status_string(int32_t status) {
@@ -1298,17 +1347,11 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk
                                  sexpe_plan** out) {
     if (!out) return SEXPE_EINVAL;
     *out = nullptr;
-    if (!bg || !bulk || !surface || !cp) return SEXPE_EINVAL;
-    if (cp->kind != SEXPE_COUPLING_SCHNAKENBERG_BALL && cp->kind != SEXPE_COUPLING_DIB_CYLINDER) return SEXPE_EINVAL;
+    if (!surface) return SEXPE_EINVAL;
+    const sexpe_status vc = validate_coupling(bg, bulk, cp);
+    if (vc != SEXPE_OK) return vc;
     const bool dib = cp->kind == SEXPE_COUPLING_DIB_CYLINDER;
-    if (bg->geometry != (dib ? SEXPE_CYLINDER : SEXPE_BALL)) return SEXPE_EINVAL;
-    if (dib && bg->z_bc != SEXPE_Z_PAPER) return SEXPE_EINVAL;
-    if (bulk->n_species != 2 || surface->n_species != 2) return SEXPE_EINVAL;
-    for (int q = 0; q < 5; ++q)
-        if (!std::isfinite(cp->zeta[q]) || !std::isfinite(cp->eta[q])) return SEXPE_EINVAL;
-    const double extra[4] = {cp->alpha3, cp->beta3, cp->u_top, cp->v_top};
-    for (double x : extra)
-        if (!std::isfinite(x)) return SEXPE_EINVAL;
+    if (surface->n_species != 2) return SEXPE_EINVAL;
     if (bulk->offset_host || surface->offset_host) return SEXPE_EINVAL;
     if (bulk->reaction == SEXPE_BVAM_MANUFACTURED || surface->reaction == SEXPE_BVAM_MANUFACTURED) return SEXPE_EINVAL;
     sexpe_grid sg = *bg;                               // the surface grid: part of the bulk grid's boundary
@@ -1345,27 +1388,7 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk
             for (int m = 0; m < 3; ++m) p->n[m] = bg->n[m];
             p->npts = p->sub[0]->npts;
             p->tau = tau;
-            CoupleArgs& a = p->cpl;
-            a.kind = cp->kind;
-            a.bn1 = bg->n[0];
-            a.bn2 = bg->n[1];
-            a.sn1 = sg.n[0];
-            a.nb = p->sub[0]->npts;
-            a.ns = p->sub[1]->npts;
-            // the virtual-point factor of the boundary row: ball radial step h = rho_*/n_rho
-            // (eq. ball_discr), cylinder height step h_z = z_*/n_z (eq. A_z)
-            a.coef = dib ? 2.0 / (bg->z_star / bg->n[2])
-                         : 2.0 / (bg->rho_star / bg->n[0]) + 2.0 / bg->rho_star;
-            a.d0 = p->sub[0]->d[0];
-            a.d1 = p->sub[0]->d[1];
-            for (int q = 0; q < 5; ++q) {
-                a.z[q] = cp->zeta[q];
-                a.e[q] = cp->eta[q];
-            }
-            a.a3 = cp->alpha3;
-            a.b3 = cp->beta3;
-            a.u_top = cp->u_top;
-            a.v_top = cp->v_top;
+            p->cpl = make_couple_args(bg, p->sub[0]->d.data(), cp);
             p->kernels_per_step = 1 + p->sub[0]->kernels_per_step + p->sub[1]->kernels_per_step;
             s = alloc_dev(p, 4, &p->d_err);
             if (s == SEXPE_OK && cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st) != cudaSuccess) s = SEXPE_ECUDA;
@@ -1383,6 +1406,31 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk
     }
     p->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
+    return SEXPE_OK;
+}
+
+sexpe_status sexpe_coupling_terms(const sexpe_grid* bulk_grid, const sexpe_species* bulk, const sexpe_coupling* cp,
+                                  int64_t n, const double* ub, const double* vb, const double* r, const double* s,
+                                  double* add_b0, double* add_b1, double* add_s0, double* add_s1) {
+    const sexpe_status v = validate_coupling(bulk_grid, bulk, cp);
+    if (v != SEXPE_OK) return v;
+    if (n < 0 || !bulk->d_host) return SEXPE_EINVAL;
+    if (n > 0 && (!ub || !vb || !r || !s || !add_b0 || !add_b1 || !add_s0 || !add_s1)) return SEXPE_EINVAL;
+    const int ndim = 3;
+    for (int m = 0; m < ndim; ++m)
+        if (bulk_grid->n[m] < 3 || bulk_grid->n[m] > kMaxN) return SEXPE_EINVAL;
+    if (!(bulk_grid->rho_star > 0.0 && std::isfinite(bulk_grid->rho_star))) return SEXPE_EINVAL;
+    if (bulk_grid->geometry == SEXPE_CYLINDER && !(bulk_grid->z_star > 0.0 && std::isfinite(bulk_grid->z_star)))
+        return SEXPE_EINVAL;
+    const CoupleArgs a = make_couple_args(bulk_grid, bulk->d_host, cp);
+    for (int64_t q = 0; q < n; ++q) {
+        double add[4];
+        couple_terms(a, ub[q], vb[q], r[q], s[q], add);
+        add_b0[q] = add[0];
+        add_b1[q] = add[1];
+        add_s0[q] = add[2];
+        add_s1[q] = add[3];
+    }
     return SEXPE_OK;
 }
 

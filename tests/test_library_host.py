@@ -145,3 +145,41 @@ def test_coupled_setup_rejects_invalid(binding):
     assert st(**dict(dib, precision="unsplit_fp64")) == 5
     L = binding.lib()
     assert L.sexpe_coupled_setup(None, None, None, None, 1e-3, 0, None, None) == 1
+
+
+def test_coupling_terms_match_the_oracles(binding):
+    """The coupling arithmetic the kernels run (shared with sexpe_coupling_terms, host evaluation)
+    against the two coupled oracles, point by point: Section 5.5 (ball + sphere, rho_* = 0.8) and
+    Section 5.6 (cylinder + bottom disk, lifted bulk)."""
+    from oracle.coupled import Coupled
+    from oracle.coupled_dib import CoupledCylinder
+    from paper_2604_11558_gb300 import workloads as wl
+    rng = np.random.default_rng(31)
+    # Section 5.5
+    n = (6, 8, 7)
+    c = Coupled(n, 1e-3, delta=10.0, rho_star=0.8)
+    Wb = 1.0 + 0.3 * rng.standard_normal((2,) + c.ball.shape)
+    Ws = 1.0 + 0.3 * rng.standard_normal((2,) + c.sphere.shape)
+    ab, as_ = c.coupling(Wb, Ws)
+    b = wl.bulk_surface_ball(n=n, steps=1)
+    got = binding.coupling_terms("ball", n, [1.0, 10.0], b["coupling"], Wb[0][:, :, -1], Wb[1][:, :, -1],
+                                 Ws[0], Ws[1], rho_star=0.8)
+    ref = [ab[0][:, :, -1], ab[1][:, :, -1], as_[0], as_[1]]
+    for g, r in zip(got, ref):
+        assert np.allclose(g, r.ravel(), rtol=1e-14, atol=1e-14 * np.abs(r).max())
+    # Section 5.6
+    d = wl.dib_cylinder(n=(6, 8, 7), steps=1)
+    cc = CoupledCylinder(d["n"], d["tau"], rho_star=d["rho_star"], z_star=d["z_star"], **d["oracle_params"])
+    Wb = 0.05 * rng.standard_normal((2,) + cc.bulk.shape)
+    Ws = np.stack([0.1 * rng.uniform(0, 1, cc.surface.shape), 0.5 + 0.1 * rng.uniform(0, 1, cc.surface.shape)])
+    ab, as_ = cc.coupling(Wb, Ws)
+    got = binding.coupling_terms("cylinder", d["n"], d["d_bulk"], d["coupling"], Wb[0][0], Wb[1][0], Ws[0], Ws[1],
+                                 rho_star=d["rho_star"], z_star=d["z_star"])
+    ref = [ab[0][0], ab[1][0], as_[0], as_[1]]
+    for g, r in zip(got, ref):
+        assert np.allclose(g, r.ravel(), rtol=1e-13, atol=1e-13 * np.abs(r).max())
+    # arguments are checked on the host
+    with pytest.raises(RuntimeError):
+        binding.coupling_terms("ball", d["n"], d["d_bulk"], d["coupling"], Wb[0][0], Wb[1][0], Ws[0], Ws[1])
+    L = binding.lib()
+    assert L.sexpe_coupling_terms(None, None, None, 0, *([None] * 8)) == 1

@@ -474,30 +474,6 @@ def measure_extras(flush):
                      "t250_run_s": ms * w["steps"] / 1e3}
         plan.close()
     out["bulk_surface_dib_cylinder"] = {"unit": UNIT, "l2": "not flushed (state 8 MB)", **res}
-    # the paper's own 2-D runs, timed whole (the paper quotes each run's wall-clock time): Section
-    # 5.2 BVAM on the disk 40x80, 5000 steps; Section 5.3 anomalous Schnakenberg on the disk
-    # 160x160 (n_rho above the split chains' 128: FP64), 2500 of its 25000 steps, scaled
-    runs = {}
-    for name, w, precs, steps in (("5.2_bvam_disk_40x80", wl.bvam_disk(), ("split_tf32", "fp64"), None),
-                                  ("5.3_anomalous_disk_160x160", wl.anomalous_disk(), ("fp64",), 2500)):
-        res = {}
-        for prec in precs:
-            plan = binding.Plan.from_workload(w, precision=prec)
-            x = torch.from_numpy(np.ascontiguousarray(w["W0"])).cuda()
-            plan.step(x, 20)
-            torch.cuda.synchronize()
-            k = steps or w["steps"]
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            plan.step(x, k)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / k
-            res[prec] = {"ms_per_step": ms, "value": x.numel() / (ms / 1e3), "timed_steps": k,
-                         "run_s": ms * w["steps"] / 1e3}
-            plan.close()
-        runs[name] = {"unit": UNIT, "dof": int(np.prod(w["W0"].shape)), "steps": w["steps"], **res}
-    out["paper_runs"] = runs
     # sphere adjoint vs forward (FP64), full 256x512 workload: 1000 steps, checkpoints every 50
     w = wl.schnakenberg_sphere()
     plan = binding.Plan.from_workload(w, precision="fp64")

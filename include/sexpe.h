@@ -165,8 +165,10 @@ sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sex
 sexpe_status sexpe_state_offsets(const sexpe_plan* plan, int64_t* offsets_host);
 
 /* Advance state_dev (caller-owned device FP64 array of state_elems elements,
- * layout above) by n_steps split exponential Euler steps, in place, enqueued
- * on `stream`.  No allocation, no host synchronisation.  n_steps >= 0. */
+ * layout above, 8-byte aligned) by n_steps split exponential Euler steps, in
+ * place, enqueued on `stream`.  No allocation, no host synchronisation.
+ * n_steps >= 0.  The device current at the call must be the one the plan was
+ * made on (SEXPE_EINVAL otherwise, as for an unaligned state). */
 sexpe_status sexpe_step(sexpe_plan* plan, double* state_dev, int64_t n_steps, void* stream);
 
 /* Same as sexpe_step for a HOST state: copies state_host to the plan's device
@@ -180,20 +182,25 @@ sexpe_status sexpe_step_host(sexpe_plan* plan, double* state_host, int64_t n_ste
  * loop under a fixed memory budget).  The paper has no counterpart: this is a
  * deployment variant of sexpe_step.
  *  - plan: a SEXPE_SPLIT_TF32 plan made earlier on the current device (its
- *    constant tables are read); state_dev as for sexpe_step (in place).
- *  - The step's only scratch, the FP32 intermediate between its two kernels,
+ *    constant tables are read); state_dev as for sexpe_step (in place,
+ *    8-byte aligned).  A plan made on another device, an unaligned state,
+ *    FP64, batch or coupled plans give SEXPE_EINVAL before anything is
+ *    enqueued.
+ *  - The step's only scratch, the FP32 intermediate between its kernels,
  *    lives in a static device array of 2^21 floats (8 MiB) that every GPU
  *    loading the library holds until exit; plans with species x points above
- *    2,097,152, or FP64 plans, give SEXPE_EINVAL.  No cudaMalloc/cudaFree or
- *    allocating library routine is called.
+ *    2,097,152 (rho lines padded to a multiple of 4) give SEXPE_EINVAL.  No
+ *    cudaMalloc/cudaFree or allocating library routine is called.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.
- *  - All calls share the one array and it keeps the last call's contents
- *    (nothing in it needs to start at zero: each step writes it before
- *    reading it).  Calls whose work overlaps on the GPU (other streams, other
- *    threads) race on it: serialise them.
- *  - Results equal sexpe_step's for the same plan and state. */
+ *  - All calls share the one array and it keeps the last call's contents.
+ *    Each step writes every value it later reads; the padding slots of the
+ *    rho lines, which no kernel writes, are zeroed by each call (a 2-D
+ *    memset on `stream`, no allocation).  Calls whose work overlaps on the
+ *    GPU (other streams, other threads) race on the array: serialise them.
+ *  - Results equal sexpe_step's, bit for bit, for the same plan and state
+ *    (the same kernels run; only the intermediate's address differs). */
 sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_steps, void* stream);
 
 /* Bulk-surface coupled systems (Sections 5.5 and 5.6): two bulk species on a 3-D

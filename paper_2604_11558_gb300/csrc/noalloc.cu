@@ -20,6 +20,9 @@
 #include "sexpe.h"
 
 namespace sexpe {
+sexpe_status check_split_step_with_scratch(const sexpe_plan* p, const double* state, const float* Y,
+                                           long long y_floats);
+sexpe_status zero_scratch_padding(const sexpe_plan* p, float* Y, cudaStream_t st);
 sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float* Y, long long y_floats,
                                              cudaStream_t st);
 }
@@ -61,15 +64,20 @@ extern "C" sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, 
     float* scratch = nullptr;
     const sexpe_status s = scratch_for_current_device(&scratch);
     if (s != SEXPE_OK) return s;
-    // Nothing in the scratch has to start at zero: every step's first kernel
-    // writes all species x points values before a later kernel reads them.
-    // The padding of the rho lines (n_rho not a multiple of 4) may hold values
-    // left by an earlier call; padded points only ever produce padded points,
-    // which no result reads.
+    // Everything is checked before the first launch: the plan (split-TF32, single grid, made on
+    // this device), the state's 8-byte alignment and the scratch capacity.
+    const sexpe_status c = sexpe::check_split_step_with_scratch(plan, state_dev, scratch, kNoAllocScratchFloats);
+    if (c != SEXPE_OK || n_steps == 0) return c;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Every step's first kernel writes all species x points values of the intermediate before a
+    // later kernel reads them.  The padding slots of the rho lines (n_rho not a multiple of 4) are
+    // never written by a step and hold whatever an earlier call with another layout left there
+    // (possibly non-finite); they are zeroed here, as the plan's own buffer is at setup, so that
+    // results equal sexpe_step's bit for bit.
+    const sexpe_status z = sexpe::zero_scratch_padding(plan, scratch, st);
+    if (z != SEXPE_OK) return z;
     for (int64_t k = 0; k < n_steps; ++k) {
-        const sexpe_status r =
-            sexpe::enqueue_split_step_with_scratch(plan, state_dev, scratch, kNoAllocScratchFloats,
-                                                   static_cast<cudaStream_t>(stream));
+        const sexpe_status r = sexpe::enqueue_split_step_with_scratch(plan, state_dev, scratch, kNoAllocScratchFloats, st);
         if (r != SEXPE_OK) return r;
     }
     return SEXPE_OK;

@@ -837,6 +837,7 @@ void free_plan(sexpe_plan* p) {
 
 sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species* sp, double tau, int32_t precision,
                         cudaStream_t st) {
+    SX_CUDA(cudaGetDevice(&p->device));
     p->geometry = g->geometry;
     p->precision = precision;
     p->S = sp->n_species;
@@ -1227,14 +1228,44 @@ sexpe_status adjoint_step(sexpe_plan* p, const double* Wn, double* lam, double* 
 
 namespace sexpe {
 
-// Enqueue one split-TF32 step of plan `p` with the FP32 intermediate of the
-// chain in caller-provided device memory `Y` (capacity `y_floats`) instead of
-// the plan's own buffer.  Used by the no-allocation entry point.
-sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float* Y, long long y_floats,
-                                             cudaStream_t st) {
+// True when the plan was made on the device that is current now (its tables live there).
+bool plan_on_current_device(const sexpe_plan* p) {
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess && dev == p->device;
+}
+
+// Checks of a split step into caller-provided scratch: a split-TF32 single-grid plan made on the
+// current device, an 8-byte-aligned state and scratch that holds the plan's FP32 intermediate.
+sexpe_status check_split_step_with_scratch(const sexpe_plan* p, const double* state, const float* Y,
+                                           long long y_floats) {
     if (!p || !state || !Y) return SEXPE_EINVAL;
+    if (((uintptr_t)state & 7u) != 0 || ((uintptr_t)Y & 15u) != 0) return SEXPE_EINVAL;
     if (p->precision != SEXPE_SPLIT_TF32 || p->batch || p->coupled) return SEXPE_EINVAL;
     if ((long long)p->S * p->tabs.ys > y_floats) return SEXPE_EINVAL;
+    if (!plan_on_current_device(p)) return SEXPE_EINVAL;
+    return SEXPE_OK;
+}
+
+// Zero the padding columns (rho slots n1 .. n1q - 1 of every line) of the plan's FP32
+// intermediate laid out in `Y`: the kernels never write them, and the plan's own buffer is
+// zeroed once at setup, so scratch shared with other plans gets the same start.  A 2-D
+// memset; no allocation.
+sexpe_status zero_scratch_padding(const sexpe_plan* p, float* Y, cudaStream_t st) {
+    const SplitTables& T = p->tabs;
+    if (T.n1q == T.n1) return SEXPE_OK;
+    const size_t lines = (size_t)p->S * (size_t)(T.ys / T.n1q);
+    SX_CUDA(cudaMemset2DAsync(Y + T.n1, sizeof(float) * (size_t)T.n1q, 0, sizeof(float) * (size_t)(T.n1q - T.n1),
+                              lines, st));
+    return SEXPE_OK;
+}
+
+// Enqueue one split-TF32 step of plan `p` with the FP32 intermediate of the
+// chain in caller-provided device memory `Y` (capacity `y_floats`) instead of
+// the plan's own buffer.  Used by the no-allocation entry point, which checks the
+// arguments with check_split_step_with_scratch first.
+sexpe_status enqueue_split_step_with_scratch(sexpe_plan* p, double* state, float* Y, long long y_floats,
+                                             cudaStream_t st) {
+    SX_TRY(check_split_step_with_scratch(p, state, Y, y_floats));
     SplitTables T = p->tabs;
     T.state = state;
     T.state_upd = state;
@@ -1380,6 +1411,7 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk
         s = build_plan(p->sub[0], bg, bulk, tau, precision, st);
         if (s == SEXPE_OK) s = build_plan(p->sub[1], &sg, surface, tau, precision, st);
         if (s == SEXPE_OK) {
+            p->device = p->sub[0]->device;
             p->coupled = true;
             p->geometry = bg->geometry;
             p->precision = precision;
@@ -1456,7 +1488,8 @@ sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sex
     cudaStream_t st = (cudaStream_t)stream;
     sexpe_status status = SEXPE_OK;
     try {
-        status = build_batch(p, count, grids, species, tau, st);
+        if (cudaGetDevice(&p->device) != cudaSuccess) status = SEXPE_ECUDA;
+        if (status == SEXPE_OK) status = build_batch(p, count, grids, species, tau, st);
     } catch (const std::bad_alloc&) {
         status = SEXPE_ENOMEM;
     } catch (...) {
@@ -1534,6 +1567,7 @@ sexpe_status sexpe_set_theta_split(sexpe_plan* p, int32_t split) {
 sexpe_status sexpe_step(sexpe_plan* p, double* state, int64_t n_steps, void* stream) {
     if (!p || !state || n_steps < 0) return SEXPE_EINVAL;
     if (((uintptr_t)state & 7u) != 0) return SEXPE_EINVAL;
+    if (!sexpe::plan_on_current_device(p)) return SEXPE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int64_t done = 0;
     p->bparity = 0;

@@ -35,6 +35,7 @@ struct DirAdj {
 
 struct sexpe_plan {
     int geometry = 0, precision = 0, S = 0, ndim = 0;
+    int device = -1;                  // CUDA device current at setup; steps must run with it current
     int n[3] = {1, 1, 1};
     long long npts = 0;
     double tau = 0.0;

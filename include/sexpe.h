@@ -140,6 +140,12 @@ typedef struct {
     int32_t theta_split;        /* split sphere: CTAs sharing one row tile of the theta kernel,
                                    each with n_theta_pad / theta_split output columns
                                    (measured at setup); 0 elsewhere                         */
+    int32_t batch_order;        /* batch plans: work-list order the setup's tuner kept:
+                                   0 = (instance, species) items longest first,
+                                   1 = instances longest first, both species adjacent;
+                                   for batch plans stencil_tile_j is the theta-lines per
+                                   stencil tile and ring_slots the ring depths it kept       */
+    float batch_step_us;        /* batch plans: measured step time at that configuration     */
 } sexpe_plan_info;
 
 /* Build a plan: FP64 host setup of the 1-D axes (Section 3: eqs. A_theta,
@@ -157,7 +163,13 @@ sexpe_status sexpe_setup(const sexpe_grid* grid, const sexpe_species* species, d
  * (geometry must be SEXPE_DISK for all; each instance has its own species
  * block).  Their states are concatenated instance after instance, each in the
  * single-plan layout; sexpe_state_offsets() gives the element offsets.  Steps
- * run as one persistent launch per step over an LPT-ordered work list. */
+ * run as one persistent cooperative launch per step: a stencil phase over
+ * tiles of theta-lines of every instance, a bounded grid barrier, then the
+ * disk chain of eq. ee_disk per (instance, species) item from a work list.
+ * The setup times every feasible combination of ring depths, stencil tile
+ * height (8, 16 or 32 lines) and work-list order on `stream` and keeps the
+ * fastest (sexpe_plan_info reports the choice and its time).  Split-TF32 only;
+ * n_rho <= 128, n_theta <= 256. */
 sexpe_status sexpe_batch_setup(int32_t count, const sexpe_grid* grids, const sexpe_species* species,
                                double tau, int32_t precision, void* stream, sexpe_plan** out);
 

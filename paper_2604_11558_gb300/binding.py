@@ -72,7 +72,8 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
                 ("stencil_tile_j", ctypes.c_int32), ("ring_slots", ctypes.c_int32 * 2),
                 ("stencil_tile_us", ctypes.c_float), ("stencil_planes", ctypes.c_int32),
-                ("stencil_ctas_per_sm", ctypes.c_int32), ("theta_split", ctypes.c_int32)]
+                ("stencil_ctas_per_sm", ctypes.c_int32), ("theta_split", ctypes.c_int32),
+                ("batch_order", ctypes.c_int32), ("batch_step_us", ctypes.c_float)]
 
 
 _lib = None

@@ -157,6 +157,7 @@ struct BatchTables {
                                     // zeroed before every launch
     const int2* ftiles;             // phase-1 stencil tiles (instance, first theta-line)
     int n_ftiles;
+    int tj;                         // theta-lines per phase-1 tile
     float* F;                       // F of every instance (phase 1 -> phase 2)
     const double* W_in;             // state before the step (all instances)
     double* W_out;                  // state after the step

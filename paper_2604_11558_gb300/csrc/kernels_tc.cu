@@ -1323,12 +1323,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, Tc
 // the LPT-ordered work list and run the disk chain of eq. ee_disk on F --
 // x_2 Q_theta^T, Hadamard, x_2 Q_theta, x_1 phi_1(tau d A_rho) -- writing the
 // updated species into the other state buffer.
-constexpr int kBatchTJ = 16;     // theta-lines per phase-1 tile
-
+// Phase-1 tiles are tj theta-lines of one instance (tj measured at setup: BatchTables.tj).
 __device__ __forceinline__ void batch_stencil_tile(const BatchInstance& I, const double* Win, float* Fout, int j0,
-                                                   float2* tile) {
+                                                   int tj, float2* tile) {
     const int n1 = I.n1, n2 = I.n2, n1q = (n1 + 3) & ~3;
-    const int lines = min(kBatchTJ, n2 - j0);
+    const int lines = min(tj, n2 - j0);
     const int nJ = lines + 2;                           // lines j0 - 1 .. j0 + lines: one wrap at most
     const long long n12 = (long long)n1 * n2;
     const int per_sp = nJ * n1;
@@ -1405,7 +1404,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_batch(BatchTables B, TcShape s
         if (it >= B.n_ftiles) break;
         const int2 t = B.ftiles[it];
         const BatchInstance& I = B.inst[t.x];
-        batch_stencil_tile(I, B.W_in + I.w_off, B.F + I.f_off, t.y, tile);
+        batch_stencil_tile(I, B.W_in + I.w_off, B.F + I.f_off, t.y, B.tj, tile);
     }
     grid_barrier(B.counter + 1, gridDim.x, B.err);
     // phase 2: the chains
@@ -1758,6 +1757,29 @@ TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols) {
     TcShape sh = slab_shape(max_n1, max_n2, false);        // one persistent CTA per SM
     sh.tmem_cols = std::max(sh.tmem_cols, tmem_cols);
     return sh;
+}
+
+// Every ring configuration of the batch kernel that fits one CTA per SM: nd data slots and
+// nm <= nd matrix slots (the matrix copies complete on the data barriers), with room for the
+// epilogue staging and for a phase-1 stencil tile of max_tj + 2 lines of both species.
+int tc_batch_shapes(int max_n1, int max_n2, uint32_t tmem_cols, int max_tj, TcShape* out, int cap) {
+    const TcShape base = tc_batch_shape(max_n1, max_n2, tmem_cols);
+    const uint32_t slack = 128 + kHeaderBytes;
+    const uint32_t n1p = round_up(max_n1, 16);
+    const uint32_t epi = kRows * (n1p + 1) * 4u;
+    const uint32_t tile = (uint32_t)(max_tj + 2) * (uint32_t)max_n1 * 2u * (uint32_t)sizeof(float2);
+    int n = 0;
+    for (uint32_t nd = 2; nd <= (uint32_t)kMaxData; ++nd)
+        for (uint32_t nm = 2; nm <= nd && nm <= (uint32_t)kMaxMat; ++nm) {
+            TcShape sh = base;
+            sh.nd = nd;
+            sh.nm = nm;
+            const uint32_t body = std::max(std::max(nm * sh.mat_bytes + nd * sh.data_bytes, epi), tile);
+            sh.smem_bytes = slack + body;
+            if (sh.smem_bytes > 227u * 1024u || n >= cap) continue;
+            out[n++] = sh;
+        }
+    return n;
 }
 
 cudaError_t tc_prepare_batch(uint32_t smem) {

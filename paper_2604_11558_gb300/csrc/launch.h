@@ -54,6 +54,7 @@ cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cuda
 int rhs_candidates(const SplitTables& T, int3* out, int max_out);
 // Batched disks: one persistent launch per step.
 TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols);
+int tc_batch_shapes(int max_n1, int max_n2, uint32_t tmem_cols, int max_tj, TcShape* out, int cap);
 cudaError_t tc_prepare_batch(uint32_t smem);
 cudaError_t launch_tc_batch(const BatchTables& B, const TcShape& sh, int grid, cudaStream_t st);
 int batch_grid(const TcShape& sh);

@@ -887,6 +887,10 @@ sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species*
 // ---------------------------------------------------------------------------
 // Batched independent disks.
 
+// Candidate phase-1 tile heights of the batch kernel and launches timed per candidate.
+const std::vector<int> kBatchTileLines = {8, 16, 32};
+constexpr int kBatchTuneReps = 3;
+
 sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, const sexpe_species* species,
                          double tau, cudaStream_t st) {
     p->batch = true;
@@ -999,30 +1003,43 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
         I.ax_theta.rs = base + o.tr;
         I.Dr = base + o.dr;
     }
-    // LPT work list: (instance, species) items, most tensor work first
+    // Work lists of (instance, species) chain items, two orders the setup times against each other:
+    // 0 = longest item first (LPT over items); 1 = instances longest first with their two species
+    // adjacent (the pair shares the instance's Q images in L2).
+    auto cost = [&](int q) {
+        const double n1 = inst[q].n1, n2 = inst[q].n2;
+        return n1 * n2 * (2.0 * n2 + n1);
+    };
     std::vector<int2> items;
     for (int q = 0; q < count; ++q)
         for (int sp = 0; sp < 2; ++sp) items.push_back(make_int2(q, sp));
-    std::stable_sort(items.begin(), items.end(), [&](const int2& a, const int2& b) {
-        auto cost = [&](const int2& x) {
-            const double n1 = inst[x.x].n1, n2 = inst[x.x].n2;
-            return n1 * n2 * (2.0 * n2 + n1);
-        };
-        return cost(a) > cost(b);
-    });
+    std::stable_sort(items.begin(), items.end(), [&](const int2& a, const int2& b) { return cost(a.x) > cost(b.x); });
+    std::vector<int> order(count);
+    for (int q = 0; q < count; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<int2> items_pairs;
+    for (int q : order) {
+        items_pairs.push_back(make_int2(q, 0));
+        items_pairs.push_back(make_int2(q, 1));
+    }
     // the instance descriptors go up as raw bytes
     std::vector<char> ibytes(sizeof(BatchInstance) * count);
     std::memcpy(ibytes.data(), inst.data(), ibytes.size());
     const char* dinst = nullptr;
     SX_TRY(upload(p, ibytes, &dinst, st));
-    const int2* ditems = nullptr;
-    SX_TRY(upload(p, items, &ditems, st));
-    // phase-1 stencil tiles: 16 theta-lines of one instance each
-    std::vector<int2> ftiles;
-    for (int q = 0; q < count; ++q)
-        for (int j0 = 0; j0 < inst[q].n2; j0 += 16) ftiles.push_back(make_int2(q, j0));
-    const int2* dftiles = nullptr;
-    SX_TRY(upload(p, ftiles, &dftiles, st));
+    const int2* ditems[2] = {nullptr, nullptr};
+    SX_TRY(upload(p, items, &ditems[0], st));
+    SX_TRY(upload(p, items_pairs, &ditems[1], st));
+    // phase-1 stencil tiles of tj theta-lines of one instance each, one list per candidate tj
+    std::vector<const int2*> dftiles(kBatchTileLines.size(), nullptr);
+    std::vector<int> nftiles(kBatchTileLines.size(), 0);
+    for (size_t c = 0; c < kBatchTileLines.size(); ++c) {
+        std::vector<int2> ftiles;
+        for (int q = 0; q < count; ++q)
+            for (int j0 = 0; j0 < inst[q].n2; j0 += kBatchTileLines[c]) ftiles.push_back(make_int2(q, j0));
+        SX_TRY(upload(p, ftiles, &dftiles[c], st));
+        nftiles[c] = (int)ftiles.size();
+    }
     float* dF = nullptr;
     SX_TRY(alloc_dev(p, (size_t)f_total, &dF));
     SX_CUDA(cudaMemsetAsync(dF, 0, sizeof(float) * (size_t)f_total, st));   // padding columns stay zero
@@ -1033,20 +1050,72 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
     SX_TRY(alloc_dev(p, (size_t)p->inst_off.back(), &p->bstate));
     SX_TRY(alloc_dev(p, (size_t)p->inst_off.back(), &p->d_host_state));
     p->btab.inst = reinterpret_cast<const BatchInstance*>(dinst);
-    p->btab.items = ditems;
     p->btab.n_items = (int)items.size();
     p->btab.counter = counter;
-    p->btab.ftiles = dftiles;
-    p->btab.n_ftiles = (int)ftiles.size();
     p->btab.F = dF;
     p->btab.tau = (float)tau;
     p->btab.err = p->d_err;
-    p->bsh = tc_batch_shape(max_n1, max_n2, tmem_cols);
-    if (p->bsh.tmem_cols > 512) return SEXPE_EUNSUPPORTED;
-    if (p->bsh.smem_bytes > 227 * 1024) return SEXPE_EUNSUPPORTED;
-    SX_CUDA(tc_prepare_batch(p->bsh.smem_bytes));
-    p->batch_grid = batch_grid(p->bsh);
-    if (p->batch_grid < 1) return SEXPE_EUNSUPPORTED;
+    // Autotuner: time every (ring configuration, phase-1 tile height, work-list order) on the
+    // plan's own buffers (a zero state; the arithmetic is data-independent) and keep the fastest.
+    TcShape shapes[16];
+    const int max_tj = *std::max_element(kBatchTileLines.begin(), kBatchTileLines.end());
+    const int nsh = tc_batch_shapes(max_n1, max_n2, tmem_cols, max_tj, shapes, 16);
+    if (nsh < 1 || shapes[0].tmem_cols > 512) return SEXPE_EUNSUPPORTED;
+    uint32_t smem_max = 0;
+    for (int c = 0; c < nsh; ++c) smem_max = std::max(smem_max, shapes[c].smem_bytes);
+    SX_CUDA(tc_prepare_batch(smem_max));
+    SX_CUDA(cudaMemsetAsync(p->bstate, 0, sizeof(double) * (size_t)p->inst_off.back(), st));
+    cudaEvent_t ev[2];
+    SX_CUDA(cudaEventCreate(&ev[0]));
+    SX_CUDA(cudaEventCreate(&ev[1]));
+    float best = 1e30f;
+    sexpe_status ts = SEXPE_OK;
+    for (int c = 0; c < nsh && ts == SEXPE_OK; ++c) {
+        const int grid = batch_grid(shapes[c]);
+        if (grid < 1) continue;
+        for (size_t t = 0; t < kBatchTileLines.size() && ts == SEXPE_OK; ++t)
+            for (int o = 0; o < 2 && ts == SEXPE_OK; ++o) {
+                BatchTables B = p->btab;
+                B.items = ditems[o];
+                B.ftiles = dftiles[t];
+                B.n_ftiles = nftiles[t];
+                B.tj = kBatchTileLines[t];
+                B.W_in = p->bstate;
+                B.W_out = p->d_host_state;
+                float ms = 0.f;
+                cudaError_t e = launch_tc_batch(B, shapes[c], grid, st);                   // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+                for (int r = 0; r < kBatchTuneReps && e == cudaSuccess; ++r) e = launch_tc_batch(B, shapes[c], grid, st);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                if (e != cudaSuccess) {
+                    ts = cuda_status(e);
+                    break;
+                }
+                ms /= kBatchTuneReps;
+                if (ms < best) {
+                    best = ms;
+                    p->bsh = shapes[c];
+                    p->batch_grid = grid;
+                    p->btab.items = ditems[o];
+                    p->btab.ftiles = dftiles[t];
+                    p->btab.n_ftiles = nftiles[t];
+                    p->btab.tj = kBatchTileLines[t];
+                    p->batch_order = o;
+                }
+            }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    SX_TRY(ts);
+    if (best >= 1e30f) return SEXPE_EUNSUPPORTED;
+    p->batch_step_us = best * 1e3f;
+    // the timing runs left a timeout flag only if a bounded wait ran out: report it now
+    int herr = 0;
+    SX_CUDA(cudaMemcpyAsync(&herr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SX_CUDA(cudaStreamSynchronize(st));
+    if (herr != 0) return SEXPE_ETIMEOUT;
     p->npts = p->inst_off.back() / 2;
     p->n[0] = max_n1;
     p->n[1] = max_n2;
@@ -1674,6 +1743,9 @@ sexpe_status sexpe_plan_get_info(const sexpe_plan* p, sexpe_plan_info* info) {
     } else if (p->batch) {
         info->ring_slots[0] = (int32_t)p->bsh.nm;
         info->ring_slots[1] = (int32_t)p->bsh.nd;
+        info->stencil_tile_j = p->btab.tj;
+        info->batch_order = p->batch_order;
+        info->batch_step_us = p->batch_step_us;
     }
     return SEXPE_OK;
 }

@@ -87,6 +87,8 @@ struct sexpe_plan {
     double setup_ms = 0.0;
     float rhs_tj_us = 0.f;     // measured stencil time at the chosen tile height
     int batch_grid = 0;        // CTAs of the cooperative batch launch
+    int batch_order = 0;       // work-list order the batch tuner kept (sexpe_plan_info.batch_order)
+    float batch_step_us = 0.f; // measured batch step at the kept configuration
     std::vector<int> th_splits;            // split sphere: theta-kernel column splits built at setup
     std::vector<sexpe::Image> th_imgs;     // their N-tiled Q_theta images
     long long* d_step = nullptr;   // steps since setup / sexpe_set_time (time-dependent sources)

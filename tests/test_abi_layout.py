@@ -16,7 +16,7 @@ STRUCTS = {
     "sexpe_plan_info": ("PlanInfo", ["geometry", "precision", "n_species", "ndim", "n", "n_instances",
                                      "kernels_per_step", "npts", "state_elems", "workspace_bytes", "setup_ms",
                                      "stencil_tile_j", "ring_slots", "stencil_tile_us", "stencil_planes",
-                                     "stencil_ctas_per_sm", "theta_split"]),
+                                     "stencil_ctas_per_sm", "theta_split", "batch_order", "batch_step_us"]),
 }
 
 

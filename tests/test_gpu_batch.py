@@ -68,3 +68,19 @@ def test_batch_full_workload_sampled():
     for q in [0, 17, 100, 255]:
         e = rel_errors(got[q], oracle_run(ws[q]))
         assert max(e) <= 1e-6, (q, ws[q]["n"], e)
+
+
+def test_batch_plan_reports_tuned_configuration():
+    """sexpe_batch_setup times every feasible (ring depths, stencil tile height, work-list order)
+    and keeps the fastest; sexpe_plan_info reports the kept choice and its measured step time."""
+    from paper_2604_11558_gb300 import binding
+    plan = binding.BatchPlan(wl.batched_disks(steps=1))
+    info = plan.info()
+    plan.close()
+    print("batch tuner choice", info["stencil_tile_j"], info["ring_slots"], info["batch_order"],
+          info["batch_step_us"])
+    assert info["stencil_tile_j"] in (8, 16, 32)
+    assert info["batch_order"] in (0, 1)
+    nm, nd = info["ring_slots"]
+    assert 2 <= nm <= nd <= 4
+    assert 0.0 < info["batch_step_us"] < 5000.0

@@ -350,10 +350,20 @@ sexpe_status sexpe_step_checkpointed(sexpe_plan* plan, double* state_dev, int64_
  * the transposed phi_1 chain in reverse order; dL/dd_s adds <mu_s, M w_s> and
  * tau <lambda_s, (dP_s/dd_s) F_s> with dphi_1(tau d s A)/dd = V diag(tau s lambda
  * phi_1'(tau d s lambda)) V^{-1}, phi_1' = phi_1 - phi_2.  Each checkpoint
- * segment is recomputed forward.  FP64 plans only (SEXPE_EUNSUPPORTED
- * otherwise); the first call builds the adjoint tables and work buffers
- * (device allocations); the parameter gradient is copied to the host and the
- * stream synchronised when dL_dparams_host is given. */
+ * segment is recomputed forward.  FP64 plans of every geometry, and
+ * SEXPE_SPLIT_TF32 sphere plans (eq. ee_sphere): there the adjoint
+ * differentiates the split forward, whose replayed states it uses, and every
+ * product of the transposed chain runs on the forward's tensor-core kernels
+ * in split TF32 with FP32 accumulation -- tau P_theta lambda and
+ * tau (dP_theta/dd_s) lambda by the theta kernel (P_theta = Q diag(Phi) Q^T is
+ * symmetric), mu = phi_1(tau d_s A_phi)^T (tau P_theta lambda) and
+ * (dphi_1(tau d_s A_phi)/dd_s) F by the phi kernel with transposed and
+ * differentiated operand images -- while lambda, the transposed stencil with
+ * the reaction Jacobian and the parameter sums stay FP64.  Other plans give
+ * SEXPE_EUNSUPPORTED, a plan of another device SEXPE_EINVAL.  The first call
+ * builds the adjoint tables and work buffers (device allocations); the
+ * parameter gradient is copied to the host and the stream synchronised when
+ * dL_dparams_host is given. */
 sexpe_status sexpe_adjoint(sexpe_plan* plan, const double* checkpoints_dev, int32_t n_ckpt, int32_t every,
                            const double* dL_dWT_dev, double* dL_dW0_dev, double* dL_dparams_host, void* stream);
 

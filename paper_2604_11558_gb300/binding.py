@@ -417,7 +417,7 @@ def _autograd_function():
         checkpointed forward and discrete adjoint.  `params` is a CPU float64
         tensor holding the values the plan was built with (reaction parameters,
         then the diffusion coefficients); its gradient is the adjoint's
-        parameter gradient.  FP64 plans."""
+        parameter gradient.  FP64 plans, and split-TF32 sphere plans."""
 
         @staticmethod
         def forward(ctx, W0, params, plan, n_steps, every):

@@ -400,4 +400,79 @@ cudaError_t launch_gemm64(const Gemm64& g, int n_species, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---- split-TF32 adjoint helpers: the adjoint variable moves between the FP64 state layout
+// [s][j][n1] (rows of n1 values, rows = npts / n1 per species) and the FP32 chain layout
+// [s][j][n1q] of the tensor-core kernels (rows padded to n1q; the padding is never written).
+
+// dst[s][r][i] = (float) src[s][r][i] for i < n1.
+__global__ void __launch_bounds__(256) k_to_chain_f32(const double* __restrict__ src, float* __restrict__ dst, int n1,
+                                                      int n1q, long long rows, long long ys, long long npts, int S) {
+    const long long total = (long long)S * npts;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long s = q / npts, rest = q - s * npts;
+        const long long r = rest / n1, i = rest - r * n1;
+        dst[s * ys + r * n1q + i] = (float)src[q];
+    }
+    (void)rows;
+}
+
+// dst[s][r][i] = src[s][r][i] (FP32 chain layout to the FP64 state layout, exact).
+__global__ void __launch_bounds__(256) k_from_chain_f32(const float* __restrict__ src, double* __restrict__ dst, int n1,
+                                                        int n1q, long long ys, long long npts, int S) {
+    const long long total = (long long)S * npts;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long s = q / npts, rest = q - s * npts;
+        const long long r = rest / n1, i = rest - r * n1;
+        dst[q] = (double)src[s * ys + r * n1q + i];
+    }
+}
+
+// acc[s] += sum over the points of a[s][r][i] (FP64 state layout) * b[s][r][i] (FP32 chain layout).
+__global__ void __launch_bounds__(256) k_dot_state_chain(const double* __restrict__ a, const float* __restrict__ b,
+                                                         int n1, int n1q, long long ys, long long npts,
+                                                         double* __restrict__ acc) {
+    __shared__ double red[8];
+    const int s = blockIdx.y;
+    double v = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npts;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long r = p / n1, i = p - r * n1;
+        v += a[s * npts + p] * (double)b[s * ys + r * n1q + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) t += red[w8];
+        atomicAdd(&acc[s], t);
+    }
+}
+
+static int helper_blocks(long long n, long long cap) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_to_chain_f32(const double* src, float* dst, int n1, int n1q, long long ys, long long npts, int S,
+                                cudaStream_t st) {
+    k_to_chain_f32<<<helper_blocks((long long)S * npts, 152LL * 8), 256, 0, st>>>(src, dst, n1, n1q, npts / n1, ys,
+                                                                                  npts, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_chain_f32(const float* src, double* dst, int n1, int n1q, long long ys, long long npts, int S,
+                                  cudaStream_t st) {
+    k_from_chain_f32<<<helper_blocks((long long)S * npts, 152LL * 8), 256, 0, st>>>(src, dst, n1, n1q, ys, npts, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_state_chain(const double* a, const float* b, int n1, int n1q, long long ys, long long npts,
+                                   int S, double* acc, cudaStream_t st) {
+    k_dot_state_chain<<<dim3((unsigned)helper_blocks(npts, 152LL * 2), S), 256, 0, st>>>(a, b, n1, n1q, ys, npts, acc);
+    return cudaGetLastError();
+}
+
 }  // namespace sexpe

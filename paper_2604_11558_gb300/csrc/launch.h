@@ -25,6 +25,14 @@ cudaError_t launch_adj_params(int geometry, const RhsTables<double>& tb, const d
 cudaError_t launch_wdot(const double* a, const double* b, const double* wt, long long npts, int S, double scale,
                         double* acc, cudaStream_t st);
 cudaError_t launch_scale(double* x, double a, long long n, cudaStream_t st);
+// Split-TF32 adjoint: the adjoint variable between the FP64 state layout [s][r][n1] and the FP32
+// chain layout [s][r][n1q] (ys floats per species), and acc[s] += <a_s, b_s> across the two layouts.
+cudaError_t launch_to_chain_f32(const double* src, float* dst, int n1, int n1q, long long ys, long long npts, int S,
+                                cudaStream_t st);
+cudaError_t launch_from_chain_f32(const float* src, double* dst, int n1, int n1q, long long ys, long long npts, int S,
+                                  cudaStream_t st);
+cudaError_t launch_dot_state_chain(const double* a, const float* b, int n1, int n1q, long long ys, long long npts,
+                                   int S, double* acc, cudaStream_t st);
 cudaError_t launch_tick(long long* step, cudaStream_t st);
 
 // Split-TF32 tensor-core path.

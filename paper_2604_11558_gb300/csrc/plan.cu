@@ -87,6 +87,12 @@ bool all_finite(const std::vector<double>& v) {
     return true;
 }
 
+bool all_finite(const std::vector<float>& v) {
+    for (float x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
 // TF32 rounding to nearest (ties away from zero) of an FP32 value, on the host.
 float tf32_rna_host(float x) {
     uint32_t u;
@@ -1205,6 +1211,172 @@ sexpe_status build_adjoint(sexpe_plan* p, cudaStream_t st) {
     return SEXPE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Discrete adjoint of the split-TF32 sphere step (eq. ee_sphere): the step is
+//     W_{n+1} = W_n + tau P_theta P_phi F(W_n),   P_theta = Q diag(Phi) Q^T,  P_phi = phi_1(tau d A_phi)
+// so, with lambda = dL/dW_{n+1} and mu = tau P^T lambda = P_phi^T (tau P_theta lambda) (P_theta is
+// symmetric: Q orthogonal, Phi diagonal),
+//     dL/dW_n = lambda + (d M + J_g(W_n))^T mu,
+//     dL/dd_s += <mu_s, M w_s> + tau <lambda_s, (dP_theta/dd_s) P_phi F_s> + tau <P_theta lambda_s, (dP_phi/dd_s) F_s>,
+// dP_theta/dd_s = Q diag(tau s lambda_theta phi_1'(tau d_s s lambda_theta)) Q^T (symmetric),
+// dP_phi/dd_s = V diag(tau lambda_phi phi_1'(tau d_s lambda_phi)) V^{-1}, phi_1' = phi_1 - phi_2.
+// Every product runs on the forward's tensor-core kernels (split TF32, FP32 accumulation) with
+// the transposed / differentiated operand images; lambda and the parameter sums stay FP64.
+
+sexpe_status build_adjoint_split(sexpe_plan* p, cudaStream_t st) {
+    if (p->sadj_built) return SEXPE_OK;
+    SX_TRY(build_rhs_tables<double>(p, &p->rhs64, st));
+    p->adj_diag = p->rhs64;                      // M^T: same off-diagonals, the full diagonal in rs
+    for (int m = 0; m < p->ndim; ++m) {
+        const double* dg = nullptr;
+        SX_TRY(upload(p, p->ax[m].diag, &dg, st));
+        p->adj_diag.ax[m].rs = dg;
+    }
+    SplitTables& T = p->tabs;
+    const int n1 = p->n[0], n2 = p->n[1], n2p = rup16(n2);
+    const int ntiles = (n2p + T.phi_nt - 1) / T.phi_nt;
+    const Mat Aphi = p->ax[1].dense();
+    const Eigen e = tridiag_eigen(p->ax[1]);
+    for (int s = 0; s < p->S; ++s) {
+        Mat X(n2);
+        for (size_t q = 0; q < X.a.size(); ++q) X.a[q] = p->tau * p->d[s] * Aphi.a[q];
+        const Mat Ps = phi1_pade(X);
+        Mat dP(n2);
+        for (int r = 0; r < n2; ++r)
+            for (int c = 0; c < n2; ++c) {
+                double acc = 0.0;
+                for (int m = 0; m < n2; ++m)
+                    acc += e.V(r, m) * p->tau * e.lam[m] * dphi1_scalar(p->tau * p->d[s] * e.lam[m]) * e.Vinv(m, c);
+                dP(r, c) = acc;
+            }
+        if (!all_finite(Ps.a) || !all_finite(dP.a)) return SEXPE_ENUMERIC;
+        std::vector<float> imgT, imgD;
+        for (int t = 0; t < ntiles; ++t) {
+            const int r0 = t * T.phi_nt, rows = std::min(T.phi_nt, n2 - r0);
+            const std::vector<float> a = make_image(rows, n2, T.phi_nt, n2p, [&](int r, int k) { return Ps(k, r0 + r); });
+            const std::vector<float> b = make_image(rows, n2, T.phi_nt, n2p, [&](int r, int k) { return dP(r0 + r, k); });
+            imgT.insert(imgT.end(), a.begin(), a.end());
+            imgD.insert(imgD.end(), b.begin(), b.end());
+        }
+        const float* pt = nullptr;
+        const float* pd = nullptr;
+        SX_TRY(upload(p, imgT, &pt, st));
+        SX_TRY(upload(p, imgD, &pd, st));
+        p->sadj_PphiT[s] = Image{pt, T.phi_nt, n2p / kKC, 2LL * T.phi_nt * kKC};
+        p->sadj_dPphi[s] = Image{pd, T.phi_nt, n2p / kKC, 2LL * T.phi_nt * kKC};
+    }
+    const Eigen th = theta_eigen(p->ax[0]);
+    std::vector<float> hd((size_t)p->S * T.ys, 0.f);
+    for (int s = 0; s < p->S; ++s)
+        for (int j = 0; j < n2; ++j)
+            for (int ip = 0; ip < n1; ++ip) {
+                const double sl = dir_scale(p, 1, 0, j, 0) * th.lam[ip];
+                hd[(size_t)s * T.ys + (size_t)j * T.n1q + ip] = (float)(p->tau * sl * dphi1_scalar(p->tau * p->d[s] * sl));
+            }
+    if (!all_finite(hd)) return SEXPE_ENUMERIC;
+    SX_TRY(upload(p, hd, &p->sadj_had_d, st));
+    const size_t yf = (size_t)p->S * T.ys, e64 = (size_t)p->S * p->npts;
+    SX_TRY(alloc_dev(p, yf, &p->sadj_Yl));
+    SX_TRY(alloc_dev(p, yf, &p->sadj_Y3));
+    SX_TRY(alloc_dev(p, yf, &p->sadj_Ymu));
+    SX_CUDA(cudaMemsetAsync(p->sadj_Yl, 0, sizeof(float) * yf, st));    // padding columns stay zero
+    SX_CUDA(cudaMemsetAsync(p->sadj_Y3, 0, sizeof(float) * yf, st));
+    SX_CUDA(cudaMemsetAsync(p->sadj_Ymu, 0, sizeof(float) * yf, st));
+    SX_TRY(alloc_dev(p, e64, &p->sadj_T64[0]));
+    SX_TRY(alloc_dev(p, e64, &p->sadj_T64[1]));
+    SX_TRY(alloc_dev(p, e64, &p->sadj_MU));
+    if (!p->adj_red) SX_TRY(alloc_dev(p, 32, &p->adj_red));
+    SX_CUDA(cudaStreamSynchronize(st));
+    p->sadj_built = true;
+    return SEXPE_OK;
+}
+
+// One adjoint step of the split sphere plan at the state W_n: lam (FP64, state layout) goes from
+// lambda_{n+1} to lambda_n; the parameter gradient accumulates in p->adj_red.
+sexpe_status adjoint_step_split(sexpe_plan* p, const double* Wn, double* lam, cudaStream_t st) {
+    const SplitTables& T0 = p->tabs;
+    const size_t e64 = (size_t)p->S * p->npts;
+    const int n1 = p->n[0];
+    double* acc_d = p->adj_red + 16;
+    // forward quantities at W_n: F (T.Y), P_phi F (T.Y2), (dP_phi/dd) F (Y3)
+    SplitTables T = T0;
+    T.state = Wn;
+    SX_CUDA(launch_rhs_split(T, st));
+    SX_CUDA(launch_tc_sphere_phi(T, p->sh3, st));
+    SplitTables Td = T;
+    Td.Y2 = p->sadj_Y3;
+    for (int s = 0; s < p->S; ++s) Td.Pphi[s] = p->sadj_dPphi[s];
+    SX_CUDA(launch_tc_sphere_phi(Td, p->sh3, st));
+    // tau P_theta lambda and tau (dP_theta/dd) lambda: the theta kernel's update adds tau x its
+    // product to a zeroed FP64 buffer
+    SX_CUDA(launch_to_chain_f32(lam, p->sadj_Yl, n1, T0.n1q, T0.ys, p->npts, p->S, st));
+    for (int q = 0; q < 2; ++q) {
+        SplitTables Tt = T0;
+        Tt.Y2 = p->sadj_Yl;
+        if (q == 1) Tt.had_sph = p->sadj_had_d;
+        Tt.state_upd = p->sadj_T64[q];
+        SX_CUDA(cudaMemsetAsync(p->sadj_T64[q], 0, sizeof(double) * e64, st));
+        SX_CUDA(launch_tc_sphere_theta(Tt, p->shs, st));
+    }
+    // d-derivative terms: <tau dP_theta lambda, P_phi F> + <tau P_theta lambda, dP_phi F>
+    SX_CUDA(launch_dot_state_chain(p->sadj_T64[1], T0.Y2, n1, T0.n1q, T0.ys, p->npts, p->S, acc_d, st));
+    SX_CUDA(launch_dot_state_chain(p->sadj_T64[0], p->sadj_Y3, n1, T0.n1q, T0.ys, p->npts, p->S, acc_d, st));
+    // mu = P_phi^T (tau P_theta lambda)
+    SX_CUDA(launch_to_chain_f32(p->sadj_T64[0], p->sadj_Yl, n1, T0.n1q, T0.ys, p->npts, p->S, st));
+    SplitTables Tm = T0;
+    Tm.Y = p->sadj_Yl;
+    Tm.Y2 = p->sadj_Ymu;
+    for (int s = 0; s < p->S; ++s) Tm.Pphi[s] = p->sadj_PphiT[s];
+    SX_CUDA(launch_tc_sphere_phi(Tm, p->sh3, st));
+    SX_CUDA(launch_from_chain_f32(p->sadj_Ymu, p->sadj_MU, n1, T0.n1q, T0.ys, p->npts, p->S, st));
+    // reaction-parameter and <mu, M w> sums, then lambda += (d M + J_g)^T mu
+    SX_CUDA(launch_adj_params(p->geometry, p->rhs64, Wn, p->sadj_MU, p->adj_red, st));
+    SX_CUDA(launch_adj_lambda(p->geometry, p->adj_diag, Wn, p->sadj_MU, lam, st));
+    return SEXPE_OK;
+}
+
+// sexpe_adjoint for a split-TF32 sphere plan: per checkpoint segment, the states are replayed by
+// the split forward step and kept, then the adjoint steps run backwards over them.
+sexpe_status adjoint_split(sexpe_plan* p, const double* checkpoints, int n_ckpt, int every, const double* dL_dWT,
+                           double* dL_dW0, double* dL_dparams, cudaStream_t st) {
+    try {
+        SX_TRY(build_adjoint_split(p, st));
+    } catch (const std::bad_alloc&) {
+        return SEXPE_ENOMEM;
+    } catch (...) {
+        return SEXPE_ENUMERIC;
+    }
+    const size_t E = (size_t)p->S * p->npts;
+    if (p->adj_seg_cap < every) {
+        double* seg = nullptr;
+        SX_TRY(alloc_dev(p, (size_t)every * E, &seg));
+        p->adj_seg = seg;
+        p->adj_seg_cap = every;
+    }
+    double* lam = dL_dW0;                      // the adjoint variable lives in the output buffer
+    if (lam != dL_dWT) SX_CUDA(cudaMemcpyAsync(lam, dL_dWT, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    SX_CUDA(cudaMemsetAsync(p->adj_red, 0, 32 * sizeof(double), st));
+    for (int c = n_ckpt - 1; c >= 0; --c) {
+        SX_CUDA(cudaMemcpyAsync(p->adj_seg, checkpoints + (size_t)c * E, E * sizeof(double), cudaMemcpyDeviceToDevice,
+                                st));
+        for (int j = 1; j < every; ++j) {
+            double* w = p->adj_seg + (size_t)j * E;
+            SX_CUDA(cudaMemcpyAsync(w, w - E, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            SX_TRY(enqueue_step(p, w, st));
+        }
+        for (int j = every - 1; j >= 0; --j) SX_TRY(adjoint_step_split(p, p->adj_seg + (size_t)j * E, lam, st));
+    }
+    if (dL_dparams) {
+        double red[32];
+        SX_CUDA(cudaMemcpyAsync(red, p->adj_red, sizeof(red), cudaMemcpyDeviceToHost, st));
+        SX_CUDA(cudaStreamSynchronize(st));
+        const int np = (int)p->params.size();
+        for (int q = 0; q < np; ++q) dL_dparams[q] = red[q];
+        for (int s = 0; s < p->S; ++s) dL_dparams[np + s] = red[16 + s];
+    }
+    return SEXPE_OK;
+}
+
 // Forward chain of the FP64 step at state W: X[0] = F, then every direction in
 // order -- X[q] its input, H[q] = Phi o (V^{-1} X[q]) for a direction in an
 // eigenbasis, X[q + 1] its output.  With `upd`, the last direction's output is
@@ -1767,12 +1939,15 @@ sexpe_status sexpe_step_checkpointed(sexpe_plan* p, double* state, int64_t n_ste
 sexpe_status sexpe_adjoint(sexpe_plan* p, const double* checkpoints, int32_t n_ckpt, int32_t every,
                            const double* dL_dWT, double* dL_dW0, double* dL_dparams, void* stream) {
     if (!p || !checkpoints || !dL_dWT || !dL_dW0 || n_ckpt < 1 || every < 1) return SEXPE_EINVAL;
-    if (p->precision != SEXPE_FP64 || p->coupled) return SEXPE_EUNSUPPORTED;
+    const bool split = p->precision == SEXPE_SPLIT_TF32 && p->geometry == SEXPE_SPHERE && !p->batch && !p->coupled;
+    if ((p->precision != SEXPE_FP64 && !split) || p->coupled) return SEXPE_EUNSUPPORTED;
     if (p->reaction == SEXPE_BVAM || p->reaction == SEXPE_BVAM_MANUFACTURED || p->reaction == SEXPE_LINEAR)
         return SEXPE_EUNSUPPORTED;
     for (double c : p->offset)
         if (c != 0.0) return SEXPE_EUNSUPPORTED;
+    if (!plan_on_current_device(p)) return SEXPE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    if (split) return adjoint_split(p, checkpoints, n_ckpt, every, dL_dWT, dL_dW0, dL_dparams, st);
     try {
         SX_TRY(build_adjoint(p, st));
     } catch (const std::bad_alloc&) {

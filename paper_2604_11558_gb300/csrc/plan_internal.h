@@ -75,6 +75,17 @@ struct sexpe_plan {
     double* adj_save = nullptr;             // forward chains of a segment's replayed steps
     int adj_save_cap = 0;
     double* adj_red = nullptr;              // device accumulators of the parameter gradient
+    // split-TF32 sphere adjoint (built on the first sexpe_adjoint call of such a plan): the
+    // transposed chain on the tensor-core kernels of the forward step with other operand images
+    bool sadj_built = false;
+    sexpe::Image sadj_PphiT[sexpe::kMaxSpecies] = {};   // phi_1(tau d_s A_phi)^T, N-tiled as Pphi
+    sexpe::Image sadj_dPphi[sexpe::kMaxSpecies] = {};   // d phi_1(tau d_s A_phi) / d d_s, N-tiled
+    const float* sadj_had_d = nullptr;     // d Phi / d d_s of the theta direction, layout of had_sph
+    float* sadj_Yl = nullptr;              // adjoint variable (then tau P_theta lambda) in the chain layout
+    float* sadj_Y3 = nullptr;              // (d phi_1(tau d_s A_phi) / d d_s) F in the chain layout
+    float* sadj_Ymu = nullptr;             // mu in the chain layout
+    double* sadj_T64[2] = {nullptr, nullptr};   // tau P_theta lambda, tau (d P_theta / d d_s) lambda
+    double* sadj_MU = nullptr;             // mu in the state layout
     // batched independent disks (sexpe_batch_setup)
     bool batch = false;
     int n_instances = 1;

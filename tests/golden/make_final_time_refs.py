@@ -2,10 +2,14 @@
 
 Runs ONLY the FP64 CPU oracle (``oracle/``) on the seeded workloads of
 ``paper_2604_11558_gb300.workloads`` to their final times and stores, per workload,
-the exact per-species 2-norms of the final state and its values at a seeded sample
+the exact per-species 2-norms of the final state, its values at a seeded sample
 of grid points (the full states are 2-25 MB each; the sample lets the GPU tests and
 the benchmark state the error of a full-size run at the final time without running
-the oracle for minutes):
+the oracle for minutes) and the storage floor of an FP32-intermediate chain: the
+per-species relative 2-norm error, over the whole final state, of the oracle run with
+F, every direction's result and the increment rounded to FP32 (its precision-emulation
+switch), which is what any implementation that keeps those intermediates in FP32 cannot
+be expected to beat:
 
 * ball 100^3 Gray-Scott, 500 steps (tau 0.5, t_* = 250);
 * cylinder 64 x 128 x 128, 3 species, 1000 steps (tau 0.05, t_* = 50);
@@ -38,15 +42,23 @@ def sample_indices(npts, k, seed):
     return np.sort(rng.choice(npts, size=min(k, npts), replace=False))
 
 
+def storage_floor(w, ref):
+    """Per-species relative 2-norm error of the oracle run with FP32 storage of every intermediate."""
+    emu = oracle_run(w, fp32_storage=True)
+    return np.array([np.linalg.norm(emu[s] - ref[s]) / np.linalg.norm(ref[s]) for s in range(ref.shape[0])])
+
+
 def single(name, w):
     t0 = time.time()
     ref = oracle_run(w)
     S = ref.shape[0]
     flat = ref.reshape(S, -1)
     idx = sample_indices(flat.shape[1], SAMPLES, SAMPLE_SEED)
+    floor = storage_floor(w, ref)
     np.savez_compressed(os.path.join(HERE, f"final_time_{name}.npz"), idx=idx, values=flat[:, idx],
                         norms=np.linalg.norm(flat, axis=1), maxabs=np.max(np.abs(flat), axis=1),
-                        steps=w["steps"], n=np.array(w["n"]), seed=w["seed"])
+                        floor=floor, steps=w["steps"], n=np.array(w["n"]), seed=w["seed"])
+    print(name, "FP32-storage floor per species", floor, flush=True)
     print(name, "done in", round(time.time() - t0), "s", flush=True)
 
 
@@ -63,6 +75,7 @@ def batch():
         out[f"values_{q}"] = flat[:, idx]
         out[f"norms_{q}"] = np.linalg.norm(flat, axis=1)
         out[f"maxabs_{q}"] = np.max(np.abs(flat), axis=1)
+        out[f"floor_{q}"] = storage_floor(ws[q], ref)
     np.savez_compressed(os.path.join(HERE, "final_time_batch.npz"), **out)
     print("batch done in", round(time.time() - t0), "s", flush=True)
 

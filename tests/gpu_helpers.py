@@ -48,10 +48,10 @@ def _oracle_reaction(w, g=None):
     return lambda W, t: [np.zeros_like(W[0]) for _ in range(len(w["d"]))]
 
 
-def oracle_run(w, steps=None):
+def oracle_run(w, steps=None, fp32_storage=False):
     g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"), lam=w.get("lam"))
     p = Problem(g, w["d"], oracle_reaction(w, g), w["tau"])
-    return run(p, w["W0"], w["steps"] if steps is None else steps)
+    return run(p, w["W0"], w["steps"] if steps is None else steps, fp32_storage=fp32_storage)
 
 
 def emulated_fp32_errors(w, ref, increments=False):

@@ -130,10 +130,25 @@ struct SplitTables {
     const float* had_sph;          // phi_1(tau d_s sin^-2 phi_j lambda_theta'), [s][j][n1q]
     Image Qsph;                    // Q_theta as B operand of the second theta product, N-tiled by th_nt rows
     int th_nt;                     // output theta columns per CTA of the theta kernel
+    // split sphere adjoint: a second image set and output of the phi kernel (phi_pair = 1 doubles
+    // its grid: species s of the second half multiplies by Pphi2[s] into Y3)
+    Image Pphi2[kMaxSpecies];
+    float* Y3;
+    int phi_pair;
     int* err;
     int rhs_tj;                    // j-lines per stencil tile (chosen by measurement at setup; 0 = model)
     int rhs_ks;                    // 0: tiled stencil kernel; > 0: rolling-window kernel, planes per CTA
     int rhs_mb;                    // rolling-window kernel: registers capped for this many CTAs per SM
+};
+
+// Arguments of the split sphere adjoint's theta kernel (see k_tc_sphere_theta_adj).
+struct SphereAdjArgs {
+    const float* lam32;       // adjoint variable rounded to FP32, chain layout [s][j][n1q]
+    const float* had_d;       // d Phi / d d_s of the theta direction, layout of had_sph
+    float* tpl;               // out: tau P_theta lambda, chain layout [s][j][n1q]
+    const float* Y2;          // P_phi F at the step's state, chain layout
+    const float* Y3;          // (dP_phi / dd_s) F, chain layout
+    double* acc_d;            // acc_d[s] += <tau dP_theta lambda, Y2> + <tau P_theta lambda, Y3>
 };
 
 // ---------------- batched independent disks (split-TF32) -------------------

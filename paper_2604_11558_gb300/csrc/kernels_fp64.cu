@@ -311,6 +311,200 @@ __global__ void __launch_bounds__(256) k_adj_params(RhsTables<double> tb, const 
     }
 }
 
+// Per-point reaction-parameter derivatives sum_s mu_s dG_s/dp into part[0 .. np).
+__device__ __forceinline__ void reaction_param_parts(const ReactionParams<double>& rp, const double* w, const double* m,
+                                                     double* part) {
+    switch (rp.kind) {
+    case R_SCHNAKENBERG: {   // params (gamma, a, b)
+        const double u2v = w[0] * w[0] * w[1];
+        part[0] += m[0] * (rp.p[1] - w[0] + u2v) + m[1] * (rp.p[2] - u2v);
+        part[1] += m[0] * rp.p[0];
+        part[2] += m[1] * rp.p[0];
+        break;
+    }
+    case R_GRAY_SCOTT:       // params (F, k)
+        part[0] += m[0] * (1.0 - w[0]) - m[1] * w[1];
+        part[1] += -m[1] * w[1];
+        break;
+    case R_LINEAR_CUBIC:     // params K (row-major): d f_a / d K_ab = u_b
+        for (int a = 0; a < rp.S; ++a)
+            for (int b = 0; b < rp.S; ++b) part[a * rp.S + b] += m[a] * w[b];
+        break;
+    default:
+        break;
+    }
+}
+
+// One pass of an adjoint step after mu is formed: lambda_r += d_r M^T mu_r + sum_s (dG_s/dW_r) mu_s
+// and the parameter sums (reaction parameters, then <mu_s, M W_s> per species) of k_adj_lambda and
+// k_adj_params in one read of W and mu, with kFusedSlots partial sums per thread.  tbT carries M^T
+// (the full diagonal in rs), tb the difference-form M.  Needs np + S <= kFusedSlots.
+constexpr int kFusedSlots = 8;
+template <int GEO>
+__global__ void __launch_bounds__(256) k_adj_fused(RhsTables<double> tb, RhsTables<double> tbT,
+                                                   const double* __restrict__ W, const double* __restrict__ mu,
+                                                   double* __restrict__ lam, double* __restrict__ acc, int np) {
+    __shared__ double red[kFusedSlots][8];
+    double part[kFusedSlots];
+#pragma unroll
+    for (int q = 0; q < kFusedSlots; ++q) part[q] = 0.0;
+    const long long npts = tb.npts;                 // < 2^31 (at most 512^3 points): 32-bit index arithmetic
+    const int n1 = tb.n1, n2 = tb.n2, np32 = (int)npts;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < np32; idx += gridDim.x * blockDim.x) {
+        const int rest = idx / n1;
+        const int i = idx - rest * n1;
+        const int k = rest / n2;
+        const int j = rest - k * n2;
+        double w[kMaxSpecies], m[kMaxSpecies];
+        for (int r = 0; r < kMaxSpecies; ++r) {
+            w[r] = r < tb.S ? W[r * npts + idx] : 0.0;
+            m[r] = r < tb.S ? mu[r * npts + idx] : 0.0;
+        }
+        reaction_param_parts(tb.reac, w, m, part);
+        for (int r = 0; r < tb.S; ++r) {
+            part[np + r] += m[r] * laplacian<F64Acc, GEO>(tb, W + r * npts, idx, i, j, k, W[r * npts + idx]);
+            lam[r * npts + idx] += tb.d[r] * laplacianT<GEO>(tbT, mu + r * npts, idx, i, j, k) +
+                                   reaction_jt(tb.reac, w, m, r);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kFusedSlots; ++q) {
+        double v = part[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < np + tb.S) {
+        const int q = threadIdx.x;
+        double v = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) v += red[q][w8];
+        atomicAdd(&acc[q < np ? q : 16 + (q - np)], v);
+    }
+}
+
+// sum_s (dG_s/dW_r) mu_s at one point, for species r, in the arithmetic type T.
+template <class T>
+__device__ __forceinline__ T reaction_jt_t(const ReactionParams<T>& rp, const T* w, const T* mu, int r) {
+    switch (rp.kind) {
+    case R_SCHNAKENBERG: {
+        const T g = rp.p[0], u = w[0], v = w[1];
+        return r == 0 ? mu[0] * g * ((T)-1 + (T)2 * u * v) - mu[1] * (T)2 * g * u * v
+                      : mu[0] * g * u * u - mu[1] * g * u * u;
+    }
+    case R_GRAY_SCOTT: {
+        const T F = rp.p[0], kk = rp.p[1], u = w[0], v = w[1];
+        return r == 0 ? mu[0] * (-v * v - F) + mu[1] * v * v
+                      : mu[0] * ((T)-2 * u * v) + mu[1] * ((T)2 * u * v - (F + kk));
+    }
+    case R_LINEAR_CUBIC: {
+        T acc = (T)-3 * w[r] * w[r] * mu[r];
+        for (int i = 0; i < rp.S; ++i) acc += mu[i] * rp.p[i * rp.S + r];
+        return acc;
+    }
+    default:
+        return (T)0;
+    }
+}
+
+// Per-point reaction-parameter derivatives in FP32, summed into FP64 partials.
+__device__ __forceinline__ void reaction_param_parts_f32(const ReactionParams<float>& rp, const float* w,
+                                                         const float* m, double* part) {
+    switch (rp.kind) {
+    case R_SCHNAKENBERG: {
+        const float u2v = w[0] * w[0] * w[1];
+        part[0] += (double)(m[0] * (rp.p[1] - w[0] + u2v) + m[1] * (rp.p[2] - u2v));
+        part[1] += (double)(m[0] * rp.p[0]);
+        part[2] += (double)(m[1] * rp.p[0]);
+        break;
+    }
+    case R_GRAY_SCOTT:
+        part[0] += (double)(m[0] * (1.f - w[0]) - m[1] * w[1]);
+        part[1] += (double)(-m[1] * w[1]);
+        break;
+    case R_LINEAR_CUBIC:
+        for (int a = 0; a < rp.S; ++a)
+            for (int b = 0; b < rp.S; ++b) part[a * rp.S + b] += (double)(m[a] * w[b]);
+        break;
+    default:
+        break;
+    }
+}
+
+// (A^T x)_r of one axis in difference form on FP32 values x (stride st in elements):
+// tbT holds the transpose's off-diagonals and its column sums in rs.
+__device__ __forceinline__ float axis_term_t32(const StencilAxis<float>& ax, const float* x, int r, long long st) {
+    const float c = x[0];
+    float acc = ax.rs[r] * c;
+    if (r > 0) acc += ax.lower[r] * (x[-st] - c);
+    else if (ax.periodic) acc += ax.lower[r] * (x[(long long)(ax.n - 1) * st] - c);
+    if (r < ax.n - 1) acc += ax.upper[r] * (x[st] - c);
+    else if (ax.periodic) acc += ax.upper[r] * (x[-(long long)(ax.n - 1) * st] - c);
+    return acc;
+}
+
+// Split-TF32 adjoint, after mu is formed by the tensor-core chain: in one pass per point,
+// lambda_r += d_r (M^T mu_r) + sum_s (dG_s/dW_r) mu_s and the parameter sums (reaction parameters,
+// then <mu_s, M w_s>), with FP32 arithmetic -- M^T mu in difference form on the FP32 mu of the
+// chain layout (tbT), M w from FP64-accurate split pairs of the state (tbF, the forward tables) --
+// and FP64 for lambda and the sums.  mu: chain layout [s][rows][n1q], ys floats per species.
+template <int GEO>
+__global__ void __launch_bounds__(256) k_adj_fused_split(RhsTables<float> tbF, RhsTables<float> tbT,
+                                                         const double* __restrict__ W, const float* __restrict__ mu,
+                                                         int n1q, long long ys, double* __restrict__ lam,
+                                                         double* __restrict__ acc, int np) {
+    __shared__ double red[kFusedSlots][8];
+    double part[kFusedSlots];
+#pragma unroll
+    for (int q = 0; q < kFusedSlots; ++q) part[q] = 0.0;
+    const long long npts = tbF.npts;
+    const int n1 = tbF.n1, n2 = tbF.n2, np32 = (int)npts;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < np32; idx += gridDim.x * blockDim.x) {
+        const int rest = idx / n1;
+        const int i = idx - rest * n1;
+        const int k = rest / n2;
+        const int j = rest - k * n2;
+        const long long cidx = (long long)rest * n1q + i;
+        float w[kMaxSpecies], m[kMaxSpecies];
+        float2 wc[kMaxSpecies];
+        for (int r = 0; r < kMaxSpecies; ++r) {
+            wc[r] = r < tbF.S ? split_f64(__ldg(W + r * npts + idx)) : make_float2(0.f, 0.f);
+            w[r] = wc[r].x + wc[r].y;
+            m[r] = r < tbF.S ? __ldg(mu + r * ys + cidx) : 0.f;
+        }
+        reaction_param_parts_f32(tbF.reac, w, m, part);
+        for (int r = 0; r < tbF.S; ++r) {
+            part[np + r] += (double)m[r] * (double)laplacian<SplitAcc, GEO>(tbF, W + r * npts, idx, i, j, k, wc[r]);
+            const float* x = mu + r * ys + cidx;
+            const float t0 = axis_term_t32(tbT.ax[0], x, i, 1);
+            const float t1 = axis_term_t32(tbT.ax[1], x, j, n1q);
+            float mt;
+            if constexpr (GEO == GEO_DISK) mt = t0 + tbT.Dr[i] * t1;
+            else if constexpr (GEO == GEO_SPHERE) mt = tbT.Dp[j] * t0 + t1;
+            else {
+                const float t2 = axis_term_t32(tbT.ax[2], x, k, (long long)n1q * n2);
+                if constexpr (GEO == GEO_BALL) mt = t0 + tbT.Dr[i] * (tbT.Dp[k] * t1 + t2);
+                else mt = t0 + tbT.Dr[i] * t1 + t2;
+            }
+            lam[r * npts + idx] += (double)(tbF.d[r] * mt + reaction_jt_t<float>(tbF.reac, w, m, r));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kFusedSlots; ++q) {
+        double v = part[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < np + tbF.S) {
+        const int q = threadIdx.x;
+        double v = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) v += red[q][w8];
+        atomicAdd(&acc[q < np ? q : 16 + (q - np)], v);
+    }
+}
+
 // acc[slot + s] += sum_p a[s][p] b[s][p] (wt ? wt[s][p] : 1) * scale for every species s.
 __global__ void __launch_bounds__(256) k_wdot(const double* __restrict__ a, const double* __restrict__ b,
                                               const double* __restrict__ wt, long long npts, double scale,
@@ -472,6 +666,35 @@ cudaError_t launch_from_chain_f32(const float* src, double* dst, int n1, int n1q
 cudaError_t launch_dot_state_chain(const double* a, const float* b, int n1, int n1q, long long ys, long long npts,
                                    int S, double* acc, cudaStream_t st) {
     k_dot_state_chain<<<dim3((unsigned)helper_blocks(npts, 152LL * 2), S), 256, 0, st>>>(a, b, n1, n1q, ys, npts, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_fused(int geometry, const RhsTables<double>& tb, const RhsTables<double>& tbT, const double* W,
+                             const double* mu, double* lam, double* acc, int np, cudaStream_t st) {
+    if (np + tb.S > kFusedSlots) return cudaErrorInvalidValue;
+    long long blocks = (tb.npts + 255) / 256;
+    if (blocks > 152LL * 4) blocks = 152LL * 4;
+    switch (geometry) {
+    case GEO_DISK: k_adj_fused<GEO_DISK><<<(int)blocks, 256, 0, st>>>(tb, tbT, W, mu, lam, acc, np); break;
+    case GEO_SPHERE: k_adj_fused<GEO_SPHERE><<<(int)blocks, 256, 0, st>>>(tb, tbT, W, mu, lam, acc, np); break;
+    case GEO_BALL: k_adj_fused<GEO_BALL><<<(int)blocks, 256, 0, st>>>(tb, tbT, W, mu, lam, acc, np); break;
+    default: k_adj_fused<GEO_CYLINDER><<<(int)blocks, 256, 0, st>>>(tb, tbT, W, mu, lam, acc, np); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_fused_split(int geometry, const RhsTables<float>& tbF, const RhsTables<float>& tbT,
+                                   const double* W, const float* mu, int n1q, long long ys, double* lam, double* acc,
+                                   int np, cudaStream_t st) {
+    if (np + tbF.S > kFusedSlots) return cudaErrorInvalidValue;
+    long long blocks = (tbF.npts + 255) / 256;
+    if (blocks > 152LL * 4) blocks = 152LL * 4;
+    switch (geometry) {
+    case GEO_DISK: k_adj_fused_split<GEO_DISK><<<(int)blocks, 256, 0, st>>>(tbF, tbT, W, mu, n1q, ys, lam, acc, np); break;
+    case GEO_SPHERE: k_adj_fused_split<GEO_SPHERE><<<(int)blocks, 256, 0, st>>>(tbF, tbT, W, mu, n1q, ys, lam, acc, np); break;
+    case GEO_BALL: k_adj_fused_split<GEO_BALL><<<(int)blocks, 256, 0, st>>>(tbF, tbT, W, mu, n1q, ys, lam, acc, np); break;
+    default: k_adj_fused_split<GEO_CYLINDER><<<(int)blocks, 256, 0, st>>>(tbF, tbT, W, mu, n1q, ys, lam, acc, np); break;
+    }
     return cudaGetLastError();
 }
 

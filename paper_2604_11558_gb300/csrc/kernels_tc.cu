@@ -1204,10 +1204,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcSh
     extern __shared__ char smem_raw[];
     const uint32_t tmem_cols = sh.tmem_cols;
     CtaRes R = cta_begin(smem_raw, sh, T.err);
-    const int s = blockIdx.z, nt = blockIdx.y;
+    const bool second = (int)blockIdx.z >= T.S;            // phi_pair: the second image set into Y3
+    const int s = second ? blockIdx.z - T.S : blockIdx.z, nt = blockIdx.y;
     const int n1 = T.n1, n2 = T.n2, n1q = T.n1q, NT = T.phi_nt;
     const int i0 = blockIdx.x * kRows;
-    Image mat = T.Pphi[s];
+    Image mat = second ? T.Pphi2[s] : T.Pphi[s];
     mat.ptr += (long long)nt * mat.k_chunks * mat.chunk_floats;
     GemmSpec gs[1] = {{mat, 0, kRows, 1, NT, mat.k_chunks, R.tmem}};
     if (threadIdx.x >= kThreads + 32) {
@@ -1229,7 +1230,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcSh
             R.P, gs[0],
             [&](int c, Pre8& p) { load8_strided(p, Yi, n1q, c * 16 + h * 8, n2, valid); },
             [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
-        float* Yo = T.Y2 + (long long)s * T.ys + i;
+        float* Yo = (second ? T.Y3 : T.Y2) + (long long)s * T.ys + i;
         for (int c = 0; c < NT / 16; ++c) {
             float v[8];
             tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
@@ -1309,6 +1310,106 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, Tc
         double* W = T.state_upd + (long long)s * n12 + (long long)j0 * n1 + i0;
         update_rows(R.tmem + (uint32_t)n1p, min(kRows, n2 - j0), min(NT, n1 - i0), NT, W, W, T.tau,
                     R.P.mat_slots, n1);
+    }
+    cta_end(R, tmem_cols);
+}
+
+// Adjoint theta step of the split sphere (the transposed eq. ee_sphere): rows = 128 phi rows j of
+// species blockIdx.y, output theta columns [z th_nt, (z + 1) th_nt).  G1: X = lambda x_1 Q_theta^T
+// (lambda rounded to FP32, chain layout); G2a: Za = (Phi o X) x_1 Q_theta and G2b: Zb =
+// (dPhi/dd o X) x_1 Q_theta for the group's columns.  Epilogue: tau Za (= tau P_theta lambda, P_theta
+// symmetric) into A.tpl, and <tau Zb, Y2> + <tau Za, Y3> into A.acc_d[s].  Accumulators: G1 at
+// [0, n1p), G2a at [n1p, n1p + th_nt), G2b after it.
+__global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta_adj(SplitTables T, TcShape sh, SphereAdjArgs A) {
+    extern __shared__ char smem_raw[];
+    __shared__ double red[kThreads / 32];
+    const uint32_t tmem_cols = sh.tmem_cols;
+    CtaRes R = cta_begin(smem_raw, sh, T.err);
+    const int s = blockIdx.y, z = blockIdx.z;
+    const int n1 = T.n1, n2 = T.n2, n1q = T.n1q, NT = T.th_nt;
+    const int n1p = (n1 + 15) & ~15;
+    const int j0 = blockIdx.x * kRows;
+    Image qz = T.Qsph;
+    qz.ptr += (long long)z * qz.k_chunks * qz.chunk_floats;
+    GemmSpec gs[3] = {{T.QT, 0, kRows, 1, n1p, n1p / kKC, R.tmem},
+                      {qz, 0, kRows, 1, NT, n1p / kKC, R.tmem + (uint32_t)n1p},
+                      {qz, 0, kRows, 1, NT, n1p / kKC, R.tmem + (uint32_t)(n1p + NT)}};
+    if (threadIdx.x >= kThreads + 32) {
+        pdl_trigger();
+        mma_issuer(R.P, gs, 3);
+    } else if (threadIdx.x >= kThreads) {
+        pdl_trigger();
+        tma_issuer(R.P, gs, 3);
+    } else {
+        pdl_wait();
+        pdl_trigger();
+        const int tid = threadIdx.x;
+        const int r = tid & (kRows - 1), h = tid >> 7;
+        const uint32_t lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
+        const int j = j0 + r;
+        const bool valid = j < n2;
+        const long long roff = (long long)s * T.ys + (long long)(valid ? j : 0) * n1q;
+        // lambda rounded to FP32 in the chain layout: eight consecutive theta values of row j in two
+        // 16-byte loads (n1q and the 8-column groups keep them aligned)
+        const float* lrow = A.lam32 + roff;
+        run_gemm(
+            R.P, gs[0],
+            [&](int c, Pre8& p) {
+                const int i = c * 16 + h * 8;
+                if (valid && i + 8 <= n1q) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(lrow + i));
+                    const float4 b = __ldg(reinterpret_cast<const float4*>(lrow + i + 4));
+                    p.v[0] = a.x; p.v[1] = a.y; p.v[2] = a.z; p.v[3] = a.w;
+                    p.v[4] = b.x; p.v[5] = b.y; p.v[6] = b.z; p.v[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) p.v[q] = (valid && i + q < n1q) ? __ldg(lrow + i + q) : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (i + q >= n1) p.v[q] = 0.f;
+            },
+            [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
+        auto load_had = [&](const float* row) {
+            return [=](int c, Pre8& p) {
+                const int i = c * 16 + h * 8;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) p.v[q] = (valid && i + q < n1) ? __ldg(row + i + q) : 0.f;
+            };
+        };
+        auto hadamard = [&](int c, char* hi, char* lo, const Pre8& p) {
+            float v[8];
+            tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
+            store_row8(hi, lo, r, h, v);
+        };
+        run_gemm(R.P, gs[1], load_had(T.had_sph + roff), hadamard);
+        run_gemm(R.P, gs[2], load_had(A.had_d + roff), hadamard);
+        const int i0 = z * NT;
+        double dot = 0.0;
+        for (int c = 0; c < NT / 16; ++c) {
+            float va[8], vb[8];
+            tmem_ld8(R.tmem + lane_base + (uint32_t)(n1p + c * 16 + h * 8), va);
+            tmem_ld8(R.tmem + lane_base + (uint32_t)(n1p + NT + c * 16 + h * 8), vb);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + c * 16 + h * 8 + q;
+                if (valid && i < n1) {
+                    const float ta = T.tau * va[q], tb = T.tau * vb[q];
+                    A.tpl[roff + i] = ta;
+                    dot += (double)tb * (double)__ldg(A.Y2 + roff + i) + (double)ta * (double)__ldg(A.Y3 + roff + i);
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+        if ((tid & 31) == 0) red[tid >> 5] = dot;
+        compute_sync();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w8 = 0; w8 < kThreads / 32; ++w8) t += red[w8];
+            atomicAdd(A.acc_d + s, t);
+        }
     }
     cta_end(R, tmem_cols);
 }
@@ -1544,6 +1645,27 @@ TcShape tc_sphere_theta_shape(int n1, int nt) {
     return sh;
 }
 
+// Adjoint theta kernel: matrices n1p rows, accumulators n1p + 2 nt columns, no update staging.
+TcShape tc_sphere_theta_adj_shape(int n1, int nt) {
+    TcShape sh{};
+    const uint32_t n1p = round_up(n1, 16);
+    sh.data_bytes = 2u * kRows * kTileRowBytes;
+    sh.mat_bytes = 2u * n1p * kTileRowBytes;
+    sh.tmem_cols = pow2_cols(n1p + 2u * (uint32_t)nt);
+    rings(sh, 0, sh.tmem_cols <= 256);
+    return sh;
+}
+
+cudaError_t launch_tc_sphere_theta_adj(const SplitTables& T, const TcShape& sh, const SphereAdjArgs& A,
+                                       cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_sphere_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sh.smem_bytes);
+    if (e != cudaSuccess) return e;
+    const int n1p = (T.n1 + 15) & ~15;
+    dim3 grid((T.n2 + kRows - 1) / kRows, T.S, (n1p + T.th_nt - 1) / T.th_nt);
+    return launch_pdl(k_tc_sphere_theta_adj, grid, dim3(kBlock), sh.smem_bytes, st, T, sh, A);
+}
+
 cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_sphere_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_phi);
     if (e == cudaSuccess)
@@ -1553,7 +1675,7 @@ cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta) {
 
 cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     const int n2p = (T.n2 + 15) & ~15;
-    dim3 grid((T.n1 + kRows - 1) / kRows, (n2p + T.phi_nt - 1) / T.phi_nt, T.S);
+    dim3 grid((T.n1 + kRows - 1) / kRows, (n2p + T.phi_nt - 1) / T.phi_nt, T.phi_pair ? 2 * T.S : T.S);
     return launch_pdl(k_tc_sphere_phi, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
 }
 

@@ -22,6 +22,14 @@ cudaError_t launch_adj_lambda(int geometry, const RhsTables<double>& tb, const d
                               double* lam, cudaStream_t st);
 cudaError_t launch_adj_params(int geometry, const RhsTables<double>& tb, const double* W, const double* mu,
                               double* acc, cudaStream_t st);
+// lambda += d M^T mu + J^T mu and the parameter sums in one pass (np reaction parameters + S <= 8).
+cudaError_t launch_adj_fused(int geometry, const RhsTables<double>& tb, const RhsTables<double>& tbT, const double* W,
+                             const double* mu, double* lam, double* acc, int np, cudaStream_t st);
+// The same for the split-TF32 adjoint in FP32 arithmetic: mu (FP32, chain layout [s][rows][n1q]) with
+// M^T in difference form (tbT), M w from split pairs of the state (tbF), lambda and the sums FP64.
+cudaError_t launch_adj_fused_split(int geometry, const RhsTables<float>& tbF, const RhsTables<float>& tbT,
+                                   const double* W, const float* mu, int n1q, long long ys, double* lam, double* acc,
+                                   int np, cudaStream_t st);
 cudaError_t launch_wdot(const double* a, const double* b, const double* wt, long long npts, int S, double scale,
                         double* acc, cudaStream_t st);
 cudaError_t launch_scale(double* x, double a, long long n, cudaStream_t st);
@@ -59,6 +67,11 @@ TcShape tc_sphere_theta_shape(int n1, int nt);
 cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta);
 cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaStream_t st);
 cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cudaStream_t st);
+// Split sphere adjoint: G1 = lambda x_1 Q^T, the Phi and dPhi/dd products x_1 Q, tau P_theta lambda out,
+// the two d-derivative dots accumulated (see k_tc_sphere_theta_adj).
+TcShape tc_sphere_theta_adj_shape(int n1, int nt);
+cudaError_t launch_tc_sphere_theta_adj(const SplitTables& T, const TcShape& sh, const SphereAdjArgs& A,
+                                       cudaStream_t st);
 int rhs_candidates(const SplitTables& T, int3* out, int max_out);
 // Batched disks: one persistent launch per step.
 TcShape tc_batch_shape(int max_n1, int max_n2, uint32_t tmem_cols);

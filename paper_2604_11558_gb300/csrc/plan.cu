@@ -837,6 +837,14 @@ void free_plan(sexpe_plan* p) {
     free_plan(p->sub[1]);
     free_profile(p);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->sadj_stream) {
+        cudaStreamSynchronize(p->sadj_stream);
+        cudaStreamDestroy(p->sadj_stream);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (p->sadj_ev_replayed[b]) cudaEventDestroy(p->sadj_ev_replayed[b]);
+        if (p->sadj_ev_swept[b]) cudaEventDestroy(p->sadj_ev_swept[b]);
+    }
     for (void* a : p->allocs) cudaFree(a);
     delete p;
 }
@@ -1223,8 +1231,40 @@ sexpe_status build_adjoint(sexpe_plan* p, cudaStream_t st) {
 // Every product runs on the forward's tensor-core kernels (split TF32, FP32 accumulation) with
 // the transposed / differentiated operand images; lambda and the parameter sums stay FP64.
 
+// FP32 tables of M^T in difference form: per axis the transpose's off-diagonals,
+// (A^T)_{r,r-1} = A_{r-1,r} and (A^T)_{r,r+1} = A_{r+1,r} (with the periodic wrap), and its column
+// sums in the rs slot (zero where they vanish, as for the symmetric circulant A_theta); the
+// diagonal factors, diffusion and reaction as in the forward tables `base`.
+sexpe_status build_transposed_tables_f32(sexpe_plan* p, const RhsTables<float>& base, RhsTables<float>* out,
+                                         cudaStream_t st) {
+    *out = base;
+    for (int m = 0; m < p->ndim; ++m) {
+        const Axis& a = p->ax[m];
+        const int n = a.n;
+        std::vector<float> lo(n), up(n), cs(n);
+        for (int r = 0; r < n; ++r) {
+            const bool has_m = r > 0 || a.periodic, has_p = r < n - 1 || a.periodic;
+            const double l = has_m ? a.upper[(r + n - 1) % n] : 0.0;
+            const double u = has_p ? a.lower[(r + 1) % n] : 0.0;
+            const double sum = a.diag[r] + l + u;
+            lo[r] = (float)l;
+            up[r] = (float)u;
+            cs[r] = (float)(std::fabs(sum) <= 1e-9 * std::fabs(a.diag[r]) ? 0.0 : sum);
+        }
+        StencilAxis<float> sa{};
+        SX_TRY(upload(p, lo, &sa.lower, st));
+        SX_TRY(upload(p, up, &sa.upper, st));
+        SX_TRY(upload(p, cs, &sa.rs, st));
+        sa.n = n;
+        sa.periodic = a.periodic ? 1 : 0;
+        out->ax[m] = sa;
+    }
+    return SEXPE_OK;
+}
+
 sexpe_status build_adjoint_split(sexpe_plan* p, cudaStream_t st) {
     if (p->sadj_built) return SEXPE_OK;
+    SX_TRY(build_transposed_tables_f32(p, p->tabs.rhs, &p->sadj_rhsT, st));
     SX_TRY(build_rhs_tables<double>(p, &p->rhs64, st));
     p->adj_diag = p->rhs64;                      // M^T: same off-diagonals, the full diagonal in rs
     for (int m = 0; m < p->ndim; ++m) {
@@ -1286,57 +1326,132 @@ sexpe_status build_adjoint_split(sexpe_plan* p, cudaStream_t st) {
     SX_TRY(alloc_dev(p, e64, &p->sadj_T64[1]));
     SX_TRY(alloc_dev(p, e64, &p->sadj_MU));
     if (!p->adj_red) SX_TRY(alloc_dev(p, 32, &p->adj_red));
+    // The merged adjoint theta kernel holds three accumulators (n1p + 2 nt columns): time it at every
+    // column split the setup built whose shape fits, on the (zeroed) work buffers, and keep the fastest.
+    SX_CUDA(cudaMemsetAsync(p->sadj_T64[0], 0, sizeof(double) * 32, st));
+    float* zchain = p->sadj_Y3;                 // zeroed chain buffer: lambda, P_phi F, dP_phi F inputs
+    cudaEvent_t ev[2];
+    SX_CUDA(cudaEventCreate(&ev[0]));
+    SX_CUDA(cudaEventCreate(&ev[1]));
+    float best = 1e30f;
+    cudaError_t te = cudaSuccess;
+    for (size_t c = 0; c < p->th_splits.size() && te == cudaSuccess; ++c) {
+        const int nt = rup16(n1) / p->th_splits[c];
+        const TcShape sh = tc_sphere_theta_adj_shape(n1, nt);
+        if (sh.tmem_cols > 512 || sh.smem_bytes > 227u * 1024u) continue;
+        SplitTables Ta = T;
+        Ta.th_nt = nt;
+        Ta.Qsph = p->th_imgs[c];
+        const SphereAdjArgs A{zchain, p->sadj_had_d, p->sadj_Ymu, zchain, zchain, p->sadj_T64[0]};
+        float ms = 0.f;
+        te = launch_tc_sphere_theta_adj(Ta, sh, A, st);
+        if (te == cudaSuccess) te = cudaEventRecord(ev[0], st);
+        for (int r = 0; r < 3 && te == cudaSuccess; ++r) te = launch_tc_sphere_theta_adj(Ta, sh, A, st);
+        if (te == cudaSuccess) te = cudaEventRecord(ev[1], st);
+        if (te == cudaSuccess) te = cudaEventSynchronize(ev[1]);
+        if (te == cudaSuccess) te = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (te == cudaSuccess && ms < best) {
+            best = ms;
+            p->sadj_shape = sh;
+            p->sadj_nt = nt;
+            p->sadj_Q = p->th_imgs[c];
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    SX_CUDA(te);
+    p->sadj_merged = best < 1e30f;
+    SX_CUDA(cudaMemsetAsync(p->sadj_Ymu, 0, sizeof(float) * yf, st));
     SX_CUDA(cudaStreamSynchronize(st));
     p->sadj_built = true;
     return SEXPE_OK;
 }
 
+// The forward quantities an adjoint step of the split sphere plan reads at the state W: F into
+// Y (chain layout), P_phi F into Y2 and (dP_phi/dd) F into Y3; with `upd`, the theta kernel then
+// completes the forward step into upd (which holds a copy of W), as sexpe_step would.
+sexpe_status split_forward_parts(sexpe_plan* p, const double* W, float* Y, float* Y2, float* Y3, double* upd,
+                                 cudaStream_t st) {
+    SplitTables T = p->tabs;
+    T.state = W;
+    T.Y = Y;
+    T.Y2 = Y2;
+    SX_CUDA(launch_rhs_split(T, st));
+    SplitTables Td = T;                           // P_phi F and (dP_phi/dd) F in one launch
+    Td.Y3 = Y3;
+    for (int s = 0; s < p->S; ++s) Td.Pphi2[s] = p->sadj_dPphi[s];
+    Td.phi_pair = 1;
+    SX_CUDA(launch_tc_sphere_phi(Td, p->sh3, st));
+    if (upd) {
+        T.state_upd = upd;
+        SX_CUDA(launch_tc_sphere_theta(T, p->shs, st));
+    }
+    return SEXPE_OK;
+}
+
 // One adjoint step of the split sphere plan at the state W_n: lam (FP64, state layout) goes from
-// lambda_{n+1} to lambda_n; the parameter gradient accumulates in p->adj_red.
-sexpe_status adjoint_step_split(sexpe_plan* p, const double* Wn, double* lam, cudaStream_t st) {
+// lambda_{n+1} to lambda_n; the parameter gradient accumulates in p->adj_red.  Y2 = P_phi F and
+// Y3 = (dP_phi/dd) F at W_n come from the segment replay.
+sexpe_status adjoint_step_split(sexpe_plan* p, const double* Wn, const float* Y2, const float* Y3, double* lam,
+                                cudaStream_t st) {
     const SplitTables& T0 = p->tabs;
     const size_t e64 = (size_t)p->S * p->npts;
     const int n1 = p->n[0];
     double* acc_d = p->adj_red + 16;
-    // forward quantities at W_n: F (T.Y), P_phi F (T.Y2), (dP_phi/dd) F (Y3)
-    SplitTables T = T0;
-    T.state = Wn;
-    SX_CUDA(launch_rhs_split(T, st));
-    SX_CUDA(launch_tc_sphere_phi(T, p->sh3, st));
-    SplitTables Td = T;
-    Td.Y2 = p->sadj_Y3;
-    for (int s = 0; s < p->S; ++s) Td.Pphi[s] = p->sadj_dPphi[s];
-    SX_CUDA(launch_tc_sphere_phi(Td, p->sh3, st));
-    // tau P_theta lambda and tau (dP_theta/dd) lambda: the theta kernel's update adds tau x its
-    // product to a zeroed FP64 buffer
-    SX_CUDA(launch_to_chain_f32(lam, p->sadj_Yl, n1, T0.n1q, T0.ys, p->npts, p->S, st));
-    for (int q = 0; q < 2; ++q) {
-        SplitTables Tt = T0;
-        Tt.Y2 = p->sadj_Yl;
-        if (q == 1) Tt.had_sph = p->sadj_had_d;
-        Tt.state_upd = p->sadj_T64[q];
-        SX_CUDA(cudaMemsetAsync(p->sadj_T64[q], 0, sizeof(double) * e64, st));
-        SX_CUDA(launch_tc_sphere_theta(Tt, p->shs, st));
+    if (p->sadj_merged) {
+        // one kernel: tau P_theta lambda into the chain buffer and both d-derivative dots
+        SX_CUDA(launch_to_chain_f32(lam, p->sadj_Yl, n1, T0.n1q, T0.ys, p->npts, p->S, st));
+        SplitTables Ta = T0;
+        Ta.th_nt = p->sadj_nt;
+        Ta.Qsph = p->sadj_Q;
+        const SphereAdjArgs A{p->sadj_Yl, p->sadj_had_d, p->sadj_Ymu, Y2, Y3, acc_d};
+        SX_CUDA(launch_tc_sphere_theta_adj(Ta, p->sadj_shape, A, st));
+    } else {
+        // tau P_theta lambda and tau (dP_theta/dd) lambda: the theta kernel's update adds tau x its
+        // product to a zeroed FP64 buffer
+        SX_CUDA(launch_to_chain_f32(lam, p->sadj_Yl, n1, T0.n1q, T0.ys, p->npts, p->S, st));
+        for (int q = 0; q < 2; ++q) {
+            SplitTables Tt = T0;
+            Tt.Y2 = p->sadj_Yl;
+            if (q == 1) Tt.had_sph = p->sadj_had_d;
+            Tt.state_upd = p->sadj_T64[q];
+            SX_CUDA(cudaMemsetAsync(p->sadj_T64[q], 0, sizeof(double) * e64, st));
+            SX_CUDA(launch_tc_sphere_theta(Tt, p->shs, st));
+        }
+        // d-derivative terms: <tau dP_theta lambda, P_phi F> + <tau P_theta lambda, dP_phi F>
+        SX_CUDA(launch_dot_state_chain(p->sadj_T64[1], Y2, n1, T0.n1q, T0.ys, p->npts, p->S, acc_d, st));
+        SX_CUDA(launch_dot_state_chain(p->sadj_T64[0], Y3, n1, T0.n1q, T0.ys, p->npts, p->S, acc_d, st));
+        SX_CUDA(launch_to_chain_f32(p->sadj_T64[0], p->sadj_Yl, n1, T0.n1q, T0.ys, p->npts, p->S, st));
     }
-    // d-derivative terms: <tau dP_theta lambda, P_phi F> + <tau P_theta lambda, dP_phi F>
-    SX_CUDA(launch_dot_state_chain(p->sadj_T64[1], T0.Y2, n1, T0.n1q, T0.ys, p->npts, p->S, acc_d, st));
-    SX_CUDA(launch_dot_state_chain(p->sadj_T64[0], p->sadj_Y3, n1, T0.n1q, T0.ys, p->npts, p->S, acc_d, st));
     // mu = P_phi^T (tau P_theta lambda)
-    SX_CUDA(launch_to_chain_f32(p->sadj_T64[0], p->sadj_Yl, n1, T0.n1q, T0.ys, p->npts, p->S, st));
     SplitTables Tm = T0;
-    Tm.Y = p->sadj_Yl;
-    Tm.Y2 = p->sadj_Ymu;
+    Tm.Y = p->sadj_merged ? p->sadj_Ymu : p->sadj_Yl;
+    Tm.Y2 = p->sadj_merged ? p->sadj_Yl : p->sadj_Ymu;
     for (int s = 0; s < p->S; ++s) Tm.Pphi[s] = p->sadj_PphiT[s];
     SX_CUDA(launch_tc_sphere_phi(Tm, p->sh3, st));
-    SX_CUDA(launch_from_chain_f32(p->sadj_Ymu, p->sadj_MU, n1, T0.n1q, T0.ys, p->npts, p->S, st));
-    // reaction-parameter and <mu, M w> sums, then lambda += (d M + J_g)^T mu
-    SX_CUDA(launch_adj_params(p->geometry, p->rhs64, Wn, p->sadj_MU, p->adj_red, st));
-    SX_CUDA(launch_adj_lambda(p->geometry, p->adj_diag, Wn, p->sadj_MU, lam, st));
+    // reaction-parameter and <mu, M w> sums, and lambda += (d M + J_g)^T mu, in one pass
+    const int np = (int)p->params.size();
+    if (np + p->S <= 8 && p->tabs.rhs.reac.lifted == 0) {
+        SX_CUDA(launch_adj_fused_split(p->geometry, p->tabs.rhs, p->sadj_rhsT, Wn, Tm.Y2, T0.n1q, T0.ys, lam,
+                                       p->adj_red, np, st));
+        return SEXPE_OK;
+    }
+    SX_CUDA(launch_from_chain_f32(Tm.Y2, p->sadj_MU, n1, T0.n1q, T0.ys, p->npts, p->S, st));
+    if (np + p->S <= 8) {
+        SX_CUDA(launch_adj_fused(p->geometry, p->rhs64, p->adj_diag, Wn, p->sadj_MU, lam, p->adj_red, np, st));
+    } else {
+        SX_CUDA(launch_adj_params(p->geometry, p->rhs64, Wn, p->sadj_MU, p->adj_red, st));
+        SX_CUDA(launch_adj_lambda(p->geometry, p->adj_diag, Wn, p->sadj_MU, lam, st));
+    }
     return SEXPE_OK;
 }
 
-// sexpe_adjoint for a split-TF32 sphere plan: per checkpoint segment, the states are replayed by
-// the split forward step and kept, then the adjoint steps run backwards over them.
+// sexpe_adjoint for a split-TF32 sphere plan.  Per checkpoint segment the states are replayed by
+// the split forward step (keeping each step's F, P_phi F and (dP_phi/dd) F), then the adjoint steps
+// run backwards over them.  The replay of segment c - 1 does not depend on the adjoint variable, so
+// it runs on a second stream into the other half of double-buffered segment storage while the
+// adjoint steps of segment c run on `st` (both are chains of small, latency-bound launches that
+// leave most SMs idle); events order each buffer's reuse.
 sexpe_status adjoint_split(sexpe_plan* p, const double* checkpoints, int n_ckpt, int every, const double* dL_dWT,
                            double* dL_dW0, double* dL_dparams, cudaStream_t st) {
     try {
@@ -1347,24 +1462,57 @@ sexpe_status adjoint_split(sexpe_plan* p, const double* checkpoints, int n_ckpt,
         return SEXPE_ENUMERIC;
     }
     const size_t E = (size_t)p->S * p->npts;
-    if (p->adj_seg_cap < every) {
+    const size_t yf = (size_t)p->S * p->tabs.ys;
+    if (p->sadj_seg_cap < every) {
         double* seg = nullptr;
-        SX_TRY(alloc_dev(p, (size_t)every * E, &seg));
-        p->adj_seg = seg;
-        p->adj_seg_cap = every;
+        float* parts = nullptr;
+        SX_TRY(alloc_dev(p, (size_t)2 * every * E, &seg));
+        SX_TRY(alloc_dev(p, (size_t)2 * 3 * every * yf, &parts));
+        SX_CUDA(cudaMemsetAsync(parts, 0, sizeof(float) * (size_t)2 * 3 * every * yf, st));   // padding stays zero
+        p->sadj_states = seg;
+        p->sadj_seg = parts;
+        p->sadj_seg_cap = every;
     }
+    if (!p->sadj_stream) {
+        SX_CUDA(cudaStreamCreateWithFlags(&p->sadj_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            SX_CUDA(cudaEventCreateWithFlags(&p->sadj_ev_replayed[b], cudaEventDisableTiming));
+            SX_CUDA(cudaEventCreateWithFlags(&p->sadj_ev_swept[b], cudaEventDisableTiming));
+        }
+    }
+    cudaStream_t st2 = p->sadj_stream;
+    auto state = [&](int b, int j) { return p->sadj_states + ((size_t)b * every + j) * E; };
+    auto part = [&](int b, int j, int q) { return p->sadj_seg + (((size_t)b * every + j) * 3 + q) * yf; };
+    auto replay = [&](int c, int b, cudaStream_t s) -> sexpe_status {
+        SX_CUDA(cudaMemcpyAsync(state(b, 0), checkpoints + (size_t)c * E, E * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+        for (int j = 0; j < every; ++j) {
+            double* next = j + 1 < every ? state(b, j + 1) : nullptr;
+            if (next) SX_CUDA(cudaMemcpyAsync(next, state(b, j), E * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            SX_TRY(split_forward_parts(p, state(b, j), part(b, j, 0), part(b, j, 1), part(b, j, 2), next, s));
+        }
+        return SEXPE_OK;
+    };
     double* lam = dL_dW0;                      // the adjoint variable lives in the output buffer
     if (lam != dL_dWT) SX_CUDA(cudaMemcpyAsync(lam, dL_dWT, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
     SX_CUDA(cudaMemsetAsync(p->adj_red, 0, 32 * sizeof(double), st));
+    // the second stream starts after everything enqueued on `st` so far (the checkpoints included)
+    SX_CUDA(cudaEventRecord(p->sadj_ev_swept[0], st));
+    SX_CUDA(cudaEventRecord(p->sadj_ev_swept[1], st));
+    SX_CUDA(cudaStreamWaitEvent(st2, p->sadj_ev_swept[0], 0));
+    SX_TRY(replay(n_ckpt - 1, 0, st2));
+    SX_CUDA(cudaEventRecord(p->sadj_ev_replayed[0], st2));
     for (int c = n_ckpt - 1; c >= 0; --c) {
-        SX_CUDA(cudaMemcpyAsync(p->adj_seg, checkpoints + (size_t)c * E, E * sizeof(double), cudaMemcpyDeviceToDevice,
-                                st));
-        for (int j = 1; j < every; ++j) {
-            double* w = p->adj_seg + (size_t)j * E;
-            SX_CUDA(cudaMemcpyAsync(w, w - E, E * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            SX_TRY(enqueue_step(p, w, st));
+        const int b = (n_ckpt - 1 - c) & 1;
+        if (c > 0) {                           // next segment's replay into the other buffer
+            SX_CUDA(cudaStreamWaitEvent(st2, p->sadj_ev_swept[b ^ 1], 0));
+            SX_TRY(replay(c - 1, b ^ 1, st2));
+            SX_CUDA(cudaEventRecord(p->sadj_ev_replayed[b ^ 1], st2));
         }
-        for (int j = every - 1; j >= 0; --j) SX_TRY(adjoint_step_split(p, p->adj_seg + (size_t)j * E, lam, st));
+        SX_CUDA(cudaStreamWaitEvent(st, p->sadj_ev_replayed[b], 0));
+        for (int j = every - 1; j >= 0; --j)
+            SX_TRY(adjoint_step_split(p, state(b, j), part(b, j, 1), part(b, j, 2), lam, st));
+        SX_CUDA(cudaEventRecord(p->sadj_ev_swept[b], st));
     }
     if (dL_dparams) {
         double red[32];

@@ -86,6 +86,16 @@ struct sexpe_plan {
     float* sadj_Ymu = nullptr;             // mu in the chain layout
     double* sadj_T64[2] = {nullptr, nullptr};   // tau P_theta lambda, tau (d P_theta / d d_s) lambda
     double* sadj_MU = nullptr;             // mu in the state layout
+    double* sadj_states = nullptr;         // replayed states, two segment buffers of sadj_seg_cap states
+    float* sadj_seg = nullptr;             // per replayed step: F, P_phi F, (dP_phi/dd) F (chain layout), x 2
+    cudaStream_t sadj_stream = nullptr;    // replay stream (overlaps the adjoint steps of the segment after)
+    cudaEvent_t sadj_ev_replayed[2] = {nullptr, nullptr}, sadj_ev_swept[2] = {nullptr, nullptr};
+    bool sadj_merged = false;              // the merged adjoint theta kernel fits (tensor memory, smem)
+    sexpe::TcShape sadj_shape{};           // its rings and tensor-memory columns
+    int sadj_nt = 0;                       // its output theta columns per CTA (measured split)
+    sexpe::RhsTables<float> sadj_rhsT{};   // FP32 M^T in difference form (transposed off-diagonals, column sums)
+    sexpe::Image sadj_Q{};                 // the N-tiled Q_theta image of that split
+    int sadj_seg_cap = 0;                  // steps a segment buffer holds
     // batched independent disks (sexpe_batch_setup)
     bool batch = false;
     int n_instances = 1;

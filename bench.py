@@ -73,19 +73,82 @@ PROFILE_THETA_SPLIT = 8        # sphere 256 x 512: theta-kernel column split the
 def kernel_work(n, S):
     """Algorithmic bytes and tensor flops per launch of the three split-path kernels of the ball step.
 
-    stencil pass: reads the FP64 state once (8 B/DOF), writes F in FP32 (4 B/DOF); no tensor work.
-    mode-3 pass: reads F and writes Y in place (4 + 4 B/DOF); two mu-mode products of length n3
-      per point, three TF32 MMAs each: 3*2*2*n3 flop/DOF.
-    slab pass: reads Y (4 B/DOF), reads and writes the FP64 state (16 B/DOF);
-      products over theta, theta, rho: 3*2*(2*n2 + n1) flop/DOF.
+    The step's algorithmic HBM traffic is its FP64 state read once and written once, 16 B/DOF.
+    Per kernel, `bytes` counts only that work: the stencil pass reads the state (8 B/DOF); the
+    mode-3 pass touches intermediates only (0: it is bounded by its tensor work); the slab pass
+    reads and writes the state in its update (16 B/DOF).  `bytes_with_intermediates` adds the FP32
+    chain buffer each pass moves (F written by the stencil, read and rewritten by mode-3, read by the
+    slab: 4 B/DOF per touch).  Tensor flops: three TF32 MMAs per product, 2 flop per
+    multiply-add; mode-3 two products of length n3 per point, the slab products over theta, theta,
+    rho.
     """
     n1, n2, n3 = n
     dof = S * n1 * n2 * n3
     return {
-        "stencil": {"bytes": 12 * dof, "flops": 0},
-        "k_tc_mode3": {"bytes": 8 * dof, "flops": 3 * 2 * 2 * n3 * dof},
-        "k_tc_slab": {"bytes": 20 * dof, "flops": 3 * 2 * (2 * n2 + n1) * dof},
+        "stencil": {"bytes": 8 * dof, "bytes_with_intermediates": 12 * dof, "flops": 0},
+        "k_tc_mode3": {"bytes": 0, "bytes_with_intermediates": 8 * dof, "flops": 3 * 2 * 2 * n3 * dof},
+        "k_tc_slab": {"bytes": 16 * dof, "bytes_with_intermediates": 20 * dof,
+                      "flops": 3 * 2 * (2 * n2 + n1) * dof},
     }
+
+
+def final_time_errors(line_steps=None):
+    """Per-species errors of the benchmark workloads at their final times against the oracle's stored
+    final states (tests/golden/final_time_*.npz, written by tests/golden/make_final_time_refs.py from
+    the oracle alone): relative 2-norm over the stored sample points, the largest sampled error
+    relative to the species' largest value, and the oracle's FP32-storage floor."""
+    import numpy as np
+    import torch
+    from paper_2604_11558_gb300 import binding
+    from paper_2604_11558_gb300 import workloads as wl
+    gold = os.path.join(ROOT, "tests", "golden")
+    out = {}
+
+    def cmp(got, idx, values, maxabs):
+        S = values.shape[0]
+        flat = got.reshape(S, -1)[:, idx]
+        return ([float(np.linalg.norm(flat[s] - values[s]) / np.linalg.norm(values[s])) for s in range(S)],
+                [float(np.max(np.abs(flat[s] - values[s])) / maxabs[s]) for s in range(S)])
+
+    for name, w, precs in (("ball", wl.gray_scott_ball(), ("split_tf32", "fp64")),
+                           ("cylinder", wl.linear_cubic_cylinder(), ("split_tf32",)),
+                           ("sphere", wl.schnakenberg_sphere(), ("split_tf32",))):
+        path = os.path.join(gold, f"final_time_{name}.npz")
+        if not os.path.exists(path):
+            continue
+        ref = np.load(path)
+        res = {"steps": int(ref["steps"]), "sampled_points_per_species": int(len(ref["idx"])),
+               "fp32_storage_floor": [float(v) for v in ref["floor"]]}
+        for prec in precs:
+            plan = binding.Plan.from_workload(w, precision=prec)
+            x = torch.from_numpy(np.ascontiguousarray(w["W0"])).cuda()
+            plan.step(x, int(ref["steps"]))
+            plan.synchronize()
+            rel, mx = cmp(x.cpu().numpy(), ref["idx"], ref["values"], ref["maxabs"])
+            res[prec] = {"rel_2norm_per_species": rel, "max_abs_rel_per_species": mx}
+            plan.close()
+        out[name] = res
+    path = os.path.join(gold, "final_time_batch.npz")
+    if os.path.exists(path):
+        ref = np.load(path)
+        ws = wl.batched_disks()
+        plan = binding.BatchPlan(ws)
+        off = plan.offsets()
+        x = torch.from_numpy(np.concatenate([w["W0"].ravel() for w in ws])).cuda()
+        plan.step(x, int(ref["steps"]))
+        plan.synchronize()
+        flat = x.cpu().numpy()
+        plan.close()
+        worst, worst_floor = 0.0, 0.0
+        for q in ref["pick"]:
+            q = int(q)
+            rel, _ = cmp(flat[off[q]:off[q + 1]].reshape(ws[q]["W0"].shape), ref[f"idx_{q}"], ref[f"values_{q}"],
+                         ref[f"maxabs_{q}"])
+            worst = max(worst, max(rel))
+            worst_floor = max(worst_floor, float(np.max(ref[f"floor_{q}"])))
+        out["batch"] = {"steps": int(ref["steps"]), "instances_checked": int(len(ref["pick"])),
+                        "split_tf32": {"worst_rel_2norm": worst}, "fp32_storage_floor_worst": worst_floor}
+    return out
 
 
 def load_peaks():
@@ -314,7 +377,7 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     state_bytes = dof * 8
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: algorithmic bytes (the state's read and write) and tensor flops
     names = ["stencil", "k_tc_mode3", "k_tc_slab"]   # stencil: the kernel the setup tuner picked
     work = kernel_work(n, S)
     hbm_gbs, bf16_tf, peak_kind = load_peaks()
@@ -322,8 +385,11 @@ def main():
     per_kernel = {}
     for nm, ms in zip(names, kernel_ms):
         bw = work[nm]["bytes"] / (ms * 1e-3) / 1e9
+        bwi = work[nm]["bytes_with_intermediates"] / (ms * 1e-3) / 1e9
         tf = work[nm]["flops"] / (ms * 1e-3) / 1e12 if work[nm]["flops"] else 0.0
-        per_kernel[nm] = {"ms": ms, "GB/s": bw, "TFLOP/s": tf, "hbm_frac": bw / hbm_gbs, "tensor_frac": tf / tf32_tf}
+        per_kernel[nm] = {"ms": ms, "GB/s": bw, "GB/s_with_intermediates": bwi, "TFLOP/s": tf,
+                          "hbm_frac": bw / hbm_gbs, "hbm_frac_with_intermediates": bwi / hbm_gbs,
+                          "tensor_frac": tf / tf32_tf}
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     d = per_kernel[dom]
     traffic = None
@@ -337,8 +403,16 @@ def main():
     else:
         roof = {"bound": "tensor", "achieved": d["TFLOP/s"], "peak": tf32_tf, "unit": "TFLOP/s",
                 "frac": d["tensor_frac"]}
-    roof.update({"traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)"
-                 if peak_kind == "measured" else "fallback", "per_kernel": per_kernel})
+    step_s = total_s / args.steps
+    roof.update({"traffic": traffic, "kernel": dom,
+                 "algorithmic_bytes_per_launch": work[dom]["bytes"],
+                 "frac_with_intermediates": d["hbm_frac_with_intermediates"],
+                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
+                 "whole_step": {"algorithmic_bytes": 16 * dof, "GB/s": 16 * dof / step_s / 1e9,
+                                "hbm_frac": 16 * dof / step_s / 1e9 / hbm_gbs,
+                                "tensor_flops": 3 * 2 * (2 * n[2] + 2 * n[1] + n[0]) * dof,
+                                "tensor_frac": 3 * 2 * (2 * n[2] + 2 * n[1] + n[0]) * dof / step_s / 1e12 / tf32_tf},
+                 "per_kernel": per_kernel})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -360,6 +434,7 @@ def main():
         "e2e": {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
         "roofline": roof,
+        "final_time_error": final_time_errors(),
         "gpu_launches": args.steps * info["kernels_per_step"],
         "clocks": clk,
         "setup_ms": info["setup_ms"],
@@ -383,8 +458,8 @@ def main():
 def measure_extras(flush):
     """The other workloads: cylinder 64x128x128 (3 species), sphere 256x512 (split and FP64), 256
     uneven disks (one persistent launch per step), the bulk-surface ball 30x50x30 (split and FP64), the
-    bulk-surface DIB cylinder (FP64 140x140x25, split 128x140x25), the paper's Section 5.2 and 5.3
-    disk runs, and the sphere 256x512 adjoint cost relative to its forward."""
+    bulk-surface DIB cylinder (FP64 140x140x25, split 128x140x25), and the sphere 256x512 adjoint cost
+    relative to its forward (split TF32 and FP64)."""
     import numpy as np
     import torch
     from paper_2604_11558_gb300 import binding
@@ -474,26 +549,29 @@ def measure_extras(flush):
                      "t250_run_s": ms * w["steps"] / 1e3}
         plan.close()
     out["bulk_surface_dib_cylinder"] = {"unit": UNIT, "l2": "not flushed (state 8 MB)", **res}
-    # sphere adjoint vs forward (FP64), full 256x512 workload: 1000 steps, checkpoints every 50
+    # sphere adjoint vs forward, full 256x512 workload: 1000 steps, checkpoints every 50, on the
+    # split-TF32 path (the product's forward) and on the FP64 path
     w = wl.schnakenberg_sphere()
-    plan = binding.Plan.from_workload(w, precision="fp64")
-    x = torch.from_numpy(w["W0"]).cuda()
     every, steps = 50, w["steps"]
-    ck = torch.empty((steps // every,) + tuple(x.shape), dtype=torch.float64, device="cuda")
-    g = torch.ones_like(x)
-    plan.adjoint(ck[:1].copy_(x.unsqueeze(0)), 1, 1, g, torch.empty_like(g))   # builds the adjoint tables
-    torch.cuda.synchronize()
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    e0.record()
-    plan.step_checkpointed(x, steps, every, ck)
-    e1.record()
-    plan.adjoint(ck, steps // every, every, g, torch.empty_like(g))
-    e2.record()
-    torch.cuda.synchronize()
-    fwd, adj = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    out["sphere_256x512_adjoint_fp64"] = {"forward_ms": fwd, "adjoint_ms": adj, "adjoint_over_forward": adj / fwd,
-                                          "steps": steps, "checkpoint_every": every}
-    plan.close()
+    for prec in ("split_tf32", "fp64"):
+        plan = binding.Plan.from_workload(w, precision=prec)
+        x = torch.from_numpy(w["W0"]).cuda()
+        ck = torch.empty((steps // every,) + tuple(x.shape), dtype=torch.float64, device="cuda")
+        g = torch.ones_like(x)
+        plan.adjoint(ck[:1].copy_(x.unsqueeze(0)), 1, 1, g, torch.empty_like(g))   # builds the adjoint tables
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        plan.step_checkpointed(x, steps, every, ck)
+        e1.record()
+        plan.adjoint(ck, steps // every, every, g, torch.empty_like(g))
+        e2.record()
+        torch.cuda.synchronize()
+        fwd, adj = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        out[f"sphere_256x512_adjoint_{prec}"] = {"forward_ms": fwd, "adjoint_ms": adj,
+                                                 "adjoint_over_forward": adj / fwd, "steps": steps,
+                                                 "checkpoint_every": every}
+        plan.close()
     return out
 
 

@@ -9,7 +9,7 @@ the oracle for minutes) and the storage floor of an FP32-intermediate chain: the
 per-species relative 2-norm error, over the whole final state, of the oracle run with
 F, every direction's result and the increment rounded to FP32 (its precision-emulation
 switch), which is what any implementation that keeps those intermediates in FP32 cannot
-be expected to beat:
+be expected to beat; for the ball also an FP64 evaluation-order floor (rowsum_exact_floor):
 
 * ball 100^3 Gray-Scott, 500 steps (tau 0.5, t_* = 250);
 * cylinder 64 x 128 x 128, 3 species, 1000 steps (tau 0.05, t_* = 50);
@@ -48,16 +48,39 @@ def storage_floor(w, ref):
     return np.array([np.linalg.norm(emu[s] - ref[s]) / np.linalg.norm(ref[s]) for s in range(ref.shape[0])])
 
 
-def single(name, w):
+def rowsum_exact_floor(w, ref):
+    """Per-species relative 2-norm difference, at the final time, between the oracle and the same
+    oracle with d M w evaluated per direction with every row of each Kronecker term summing to exactly
+    0 (the two are equal in exact arithmetic; every row of the benchmark grids is a Neumann or
+    periodic row): how far two FP64 evaluations of the same operator drift apart over the run."""
+    import scipy.sparse as sp
+    from oracle.operators import Grid
+    from oracle.stepper import Problem, run
+    from tests.gpu_helpers import oracle_reaction
+    g = Grid(w["geometry"], w["n"], z_bc=w.get("z_bc", "neumann"), lam=w.get("lam"))
+    Ms = {}
+    for mu, M in g.M.items():
+        M = sp.csr_matrix(M)
+        Ms[mu] = M - sp.diags(np.asarray(M.sum(axis=1)).ravel())
+    g.apply_M = lambda x: sum((Ms[mu] @ x.ravel()).reshape(x.shape) for mu in sorted(Ms))
+    alt = run(Problem(g, w["d"], oracle_reaction(w, g), w["tau"]), w["W0"], w["steps"])
+    return np.array([np.linalg.norm(alt[s] - ref[s]) / np.linalg.norm(ref[s]) for s in range(ref.shape[0])])
+
+
+def single(name, w, fp64_floor=False):
     t0 = time.time()
     ref = oracle_run(w)
     S = ref.shape[0]
     flat = ref.reshape(S, -1)
     idx = sample_indices(flat.shape[1], SAMPLES, SAMPLE_SEED)
     floor = storage_floor(w, ref)
+    extra = {}
+    if fp64_floor:
+        extra["floor64"] = rowsum_exact_floor(w, ref)
+        print(name, "FP64 evaluation-order floor per species", extra["floor64"], flush=True)
     np.savez_compressed(os.path.join(HERE, f"final_time_{name}.npz"), idx=idx, values=flat[:, idx],
                         norms=np.linalg.norm(flat, axis=1), maxabs=np.max(np.abs(flat), axis=1),
-                        floor=floor, steps=w["steps"], n=np.array(w["n"]), seed=w["seed"])
+                        floor=floor, steps=w["steps"], n=np.array(w["n"]), seed=w["seed"], **extra)
     print(name, "FP32-storage floor per species", floor, flush=True)
     print(name, "done in", round(time.time() - t0), "s", flush=True)
 
@@ -83,7 +106,7 @@ def batch():
 def main(which):
     for name in which:
         if name == "ball":
-            single("ball", wl.gray_scott_ball())
+            single("ball", wl.gray_scott_ball(), fp64_floor=True)
         elif name == "cylinder":
             single("cylinder", wl.linear_cubic_cylinder())
         elif name == "sphere":

@@ -13,9 +13,9 @@ same seeded inputs and compares element by element.  Tolerances:
   result and the increment rounded to FP32) -- the storage-precision floor
   of any FP32-intermediate chain, times the 3xTF32 product factor.
 * split-TF32 over hundreds of steps: whole-state relative error within 1e-6;
-  a species that decays towards zero (here to ~1e-13) carries a systematic
-  operator error (TF32 hi+lo matrices, FP32 coefficients ~1e-7) times the
-  decay exponent, so its own relative error is only held to 1e-4.
+  a species that decays towards zero (here to ~1e-12) accumulates the bias of
+  the tensor cores' truncating FP32 accumulation, so it is held to 4x an
+  emulation of that arithmetic.
 Sizes span several 128-row tiles and 16-wide K-chunks with ragged tails, the
 two-tile theta case (n_theta > 128), the largest supported sizes and n = 3.
 """
@@ -153,15 +153,30 @@ def test_cylinder_full_size_split():
 
 
 def test_ball_500_steps_split_vs_oracle_reduced_grid():
-    """Final-time parity over the full step count on a reduced ball (oracle in seconds)."""
+    """Final-time parity over the full step count on a reduced ball (oracle in seconds).  The whole
+    state and u are held to the 1e-6 target.  The decaying species v (to ~1e-12 at t_* = 250) is held
+    to 4x an emulation of the chain's arithmetic (tests/precision_emulation.py: F and intermediates
+    FP32, three TF32 products per product, the accumulator rounded toward zero after every 8-wide
+    K step as in the tensor cores; the rho direction as one plain phi_1 product as on the GPU):
+    truncation biases every product's magnitude low, and v's relative error accumulates that bias
+    over the steps (the full-size ball at t_* is tested in tests/test_gpu_final_time.py)."""
+    from oracle.operators import Grid
+    from oracle.stepper import Problem
+    from tests.gpu_helpers import oracle_reaction
+    from tests.precision_emulation import run as emulate
     w = wl.gray_scott_ball(n=(24, 20, 16), steps=500)
     ref = oracle_run(w)
     got = gpu_run(w, "split_tf32")
     whole = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     e = rel_errors(got, ref)
-    print("split vs oracle, ball 24x20x16, 500 steps: whole", whole, "per species", e)
+    g = Grid(w["geometry"], w["n"])
+    emu = emulate(Problem(g, w["d"], oracle_reaction(w, g), w["tau"]), w["W0"], w["steps"], accumulate="rz8",
+                  plain=(1,))
+    fe = rel_errors(emu, ref)
+    print("split vs oracle, ball 24x20x16, 500 steps: whole", whole, "per species", e, "emulated", fe)
     assert whole <= 1e-6
-    assert max(e) <= 1e-4
+    assert e[0] <= 1e-6
+    assert e[1] <= max(1e-6, 4 * fe[1])
 
 
 def test_graph_replay_equals_single_steps():

@@ -39,3 +39,22 @@ def test_bf16_three_pieces_meet_it(ball):
     e6 = rel(emulated_run(p, w["W0"], w["steps"], "bf16x6"), ref)
     e3 = rel(emulated_run(p, w["W0"], w["steps"], "tf32x3"), ref)
     assert e6 < 1e-6 and e6 < 2 * e3
+
+
+def test_truncating_accumulation_model():
+    """The 'rz8' accumulation model: with inputs whose pieces and partial sums are exact in FP32 it
+    equals the exact product; with positive operands it never exceeds the exact product (rounding
+    toward zero) and stays within one FP32 ulp of it per accumulation step."""
+    import numpy as np
+    from tests.precision_emulation import matmul
+    rng = np.random.default_rng(3)
+    A = rng.integers(-64, 64, (5, 24)).astype(np.float64)
+    B = rng.integers(-64, 64, (24, 7)).astype(np.float64)
+    assert np.array_equal(matmul(A, B, accumulate="rz8"), A @ B)
+    A = rng.uniform(0.5, 1.0, (6, 40))
+    B = rng.uniform(0.5, 1.0, (40, 9))
+    exact = A.astype(np.float32).astype(np.float64) @ B.astype(np.float32).astype(np.float64)
+    got = matmul(A, B, accumulate="rz8")
+    assert np.all(got <= exact * (1 + 1e-7))
+    steps = 3 * (40 // 8)
+    assert np.all(exact - got <= steps * np.spacing(exact.astype(np.float32)).astype(np.float64) + 1e-6 * exact)

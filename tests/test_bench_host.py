@@ -41,7 +41,10 @@ def test_kernel_work_table():
     import bench
     wk = bench.kernel_work((100, 100, 100), 2)
     dof = 2 * 10**6
-    assert wk["k_tc_slab"]["bytes"] == 20 * dof
+    # algorithmic bytes: the state read by the stencil, read and written by the slab's update
+    assert wk["stencil"]["bytes"] == 8 * dof and wk["k_tc_mode3"]["bytes"] == 0
+    assert wk["k_tc_slab"]["bytes"] == 16 * dof
+    assert wk["k_tc_slab"]["bytes_with_intermediates"] == 20 * dof
     assert wk["k_tc_mode3"]["flops"] == 3 * 2 * 2 * 100 * dof
     # split-TF32 flops per DOF of the whole chain: 3 passes x 2 x (2 n_phi + 2 n_theta + n_rho)
     total = sum(v["flops"] for v in wk.values()) / dof

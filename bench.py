@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cylinder, batched-disk and sphere-adjoint measurements")
     ap.add_argument("--profile-case", nargs="?", const="ball", default=None,
-                    choices=["ball", "sphere", "batch", "cylinder", "ball-fp64", "bulk-surface"],
+                    choices=["ball", "sphere", "batch", "cylinder", "ball-fp64", "bulk-surface", "dib", "dib-fp64",
+                             "sphere-adjoint"],
                     help="run only setup + 3 + 3 split steps of the ball workload (or the 256 x 512 sphere, the "
                          "256 batched disks, the 64 x 128 x 128 cylinder, the ball on the FP64 path, or the split bulk-surface "
                          "ball 30 x 50 x 30), the last "
@@ -293,7 +294,8 @@ def main():
     from paper_2604_11558_gb300 import binding
     from paper_2604_11558_gb300 import workloads as wl
 
-    if args.profile_case in ("sphere", "batch", "cylinder", "ball-fp64", "bulk-surface"):
+    if args.profile_case in ("sphere", "batch", "cylinder", "ball-fp64", "bulk-surface", "dib", "dib-fp64",
+                             "sphere-adjoint"):
         return profile_other(args.profile_case)
     w = wl.gray_scott_ball()
     n, S = w["n"], len(w["d"])
@@ -577,8 +579,9 @@ def measure_extras(flush):
 
 def profile_other(case):
     """Setup, 3 untimed steps, then 3 steps in the NVTX range sexpe_step, of the 256 x 512 sphere, the
-    256 batched disks, the 64 x 128 x 128 cylinder (split path), the ball on the FP64 path or the
-    bulk-surface ball 30 x 50 x 30 (split path), for an ncu capture of their kernels."""
+    256 batched disks, the 64 x 128 x 128 cylinder (split path), the ball on the FP64 path, the
+    bulk-surface ball 30 x 50 x 30 (split path) or the bulk-surface DIB cylinder (split 128 x 140 x 25,
+    FP64 140 x 140 x 25); or one split adjoint call of the 256 x 512 sphere; for an ncu capture."""
     import torch
     from paper_2604_11558_gb300 import binding
     from paper_2604_11558_gb300 import workloads as wl
@@ -596,6 +599,34 @@ def profile_other(case):
                                    w["coupling"], w["tau"], rho_star=w["rho_star"], precision="split_tf32")
         import numpy as np
         x = torch.from_numpy(np.concatenate([w["Wb"].ravel(), w["Ws"].ravel()])).cuda()
+    elif case in ("dib", "dib-fp64"):
+        # bulk-surface DIB (Section 5.6): split chains at 128 x 140 x 25 (n_rho <= 128), FP64 at the
+        # paper's 140 x 140 x 25
+        import numpy as np
+        prec, n = ("split_tf32", (128, 140, 25)) if case == "dib" else ("fp64", (140, 140, 25))
+        w = wl.dib_cylinder(n=n, steps=1)
+        plan = binding.CoupledPlan(n, w["d_bulk"], w["bulk_params"], w["d_surface"], w["surface_params"],
+                                   w["coupling"], w["tau"], rho_star=w["rho_star"], precision=prec,
+                                   reaction=w["bulk_reaction"], surface_reaction=w["surface_reaction"],
+                                   geometry="cylinder", z_star=w["z_star"])
+        x = torch.from_numpy(np.concatenate([w["Wb"].ravel(), w["Ws"].ravel()])).cuda()
+    elif case == "sphere-adjoint":
+        # split adjoint of the 256 x 512 sphere: checkpoints every 50 of 100 steps, then one adjoint
+        # call over the last 4 steps inside the NVTX range (its replay and adjoint launches)
+        w = wl.schnakenberg_sphere(steps=1)
+        plan = binding.Plan.from_workload(w, precision="split_tf32")
+        x = torch.from_numpy(w["W0"]).cuda()
+        ck = torch.empty((2,) + tuple(x.shape), dtype=torch.float64, device="cuda")
+        plan.step_checkpointed(x, 100, 50, ck)
+        g = torch.ones_like(x)
+        plan.adjoint(ck, 2, 50, g, torch.empty_like(g))
+        plan.synchronize()
+        torch.cuda.nvtx.range_push("sexpe_step")
+        plan.adjoint(ck[:1], 1, 4, g, torch.empty_like(g))
+        plan.synchronize()
+        torch.cuda.nvtx.range_pop()
+        plan.close()
+        return
     elif case == "sphere":
         w = wl.schnakenberg_sphere(steps=1)
         plan = binding.Plan.from_workload(w, precision="split_tf32")

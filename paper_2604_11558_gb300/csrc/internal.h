@@ -139,6 +139,7 @@ struct SplitTables {
     int rhs_tj;                    // j-lines per stencil tile (chosen by measurement at setup; 0 = model)
     int rhs_ks;                    // 0: tiled stencil kernel; > 0: rolling-window kernel, planes per CTA
     int rhs_mb;                    // rolling-window kernel: registers capped for this many CTAs per SM
+    int theta_comp;                // slab pass: compensated theta-mean coefficient (disks, coupled plans)
 };
 
 // Arguments of the split sphere adjoint's theta kernel (see k_tc_sphere_theta_adj).

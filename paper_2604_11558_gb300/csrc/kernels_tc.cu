@@ -1109,6 +1109,8 @@ __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int
     compute_sync();
 }
 
+// COMP: also form the theta-mean coefficient X[i][0] by compensated summation (see below).
+template <bool COMP>
 __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* gs, const uint32_t* cols, Pipe& P,
                                              uint32_t tmem, char* epi) {
     const int tid = threadIdx.x;
@@ -1124,12 +1126,46 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
     auto load_rows = [&](const float* base) {
         return [=](int c, Pre8& p) { load8_strided(p, base + r, n1q, c * 16 + h * 8, n2, r < n1); };
     };
-    run_gemm(P, gs[0], load_rows(J.Y),
-             [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
+    // The theta-mean coefficient X[i][0] = (1/sqrt(n2)) sum_j Y[i][j] (Q's first column is the
+    // constant vector) is also summed by the producers with compensation (Neumaier's variant of
+    // Kahan summation): near the axis Y is dominated by the theta-Laplacian, values ~1e4 whose
+    // theta-mean is ~0, and the tensor cores' truncating FP32 accumulation of that cancelling sum
+    // leaves a coherent bias in the one coefficient that no Phi damps (Phi_0 = 1).
+    // The compensation costs ~4% of the slab on the 100^3 ball and is compiled in where the setup
+    // enables it (SplitTables::theta_comp: disks and the grids of coupled plans).
+    float rs_s = 0.f, rs_c = 0.f;
+    run_gemm(P, gs[0], load_rows(J.Y), [&](int, char* hi, char* lo, const Pre8& p) {
+        store_row8(hi, lo, r, h, p.v);
+        if constexpr (COMP) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float t = rs_s + p.v[q];
+                rs_c += fabsf(rs_s) >= fabsf(p.v[q]) ? (rs_s - t) + p.v[q] : (p.v[q] - t) + rs_s;
+                rs_s = t;
+            }
+        }
+    });
+    // the two halves of a row meet in the data slot of G1's last chunk (free once G1 completed;
+    // the next chunk to reuse it comes nd - 1 chunks into G2, after the second barrier)
+    float x0 = 0.f;
+    if constexpr (COMP) {
+        const uint32_t last = P.sd == 0 ? P.nd - 1 : P.sd - 1;
+        float2* xch = reinterpret_cast<float2*>(P.data_slots + (size_t)last * P.data_bytes);
+        if (h == 1) xch[r] = make_float2(rs_s, rs_c);
+        compute_sync();
+        if (h == 0) {
+            const float2 o = xch[r];
+            const float t = rs_s + o.x;
+            const float c = (fabsf(rs_s) >= fabsf(o.x) ? (rs_s - t) + o.x : (o.x - t) + rs_s) + (rs_c + o.y);
+            x0 = (float)((double)(t + c) / sqrt((double)n2));
+        }
+        compute_sync();
+    }
     // G2: Z^T[j][i] = sum_j' Q[j][j'] (Phi o X)[i][j']   (x_2 Q_theta), data in B, rows j
     run_gemm(P, gs[1], load_rows(J.had), [&](int c, char* hi, char* lo, const Pre8& p) {
         float v[8];
         tmem_ld8(tmem + lane_base + c1 + (uint32_t)(c * 16 + h * 8), v);
+        if (COMP && c == 0 && h == 0) v[0] = x0;        // the compensated theta-mean coefficient
         if (r < n1p) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
@@ -1156,6 +1192,7 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
                     J.Win + (long long)mt * kRows * n1, J.W + (long long)mt * kRows * n1, J.tau_f, epi);
 }
 
+template <bool COMP>
 __global__ void __launch_bounds__(kBlock, 2)
     k_tc_slab(SplitTables T, TcShape sh) {
     extern __shared__ char smem_raw[];
@@ -1189,7 +1226,7 @@ __global__ void __launch_bounds__(kBlock, 2)
     } else {
         pdl_wait();                         // Y from the earlier directions
         pdl_trigger();
-        slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
+        slab_compute<COMP>(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
     }
     cta_end(R, tmem_cols);
 }
@@ -1539,7 +1576,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_batch(BatchTables B, TcShape s
         slab_specs(J, R.tmem, tmem_cols, gs, cols);
         if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
         else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
-        else slab_compute(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
+        else slab_compute<true>(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
     }
     cta_end(R, tmem_cols);
 }
@@ -1694,7 +1731,11 @@ cudaError_t tc_prepare(uint32_t smem_mode3, uint32_t smem_slab) {
                                  smem_mode3);
         if (e != cudaSuccess) return e;
     }
-    if (smem_slab) e = cudaFuncSetAttribute(k_tc_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_slab);
+    if (smem_slab) {
+        e = cudaFuncSetAttribute(k_tc_slab<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_slab);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_slab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_slab);
+    }
     if (e != cudaSuccess) return e;
     const int big = 212 * 1024;   // stencil tiles (all species) are sized to at most 212 KB
     e = cudaFuncSetAttribute(k_rhs_tile<GEO_DISK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1744,7 +1785,8 @@ cudaError_t launch_tc_mode3(const SplitTables& T, const TcShape& sh, cudaStream_
 
 cudaError_t launch_tc_slab(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     dim3 grid(T.geometry == GEO_DISK ? 1 : T.n3, T.S);
-    return launch_pdl(k_tc_slab, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
+    if (T.theta_comp) return launch_pdl(k_tc_slab<true>, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
+    return launch_pdl(k_tc_slab<false>, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
 }
 
 // j-tile of the stencil pass: among the sizes whose all-species tile fits in

@@ -605,6 +605,9 @@ sexpe_status build_split(sexpe_plan* p, cudaStream_t st) {
     if (p->shs.tmem_cols > 512 || (p->ndim == 3 && p->sh3.tmem_cols > 512)) return SEXPE_EUNSUPPORTED;
     SX_CUDA(tc_prepare(p->ndim == 3 ? p->sh3.smem_bytes : 0, p->shs.smem_bytes));
     p->kernels_per_step = p->ndim == 3 ? 3 : 2;
+    // the theta-mean coefficient by compensated summation on disks (whose F near the axis is the
+    // cancelling theta-Laplacian of the whole field); coupled plans turn it on for both grids
+    T.theta_comp = p->geometry == SEXPE_DISK ? 1 : 0;
     return tune_stencil(p, st);
 }
 
@@ -1800,6 +1803,7 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk
         s = build_plan(p->sub[0], bg, bulk, tau, precision, st);
         if (s == SEXPE_OK) s = build_plan(p->sub[1], &sg, surface, tau, precision, st);
         if (s == SEXPE_OK) {
+            for (int q = 0; q < 2; ++q) p->sub[q]->tabs.theta_comp = 1;
             p->device = p->sub[0]->device;
             p->coupled = true;
             p->geometry = bg->geometry;

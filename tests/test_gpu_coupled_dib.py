@@ -152,7 +152,7 @@ def _dib_120x140x25():
 
 
 @pytest.mark.xfail(strict=True, reason="known accuracy defect of the split DIB chain near the axis: r, w_u, w_v "
-                   "reach ~1e-4 on 120 x 140 x 25 (mechanism in the characterisation test below)")
+                   "reach ~1e-5 on 120 x 140 x 25 (mechanism in the characterisation test below)")
 def test_dib_split_tf32_meets_target_on_120x140x25():
     """The 1e-6 target on the 120 x 140 x 25 grid: not met by this build (strict expected failure, so
     that a fix shows as an unexpected pass)."""
@@ -163,20 +163,19 @@ def test_dib_split_tf32_meets_target_on_120x140x25():
 def test_dib_split_tf32_characterised_on_120x140x25():
     """Characterisation of the defect, not the 1e-6 target: on the 120 x 140 x 25 grid (rho_* = 15,
     tau = 0.025, 20 steps) the surface species s, which the chain computes directly, stays within
-    1e-6 (measured 3.8e-7), but r, w_u, w_v reach ~1e-4 of their own size (measured 0.8-1.0e-4
-    against the oracle and against the FP64 GPU path alike).  Mechanism: near the axis the F of
-    rough surface data is dominated by the theta-Laplacian (~1e4, zero theta-mean), so the
-    FP32-accumulated theta transform leaves a coherent error in the undamped theta-mean of s
-    (measured ring-mean bias ~1.5e-7, uniform over the inner rings); r and w are driven by
-    zeta4 (s - zeta5) with s ~ zeta5 and are ~1e-2 of s, which amplifies it ~100x.  An emulation of
-    the chain's arithmetic with round-to-nearest accumulation tracks the GPU within 3-5x after 3
-    steps but decays by step 20; with the accumulator rounded toward zero per 8-wide K step
-    (truncating tensor-core accumulation) the error grows with the steps as on the GPU, to within
-    ~6x.  These bounds hold the measured values with a margin of ~3 so that a regression shows; the
-    FP64 path is the one to use for this model."""
+    1e-6 (measured 8.8e-8), but r, w_u, w_v reach ~1e-5 of their own size (measured 0.90-0.99e-5).
+    Mechanism: near the axis the F of rough surface data is dominated by the theta-Laplacian (~1e4,
+    zero theta-mean); r and w are driven by zeta4 (s - zeta5) with s ~ zeta5 and are ~1e-2 of s, so a
+    coherent error in the undamped theta-mean of s reappears ~100x larger in them.  The tensor cores'
+    truncating FP32 accumulation biases that cancelling sum; the slab pass of these plans forms the
+    theta-mean coefficient by compensated summation on the producers instead (this took the errors
+    from 0.8-1.0e-4 to ~1e-5); the rest is attributed to the same truncation in the later products
+    (an emulation with the accumulator rounded toward zero per 8-wide K step grows with the steps as
+    the GPU error does; with round-to-nearest it decays).  These bounds hold the measured values with
+    a margin of ~3 so that a regression shows; the FP64 path is the one to use for this model."""
     (wu, wui), (wv, wvi), (r, ri), (s, si) = _dib_120x140x25()
-    assert s <= 1e-6 and si <= 1e-5
-    assert max(wu, wv, r) <= 3e-4 and max(wui, wvi, ri) <= 1e-4
+    assert s <= 1e-6 and si <= 5e-6
+    assert max(wu, wv, r) <= 3e-5 and max(wui, wvi, ri) <= 1.2e-5
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split_tf32"])

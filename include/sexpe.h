@@ -279,7 +279,9 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bulk_grid, const sexpe_specie
  * add_s1), with the virtual-point factor and the bulk diffusion taken from bulk_grid and bulk as
  * in sexpe_coupled_setup.  All arrays host, n doubles, caller-owned.  Arguments are checked as by
  * sexpe_coupled_setup (the surface species aside); n < 0 or a NULL array with n > 0 gives
- * SEXPE_EINVAL. */
+ * SEXPE_EINVAL.  The host compiles the same source as the coupling kernels, but the device
+ * compiler may contract its multiply-adds into FMAs, so host and device results agree to FP64
+ * rounding, not bit for bit. */
 sexpe_status sexpe_coupling_terms(const sexpe_grid* bulk_grid, const sexpe_species* bulk, const sexpe_coupling* cp,
                                   int64_t n, const double* ub, const double* vb, const double* r, const double* s,
                                   double* add_b0, double* add_b1, double* add_s0, double* add_s1);

@@ -213,12 +213,18 @@ __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Producer&& 
 // slot 0 are formed once per product and moved by constant offsets (in the
 // descriptor's 16-byte address units, which cannot carry out of the 14-bit
 // field below 256 KB), and the usual one-tile product is fully unrolled.
-__device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
+//
+// The NG products are walked in an unrolled loop (NG is a compile-time constant at
+// every call site), so the specs stay in registers instead of a local-memory array
+// indexed at run time.
+template <int NG>
+__device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs) {
     if ((threadIdx.x & 31) != 0) return;
     const uint32_t mat16 = P.mat_bytes >> 4, data16 = P.data_bytes >> 4;
     constexpr uint64_t kKStep = (2 * kLBO) >> 4;       // next 8 K-columns: two core matrices
     const uint32_t mslot0 = smem_u32(P.mat_slots), dslot0 = smem_u32(P.data_slots);
-    for (int q = 0; q < n_gemms; ++q) {
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
         const GemmSpec& G = gs[q];
         const int nsub = G.n_pad < 256 ? G.n_pad : 256;
         const int n_halves = G.n_pad / nsub;
@@ -279,9 +285,11 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs, int n_ge
 // the CTA in order and copies each chunk's matrix image (hi tile then lo tile,
 // one bulk copy) into its slot as soon as the slot is free, up to nm chunks ahead
 // of the MMAs.
-__device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs, int n_gemms) {
+template <int NG>
+__device__ __forceinline__ void tma_issuer(Pipe& P, const GemmSpec* gs) {
     if ((threadIdx.x & 31) != 0) return;
-    for (int q = 0; q < n_gemms; ++q) {
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
         const GemmSpec& G = gs[q];
         const uint32_t tile = (uint32_t)G.mat.rows_pad * kTileRowBytes;
         for (int c = 0; c < G.k_chunks; ++c, P.advance()) {
@@ -986,10 +994,10 @@ __global__ void __launch_bounds__(kBlock, 1)
                       {T.M3b[0], 0, kRows, 1, n3p, n3p / kKC, R.tmem + (uint32_t)n3p}};
     if (threadIdx.x >= kThreads + 32) {
         pdl_trigger();
-        mma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);
+        mma_issuer<GEO == GEO_BALL ? 2 : 1>(R.P, gs);
     } else if (threadIdx.x >= kThreads) {
         pdl_trigger();
-        tma_issuer(R.P, gs, GEO == GEO_BALL ? 2 : 1);     // constant matrices only
+        tma_issuer<GEO == GEO_BALL ? 2 : 1>(R.P, gs);     // constant matrices only
     } else {
         pdl_wait();      // F from the stencil pass
         pdl_trigger();
@@ -1219,10 +1227,10 @@ __global__ void __launch_bounds__(kBlock, 2)
     slab_specs(J, R.tmem, tmem_cols, gs, cols);
     if (threadIdx.x >= kThreads + 32) {
         pdl_trigger();
-        mma_issuer(R.P, gs, 3);
+        mma_issuer<3>(R.P, gs);
     } else if (threadIdx.x >= kThreads) {
         pdl_trigger();
-        tma_issuer(R.P, gs, 3);             // constant matrices only
+        tma_issuer<3>(R.P, gs);             // constant matrices only
     } else {
         pdl_wait();                         // Y from the earlier directions
         pdl_trigger();
@@ -1250,10 +1258,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcSh
     GemmSpec gs[1] = {{mat, 0, kRows, 1, NT, mat.k_chunks, R.tmem}};
     if (threadIdx.x >= kThreads + 32) {
         pdl_trigger();
-        mma_issuer(R.P, gs, 1);
+        mma_issuer<1>(R.P, gs);
     } else if (threadIdx.x >= kThreads) {
         pdl_trigger();
-        tma_issuer(R.P, gs, 1);
+        tma_issuer<1>(R.P, gs);
     } else {
         pdl_wait();
         pdl_trigger();
@@ -1302,10 +1310,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, Tc
                       {qz, 0, kRows, 1, NT, n1p / kKC, R.tmem + (uint32_t)n1p}};
     if (threadIdx.x >= kThreads + 32) {
         pdl_trigger();
-        mma_issuer(R.P, gs, 2);
+        mma_issuer<2>(R.P, gs);
     } else if (threadIdx.x >= kThreads) {
         pdl_trigger();
-        tma_issuer(R.P, gs, 2);
+        tma_issuer<2>(R.P, gs);
     } else {
         pdl_wait();
         pdl_trigger();
@@ -1373,10 +1381,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta_adj(SplitTables T
                       {qz, 0, kRows, 1, NT, n1p / kKC, R.tmem + (uint32_t)(n1p + NT)}};
     if (threadIdx.x >= kThreads + 32) {
         pdl_trigger();
-        mma_issuer(R.P, gs, 3);
+        mma_issuer<3>(R.P, gs);
     } else if (threadIdx.x >= kThreads) {
         pdl_trigger();
-        tma_issuer(R.P, gs, 3);
+        tma_issuer<3>(R.P, gs);
     } else {
         pdl_wait();
         pdl_trigger();
@@ -1574,8 +1582,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_batch(BatchTables B, TcShape s
         GemmSpec gs[3];
         uint32_t cols[3];
         slab_specs(J, R.tmem, tmem_cols, gs, cols);
-        if (threadIdx.x >= kThreads + 32) mma_issuer(R.P, gs, 3);
-        else if (threadIdx.x >= kThreads) tma_issuer(R.P, gs, 3);
+        if (threadIdx.x >= kThreads + 32) mma_issuer<3>(R.P, gs);
+        else if (threadIdx.x >= kThreads) tma_issuer<3>(R.P, gs);
         else slab_compute<true>(J, gs, cols, R.P, R.tmem, R.P.mat_slots);
     }
     cta_end(R, tmem_cols);

@@ -849,7 +849,19 @@ void free_plan(sexpe_plan* p) {
         if (p->sadj_ev_swept[b]) cudaEventDestroy(p->sadj_ev_swept[b]);
     }
     for (void* a : p->allocs) cudaFree(a);
+    if (p->h_err) cudaFreeHost(p->h_err);
     delete p;
+}
+
+// The plan's device error word (zeroed on `st`) and its pinned host copy.
+static sexpe_status alloc_err_word(sexpe_plan* p, cudaStream_t st) {
+    SX_TRY(alloc_dev(p, 4, &p->d_err));
+    SX_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st));
+    if (cudaHostAlloc((void**)&p->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        p->h_err = nullptr;       // sexpe_synchronize then reads the word with a blocking copy
+    }
+    return SEXPE_OK;
 }
 
 sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species* sp, double tau, int32_t precision,
@@ -891,8 +903,7 @@ sexpe_status build_plan(sexpe_plan* p, const sexpe_grid* g, const sexpe_species*
         p->ax[2] = build_axis(g->z_bc == SEXPE_Z_PAPER ? AX_Z_PAPER : AX_Z_NEUMANN, p->n[2], g->z_star);
         break;
     }
-    SX_TRY(alloc_dev(p, 4, &p->d_err));
-    SX_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st));
+    SX_TRY(alloc_err_word(p, st));
     SX_TRY(alloc_dev(p, (size_t)p->S * p->npts, &p->d_host_state));
     if (precision == SEXPE_FP64) SX_TRY(build_fp64(p, st));
     else if (precision == SEXPE_UNSPLIT_FP64) SX_TRY(build_unsplit(p, st));
@@ -1060,8 +1071,7 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
     float* dF = nullptr;
     SX_TRY(alloc_dev(p, (size_t)f_total, &dF));
     SX_CUDA(cudaMemsetAsync(dF, 0, sizeof(float) * (size_t)f_total, st));   // padding columns stay zero
-    SX_TRY(alloc_dev(p, 4, &p->d_err));
-    SX_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st));
+    SX_TRY(alloc_err_word(p, st));
     int* counter = nullptr;
     SX_TRY(alloc_dev(p, 4, &counter));
     SX_TRY(alloc_dev(p, (size_t)p->inst_off.back(), &p->bstate));
@@ -1815,8 +1825,7 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk
             p->tau = tau;
             p->cpl = make_couple_args(bg, p->sub[0]->d.data(), cp);
             p->kernels_per_step = 1 + p->sub[0]->kernels_per_step + p->sub[1]->kernels_per_step;
-            s = alloc_dev(p, 4, &p->d_err);
-            if (s == SEXPE_OK && cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st) != cudaSuccess) s = SEXPE_ECUDA;
+            s = alloc_err_word(p, st);
             if (s == SEXPE_OK) s = alloc_dev(p, (size_t)state_elems(p), &p->d_host_state);
             if (s == SEXPE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SEXPE_ECUDA;
         }
@@ -2030,9 +2039,17 @@ sexpe_status sexpe_selftest_wait_timeout(void* stream) {
 
 sexpe_status sexpe_synchronize(sexpe_plan* p, void* stream) {
     if (!p) return SEXPE_EINVAL;
-    SX_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
     int err = 0;
-    SX_CUDA(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (p->h_err) {
+        // the error word is copied on the stream behind the plan's work: one synchronisation
+        SX_CUDA(cudaMemcpyAsync(p->h_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SX_CUDA(cudaStreamSynchronize(st));
+        err = *p->h_err;
+    } else {
+        SX_CUDA(cudaStreamSynchronize(st));
+        SX_CUDA(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    }
     if (err != 0) {
         SX_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
         return SEXPE_ETIMEOUT;

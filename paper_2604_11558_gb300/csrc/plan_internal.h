@@ -45,6 +45,7 @@ struct sexpe_plan {
     std::vector<void*> allocs;
     size_t bytes = 0;
     int* d_err = nullptr;
+    int* h_err = nullptr;             // pinned host copy of the error word (read by sexpe_synchronize)
     double* d_host_state = nullptr;   // staging buffer of sexpe_step_host
     // FP64 path
     sexpe::RhsTables<double> rhs64{};

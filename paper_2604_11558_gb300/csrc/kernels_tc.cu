@@ -158,11 +158,25 @@ __device__ __forceinline__ void load8_strided(Pre8& p, const float* base, int st
 // AND the chunk's matrix copy has landed, so the MMA thread waits on a single
 // barrier per chunk (every wait costs the issuing thread ~100+ cycles during
 // which the tensor pipe runs dry).
-template <class Loader, class Producer>
-__device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Loader&& load, Producer&& produce) {
+// `tail()` runs after the last chunk is handed over and before the wait for the
+// product's completion: loads that need nothing of this product (the next
+// product's first chunks, the update's first state values) overlap that wait.
+// With PRE the loads of chunks 0 and 1 were issued earlier, into pre[0..1].
+struct NoTail {
+    __device__ void operator()() const {}
+};
+
+template <bool PRE = false, class Loader, class Producer, class Tail = NoTail>
+__device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Loader&& load, Producer&& produce,
+                                         Tail&& tail = Tail{}, const Pre8* pre = nullptr) {
     Pre8 p0, p1;
-    load(0, p0);
-    if (G.k_chunks > 1) load(1, p1);
+    if constexpr (PRE) {
+        p0 = pre[0];
+        p1 = pre[1];
+    } else {
+        load(0, p0);
+        if (G.k_chunks > 1) load(1, p1);
+    }
     uint32_t last_sd = 0, last_pd = 0;
     const bool lane0 = (threadIdx.x & 31) == 0;
     for (int c = 0; c < G.k_chunks; ++c) {
@@ -191,6 +205,7 @@ __device__ __forceinline__ void run_gemm(Pipe& P, const GemmSpec& G, Loader&& lo
         p0 = p1;
         p1 = p2;
     }
+    tail();
     // the product is complete in tensor memory once the last chunk's MMAs are
     if (lane0) pipe_wait(P, &P.data_empty[last_sd], last_pd, DERR_TIMEOUT_MMA);
     __syncwarp();
@@ -1007,23 +1022,31 @@ __global__ void __launch_bounds__(kBlock, 1)
         const bool valid = r < tile_rows;
         const int i = (int)((row0 + r) % n1q);
         float* Yr = Ys + row0 + r;
+        const float* hp = T.had_phi + (long long)s * n3 * n1q + i;     // ball only
+        auto load_h = [&](int c, Pre8& p) { load8_strided(p, hp, n1q, c * 16 + h * 8, n3, valid); };
+        Pre8 hpre[2] = {};                   // the ball's G2: first two chunks of Hadamard factors
+        auto g1_tail = [&] {
+            if constexpr (GEO == GEO_BALL) {
+                load_h(0, hpre[0]);
+                if (gs[1].k_chunks > 1) load_h(1, hpre[1]);
+            }
+        };
         run_gemm(
             R.P, gs[0],
             [&](int c, Pre8& p) { load8_strided(p, Yr, (int)plane, c * 16 + h * 8, n3, valid); },
-            [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
+            [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); }, g1_tail);
         uint32_t last = 0;
         if constexpr (GEO == GEO_BALL) {
-            const float* hp = T.had_phi + (long long)s * n3 * n1q + i;
-            run_gemm(
-                R.P, gs[1],
-                [&](int c, Pre8& p) { load8_strided(p, hp, n1q, c * 16 + h * 8, n3, valid); },
+            run_gemm<true>(
+                R.P, gs[1], load_h,
                 [&](int c, char* hi, char* lo, const Pre8& p) {
                     float v[8];
                     tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
                     store_row8(hi, lo, r, h, v);
-                });
+                },
+                NoTail{}, hpre);
             last = (uint32_t)n3p;
         }
         for (int c = 0; c < n3p / 16; ++c) {
@@ -1080,8 +1103,25 @@ __device__ __forceinline__ void slab_specs(const SlabJob& J, uint32_t tmem, uint
 // read-modify-writes in flight per thread.  Called by the 256 producer threads.
 constexpr int kUpdBatch = 16;   // FP64 read-modify-writes in flight per thread in update_rows
 
+// The first batch of state values update_rows reads (same rows, n1, stride), loaded ahead of it.
+__device__ __forceinline__ void update_prefetch(double (&w)[kUpdBatch], int rows, int n1, const double* Win,
+                                                int stride = 0) {
+    if (stride == 0) stride = n1;
+    const int count = rows * n1;
+    const uint32_t m_n1 = div_magic((uint32_t)n1);
+#pragma unroll
+    for (int u = 0; u < kUpdBatch; ++u) {
+        const int f = (int)threadIdx.x + u * kThreads;
+        const int jl = div_by(f, m_n1);
+        w[u] = f < count ? Win[jl * stride + (f - jl * n1)] : 0.0;
+    }
+}
+
+// With PRE the first batch comes from `wpre` (update_prefetch with the same arguments).
+template <bool PRE = false>
 __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int n1p, const double* Win,
-                                            double* W, float tau_f, char* epi, int stride = 0) {
+                                            double* W, float tau_f, char* epi, int stride = 0,
+                                            const double* wpre = nullptr) {
     if (stride == 0) stride = n1;
     const int tid = threadIdx.x;
     const int r = tid & (kRows - 1), h = tid >> 7;
@@ -1099,11 +1139,16 @@ __device__ __forceinline__ void update_rows(uint32_t dcol, int rows, int n1, int
     const uint32_t m_n1 = div_magic((uint32_t)n1);
     for (int f0 = tid; f0 < count; f0 += kThreads * kUpdBatch) {
         double w[kUpdBatch];
+        if (PRE && f0 == tid) {
 #pragma unroll
-        for (int u = 0; u < kUpdBatch; ++u) {
-            const int f = f0 + u * kThreads;
-            const int jl = div_by(f, m_n1);
-            w[u] = f < count ? Win[jl * stride + (f - jl * n1)] : 0.0;     // offsets < 2^31
+            for (int u = 0; u < kUpdBatch; ++u) w[u] = wpre[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < kUpdBatch; ++u) {
+                const int f = f0 + u * kThreads;
+                const int jl = div_by(f, m_n1);
+                w[u] = f < count ? Win[jl * stride + (f - jl * n1)] : 0.0;     // offsets < 2^31
+            }
         }
 #pragma unroll
         for (int u = 0; u < kUpdBatch; ++u) {
@@ -1142,6 +1187,12 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
     // The compensation costs ~4% of the slab on the 100^3 ball and is compiled in where the setup
     // enables it (SplitTables::theta_comp: disks and the grids of coupled plans).
     float rs_s = 0.f, rs_c = 0.f;
+    const auto load_had = load_rows(J.had);
+    Pre8 hpre[2] = {};                       // G2's first two chunks of Hadamard factors
+    auto g1_tail = [&] {
+        load_had(0, hpre[0]);
+        if (gs[1].k_chunks > 1) load_had(1, hpre[1]);
+    };
     run_gemm(P, gs[0], load_rows(J.Y), [&](int, char* hi, char* lo, const Pre8& p) {
         store_row8(hi, lo, r, h, p.v);
         if constexpr (COMP) {
@@ -1152,7 +1203,7 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
                 rs_s = t;
             }
         }
-    });
+    }, g1_tail);
     // the two halves of a row meet in the data slot of G1's last chunk (free once G1 completed;
     // the next chunk to reuse it comes nd - 1 chunks into G2, after the second barrier)
     float x0 = 0.f;
@@ -1170,7 +1221,7 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
         compute_sync();
     }
     // G2: Z^T[j][i] = sum_j' Q[j][j'] (Phi o X)[i][j']   (x_2 Q_theta), data in B, rows j
-    run_gemm(P, gs[1], load_rows(J.had), [&](int c, char* hi, char* lo, const Pre8& p) {
+    run_gemm<true>(P, gs[1], load_had, [&](int c, char* hi, char* lo, const Pre8& p) {
         float v[8];
         tmem_ld8(tmem + lane_base + c1 + (uint32_t)(c * 16 + h * 8), v);
         if (COMP && c == 0 && h == 0) v[0] = x0;        // the compensated theta-mean coefficient
@@ -1179,9 +1230,11 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
             for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
             store_row8(hi, lo, r, h, v);
         }
-    });
+    }, NoTail{}, hpre);
     // G3: R^T[j][i'] = sum_i Z^T[j][i] P[i'][i]      (x_1 phi_1(tau d A_rho)), rows j
-    run_gemm(P, gs[2], [&](int c, char* hi, char* lo, const Pre8&) {
+    double wpre[kUpdBatch];                 // the update's first state values, read during G3's last wait
+    auto g3_tail = [&] { update_prefetch(wpre, min(kRows, n2), n1, J.Win); };
+    run_gemm(P, gs[2], [](int, Pre8&) {}, [&](int c, char* hi, char* lo, const Pre8&) {
         for (int mt = 0; mt < m2; ++mt) {
             float v[8];
             tmem_ld8(tmem + lane_base + c2 + (uint32_t)(mt * n1p + c * 16 + h * 8), v);
@@ -1193,9 +1246,10 @@ __device__ __forceinline__ void slab_compute(const SlabJob& J, const GemmSpec* g
             }
             store_row8(hi, lo, mt * kRows + r, h, v);
         }
-    });
+    }, g3_tail);
     // w[k][j][i'] += tau R^T[j][i']
-    for (int mt = 0; mt < m2; ++mt)
+    update_rows<true>(tmem + c3, min(kRows, n2), n1, n1p, J.Win, J.W, J.tau_f, epi, 0, wpre);
+    for (int mt = 1; mt < m2; ++mt)
         update_rows(tmem + c3 + (uint32_t)(mt * n1p), min(kRows, n2 - mt * kRows), n1, n1p,
                     J.Win + (long long)mt * kRows * n1, J.W + (long long)mt * kRows * n1, J.tau_f, epi);
 }

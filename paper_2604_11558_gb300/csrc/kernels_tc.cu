@@ -1395,20 +1395,28 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta(SplitTables T, Tc
             };
         };
         const long long roff = (long long)s * T.ys + (long long)(valid ? j : 0) * n1q;
+        const auto load_had = load_row8(T.had_sph + roff);
+        Pre8 hpre[2] = {};                   // G2's first two chunks of Hadamard factors, read during G1's last wait
+        auto g1_tail = [&] {
+            load_had(0, hpre[0]);
+            if (gs[1].k_chunks > 1) load_had(1, hpre[1]);
+        };
         run_gemm(R.P, gs[0], load_row8(T.Y2 + roff),
-                 [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
-        run_gemm(R.P, gs[1], load_row8(T.had_sph + roff), [&](int c, char* hi, char* lo, const Pre8& p) {
+                 [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); }, g1_tail);
+        const long long n12 = (long long)n1 * n2;
+        const int i0 = z * NT;
+        double* W = T.state_upd + (long long)s * n12 + (long long)j0 * n1 + i0;
+        const int rows = min(kRows, n2 - j0), cols = min(NT, n1 - i0);
+        double wpre[kUpdBatch];              // the update's first state values, read during G2's last wait
+        auto g2_tail = [&] { update_prefetch(wpre, rows, cols, W, n1); };
+        run_gemm<true>(R.P, gs[1], load_had, [&](int c, char* hi, char* lo, const Pre8& p) {
             float v[8];
             tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
             store_row8(hi, lo, r, h, v);
-        });
-        const long long n12 = (long long)n1 * n2;
-        const int i0 = z * NT;
-        double* W = T.state_upd + (long long)s * n12 + (long long)j0 * n1 + i0;
-        update_rows(R.tmem + (uint32_t)n1p, min(kRows, n2 - j0), min(NT, n1 - i0), NT, W, W, T.tau,
-                    R.P.mat_slots, n1);
+        }, g2_tail, hpre);
+        update_rows<true>(R.tmem + (uint32_t)n1p, rows, cols, NT, W, W, T.tau, R.P.mat_slots, n1, wpre);
     }
     cta_end(R, tmem_cols);
 }
@@ -1451,6 +1459,24 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta_adj(SplitTables T
         // lambda rounded to FP32 in the chain layout: eight consecutive theta values of row j in two
         // 16-byte loads (n1q and the 8-column groups keep them aligned)
         const float* lrow = A.lam32 + roff;
+        auto load_had = [&](const float* row) {
+            return [=](int c, Pre8& p) {
+                const int i = c * 16 + h * 8;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) p.v[q] = (valid && i + q < n1) ? __ldg(row + i + q) : 0.f;
+            };
+        };
+        const auto load_had1 = load_had(T.had_sph + roff), load_had2 = load_had(A.had_d + roff);
+        // each product's first two chunks of Hadamard factors, read during the previous product's last wait
+        Pre8 hpre1[2] = {}, hpre2[2] = {};
+        auto g1_tail = [&] {
+            load_had1(0, hpre1[0]);
+            if (gs[1].k_chunks > 1) load_had1(1, hpre1[1]);
+        };
+        auto g2_tail = [&] {
+            load_had2(0, hpre2[0]);
+            if (gs[2].k_chunks > 1) load_had2(1, hpre2[1]);
+        };
         run_gemm(
             R.P, gs[0],
             [&](int c, Pre8& p) {
@@ -1468,14 +1494,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta_adj(SplitTables T
                 for (int q = 0; q < 8; ++q)
                     if (i + q >= n1) p.v[q] = 0.f;
             },
-            [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
-        auto load_had = [&](const float* row) {
-            return [=](int c, Pre8& p) {
-                const int i = c * 16 + h * 8;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) p.v[q] = (valid && i + q < n1) ? __ldg(row + i + q) : 0.f;
-            };
-        };
+            [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); }, g1_tail);
         auto hadamard = [&](int c, char* hi, char* lo, const Pre8& p) {
             float v[8];
             tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
@@ -1483,8 +1502,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta_adj(SplitTables T
             for (int q = 0; q < 8; ++q) v[q] *= p.v[q];
             store_row8(hi, lo, r, h, v);
         };
-        run_gemm(R.P, gs[1], load_had(T.had_sph + roff), hadamard);
-        run_gemm(R.P, gs[2], load_had(A.had_d + roff), hadamard);
+        run_gemm<true>(R.P, gs[1], load_had1, hadamard, g2_tail, hpre1);
+        run_gemm<true>(R.P, gs[2], load_had2, hadamard, NoTail{}, hpre2);
         const int i0 = z * NT;
         double dot = 0.0;
         for (int c = 0; c < NT / 16; ++c) {

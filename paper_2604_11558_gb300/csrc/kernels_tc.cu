@@ -1552,13 +1552,24 @@ __device__ __forceinline__ void batch_stencil_tile(const BatchInstance& I, const
     const int per_sp = nJ * n1;
     const int items = 2 * per_sp;
     const uint32_t m_n1 = div_magic((uint32_t)n1);
-    for (int q = threadIdx.x; q < items; q += kBlock) {
-        const int sp = q >= per_sp;
-        const int qq = q - sp * per_sp;
-        const int jj = div_by(qq, m_n1), i = qq - jj * n1;
-        int j = j0 - 1 + jj;
-        j = j < 0 ? j + n2 : (j >= n2 ? j - n2 : j);      // theta is periodic
-        tile[q] = split_f64(__ldg(Win + sp * n12 + (long long)j * n1 + i));
+    // kTileBatch loads in flight per thread: the tile fill is otherwise one DRAM latency per value
+    for (int q0 = threadIdx.x; q0 < items; q0 += kBlock * kTileBatch) {
+        double v[kTileBatch];
+#pragma unroll
+        for (int u = 0; u < kTileBatch; ++u) {
+            const int q = q0 + u * kBlock;
+            const int sp = q >= per_sp;
+            const int qq = q - sp * per_sp;
+            const int jj = div_by(qq, m_n1), i = qq - jj * n1;
+            int j = j0 - 1 + jj;
+            j = j < 0 ? j + n2 : (j >= n2 ? j - n2 : j);  // theta is periodic
+            v[u] = q < items ? __ldg(Win + sp * n12 + (long long)j * n1 + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kTileBatch; ++u) {
+            const int q = q0 + u * kBlock;
+            if (q < items) tile[q] = split_f64(v[u]);
+        }
     }
     __syncthreads();
     const int total = lines * n1;
@@ -1613,17 +1624,26 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_batch(BatchTables B, TcShape s
     __shared__ int s_item;
     const uint32_t tmem_cols = sh.tmem_cols;
     CtaRes R = cta_begin(smem_raw, sh, B.err);
-    // phase 1: F of every instance
+    // phase 1: F of every instance.  The tile's instance record is copied to shared memory
+    // once: read through a global reference, its fields (sizes, table pointers, reaction
+    // parameters) are reloaded after every store of the tile loops, which may alias it.
     float2* tile = reinterpret_cast<float2*>(R.P.mat_slots);
+    __shared__ __align__(16) BatchInstance s_inst;
+    __shared__ int2 s_tile;
+    constexpr int kInstWords = (int)(sizeof(BatchInstance) / sizeof(int));
+    static_assert(sizeof(BatchInstance) % sizeof(int) == 0, "instance record copied as words");
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(B.counter + 2, 1);
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(B.counter + 2, 1);
+            s_tile = it < B.n_ftiles ? B.ftiles[it] : make_int2(-1, 0);
+        }
         __syncthreads();
-        const int it = s_item;
+        const int2 t = s_tile;
+        if (t.x < 0) break;
+        const int* src = reinterpret_cast<const int*>(B.inst + t.x);
+        for (int q = threadIdx.x; q < kInstWords; q += kBlock) reinterpret_cast<int*>(&s_inst)[q] = src[q];
         __syncthreads();
-        if (it >= B.n_ftiles) break;
-        const int2 t = B.ftiles[it];
-        const BatchInstance& I = B.inst[t.x];
-        batch_stencil_tile(I, B.W_in + I.w_off, B.F + I.f_off, t.y, B.tj, tile);
+        batch_stencil_tile(s_inst, B.W_in + s_inst.w_off, B.F + s_inst.f_off, t.y, B.tj, tile);
     }
     grid_barrier(B.counter + 1, gridDim.x, B.err);
     // phase 2: the chains

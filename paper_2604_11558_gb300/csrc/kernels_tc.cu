@@ -250,6 +250,7 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs) {
         const uint64_t ddh = smem_desc(dslot0, kLBO, kSBO), ddl = smem_desc(dslot0 + dtile, kLBO, kSBO);
         const uint32_t d = G.tmem_d;
         const bool one_tile = G.m_tiles == 1 && n_halves == 1;
+        const bool two_tiles = G.m_tiles == 2 && n_halves == 1;
         for (int c = 0; c < G.k_chunks; ++c, P.advance()) {
             const uint32_t sm = P.sm, sd = P.sd;
             pipe_wait(P, &P.data_full[sd], P.pd, DERR_TIMEOUT_MMA);     // data written, matrix landed
@@ -265,6 +266,22 @@ __device__ __forceinline__ void mma_issuer(Pipe& P, const GemmSpec* gs) {
                     mma_tf32(d, al + k, bh + k, idesc, (c | ks) != 0);
                     mma_tf32(d, ah + k, bl + k, idesc, 1u);
                     mma_tf32(d, ah + k, bh + k, idesc, 1u);
+                }
+            } else if (two_tiles) {
+                // two 128-row tiles of A, one N range: the general loop's order, unrolled (the
+                // issuing thread's per-MMA overhead otherwise doubles the chunk's issue time)
+                constexpr uint64_t kTile = (16 * kSBO) >> 4;  // next 128 rows of A
+                const uint32_t d1 = d + (uint32_t)G.n_pad;
+#pragma unroll
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    const uint64_t k = (uint64_t)ks * kKStep;
+                    const uint32_t acc = (c | ks) != 0;
+                    mma_tf32(d, al + k, bh + k, idesc, acc);
+                    mma_tf32(d1, al + kTile + k, bh + k, idesc, acc);
+                    mma_tf32(d, ah + k, bl + k, idesc, 1u);
+                    mma_tf32(d1, ah + kTile + k, bl + k, idesc, 1u);
+                    mma_tf32(d, ah + k, bh + k, idesc, 1u);
+                    mma_tf32(d1, ah + kTile + k, bh + k, idesc, 1u);
                 }
             } else {
 #pragma unroll

@@ -709,14 +709,35 @@ sexpe_status enqueue_coupled_step(sexpe_plan* p, double* state, cudaStream_t st)
         Tb.state = Tb.state_upd = Wb;
         Ts.state = Ts.state_upd = Ws;
         Tb.err = Ts.err = p->d_err;                    // bounded-wait timeouts reported by sexpe_synchronize
+        // The surface component runs on a second stream beside the bulk one: its stencil beside
+        // the bulk stencil, its chain beside the bulk chain; the coupling kernel, which reads and
+        // writes both, joins them (profiled steps keep one stream, in the order of their slots).
+        const bool fork = p->cpl_stream && !p->profiling;
+        cudaStream_t s2 = fork ? p->cpl_stream : st;
+        if (fork) {
+            SX_CUDA(cudaEventRecord(p->cpl_ev[0], st));
+            SX_CUDA(cudaStreamWaitEvent(s2, p->cpl_ev[0], 0));
+        }
         SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_rhs_split(Tb, st));
         SX_CUDA(prof_mark(p, st));
-        SX_CUDA(launch_rhs_split(Ts, st));
+        SX_CUDA(launch_rhs_split(Ts, s2));
+        if (fork) {
+            SX_CUDA(cudaEventRecord(p->cpl_ev[1], s2));
+            SX_CUDA(cudaStreamWaitEvent(st, p->cpl_ev[1], 0));
+        }
         SX_CUDA(prof_mark(p, st));
         SX_CUDA(launch_couple_split(p->cpl, Wb, Ws, Tb.Y, Ts.Y, Tb.n1q, Tb.ys, Ts.n1q, Ts.ys, st));
+        if (fork) {
+            SX_CUDA(cudaEventRecord(p->cpl_ev[2], st));
+            SX_CUDA(cudaStreamWaitEvent(s2, p->cpl_ev[2], 0));
+        }
         SX_TRY(enqueue_split_products(b, p, Tb, st));
-        SX_TRY(enqueue_split_products(s, p, Ts, st));
+        SX_TRY(enqueue_split_products(s, p, Ts, s2));
+        if (fork) {
+            SX_CUDA(cudaEventRecord(p->cpl_ev[3], s2));
+            SX_CUDA(cudaStreamWaitEvent(st, p->cpl_ev[3], 0));
+        }
         return SEXPE_OK;
     }
     SX_CUDA(prof_mark(p, st));
@@ -848,6 +869,12 @@ void free_plan(sexpe_plan* p) {
         if (p->sadj_ev_replayed[b]) cudaEventDestroy(p->sadj_ev_replayed[b]);
         if (p->sadj_ev_swept[b]) cudaEventDestroy(p->sadj_ev_swept[b]);
     }
+    if (p->cpl_stream) {
+        cudaStreamSynchronize(p->cpl_stream);
+        cudaStreamDestroy(p->cpl_stream);
+    }
+    for (cudaEvent_t e : p->cpl_ev)
+        if (e) cudaEventDestroy(e);
     for (void* a : p->allocs) cudaFree(a);
     if (p->h_err) cudaFreeHost(p->h_err);
     delete p;
@@ -1826,6 +1853,11 @@ sexpe_status sexpe_coupled_setup(const sexpe_grid* bg, const sexpe_species* bulk
             p->cpl = make_couple_args(bg, p->sub[0]->d.data(), cp);
             p->kernels_per_step = 1 + p->sub[0]->kernels_per_step + p->sub[1]->kernels_per_step;
             s = alloc_err_word(p, st);
+            if (s == SEXPE_OK && precision == SEXPE_SPLIT_TF32) {
+                if (cudaStreamCreateWithFlags(&p->cpl_stream, cudaStreamNonBlocking) != cudaSuccess) s = SEXPE_ECUDA;
+                for (int e = 0; e < 4 && s == SEXPE_OK; ++e)
+                    if (cudaEventCreateWithFlags(&p->cpl_ev[e], cudaEventDisableTiming) != cudaSuccess) s = SEXPE_ECUDA;
+            }
             if (s == SEXPE_OK) s = alloc_dev(p, (size_t)state_elems(p), &p->d_host_state);
             if (s == SEXPE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SEXPE_ECUDA;
         }

@@ -46,6 +46,8 @@ struct sexpe_plan {
     size_t bytes = 0;
     int* d_err = nullptr;
     int* h_err = nullptr;             // pinned host copy of the error word (read by sexpe_synchronize)
+    cudaStream_t cpl_stream = nullptr;   // split coupled plans: the surface component's stream
+    cudaEvent_t cpl_ev[4] = {};          // its fork and join points within a step
     double* d_host_state = nullptr;   // staging buffer of sexpe_step_host
     // FP64 path
     sexpe::RhsTables<double> rhs64{};

@@ -145,6 +145,29 @@ def test_coupled_single_calls_equal_one_call(precision):
         assert np.array_equal(x, y)
 
 
+def test_coupled_split_two_streams_equal_one_stream():
+    """Split coupled steps run the surface component on a second stream beside the bulk's; profiled
+    steps keep one stream.  Both orders give the same state bit for bit (the kernels and their
+    inputs are the same; only their overlap differs)."""
+    import torch
+    w = case((7, 10, 9), 6, 1e-3, 66, noise=2e-2)
+    out = []
+    for profiled in (False, True):
+        plan = plan_for(w, precision="split_tf32")
+        x = torch.from_numpy(flat(w["Wb"], w["Ws"])).cuda()
+        if profiled:
+            plan.profile_begin(6)
+        for _ in range(6):
+            plan.step(x, 1)
+        if profiled:
+            plan.profile_end()
+        plan.synchronize()
+        out.append(x.cpu().numpy())
+        plan.close()
+    assert np.all(np.isfinite(out[0]))
+    assert np.array_equal(out[0], out[1])
+
+
 def test_coupled_step_host_equals_device():
     w = case((6, 9, 8), 3, 1e-3, 65, noise=2e-2)
     dev = gpu_coupled(w, 3)

@@ -174,6 +174,7 @@ struct BatchTables {
     const int2* ftiles;             // phase-1 stencil tiles (instance, first theta-line)
     int n_ftiles;
     int tj;                         // theta-lines per phase-1 tile
+    int tile_f2;                    // float2 slots of one phase-1 tile buffer (two buffers in the rings)
     float* F;                       // F of every instance (phase 1 -> phase 2)
     const double* W_in;             // state before the step (all instances)
     double* W_out;                  // state after the step

@@ -1559,37 +1559,56 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_theta_adj(SplitTables T
 // the LPT-ordered work list and run the disk chain of eq. ee_disk on F --
 // x_2 Q_theta^T, Hadamard, x_2 Q_theta, x_1 phi_1(tau d A_rho) -- writing the
 // updated species into the other state buffer.
-// Phase-1 tiles are tj theta-lines of one instance (tj measured at setup: BatchTables.tj).
-__device__ __forceinline__ void batch_stencil_tile(const BatchInstance& I, const double* Win, float* Fout, int j0,
-                                                   int tj, float2* tile) {
-    const int n1 = I.n1, n2 = I.n2, n1q = (n1 + 3) & ~3;
-    const int lines = min(tj, n2 - j0);
-    const int nJ = lines + 2;                           // lines j0 - 1 .. j0 + lines: one wrap at most
-    const long long n12 = (long long)n1 * n2;
-    const int per_sp = nJ * n1;
-    const int items = 2 * per_sp;
-    const uint32_t m_n1 = div_magic((uint32_t)n1);
-    // kTileBatch loads in flight per thread: the tile fill is otherwise one DRAM latency per value
-    for (int q0 = threadIdx.x; q0 < items; q0 += kBlock * kTileBatch) {
-        double v[kTileBatch];
-#pragma unroll
-        for (int u = 0; u < kTileBatch; ++u) {
-            const int q = q0 + u * kBlock;
-            const int sp = q >= per_sp;
-            const int qq = q - sp * per_sp;
-            const int jj = div_by(qq, m_n1), i = qq - jj * n1;
-            int j = j0 - 1 + jj;
-            j = j < 0 ? j + n2 : (j >= n2 ? j - n2 : j);  // theta is periodic
-            v[u] = q < items ? __ldg(Win + sp * n12 + (long long)j * n1 + i) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kTileBatch; ++u) {
-            const int q = q0 + u * kBlock;
-            if (q < items) tile[q] = split_f64(v[u]);
-        }
+// Phase-1 tiles are tj theta-lines of one instance (tj measured at setup: BatchTables.tj), both
+// species, with a one-line halo in theta: values [s][jj][i], jj = 0 .. lines + 1 for the lines
+// j0 - 1 .. j0 + lines (periodic), as split pairs.  A tile's raw FP64 values arrive by
+// asynchronous copies (batch_tile_issue) while the CTA computes the previous tile, are split in
+// place (batch_tile_convert) and then used (batch_tile_compute).
+struct FTileGeom {
+    int n1, n2, lines, per_sp, items;
+};
+__device__ __forceinline__ FTileGeom ftile_geom(const BatchInstance& I, int j0, int tj) {
+    FTileGeom g;
+    g.n1 = I.n1;
+    g.n2 = I.n2;
+    g.lines = min(tj, g.n2 - j0);
+    g.per_sp = (g.lines + 2) * g.n1;                    // lines j0 - 1 .. j0 + lines: one wrap at most
+    g.items = 2 * g.per_sp;
+    return g;
+}
+
+__device__ __forceinline__ void batch_tile_issue(const BatchInstance& I, const double* Win, int j0, int tj,
+                                                 double* raw) {
+    const FTileGeom g = ftile_geom(I, j0, tj);
+    const long long n12 = (long long)g.n1 * g.n2;
+    const uint32_t m_n1 = div_magic((uint32_t)g.n1);
+    for (int q = threadIdx.x; q < g.items; q += kBlock) {
+        const int sp = q >= g.per_sp;
+        const int qq = q - sp * g.per_sp;
+        const int jj = div_by(qq, m_n1), i = qq - jj * g.n1;
+        int j = j0 - 1 + jj;
+        j = j < 0 ? j + g.n2 : (j >= g.n2 ? j - g.n2 : j);   // theta is periodic
+        cp_async8(smem_u32(raw + q), Win + sp * n12 + (long long)j * g.n1 + i);
     }
-    __syncthreads();
-    const int total = lines * n1;
+    cp_async_commit();
+}
+
+// Each thread splits the values it copied (its own copies are complete after cp_async_wait).
+__device__ __forceinline__ void batch_tile_convert(const BatchInstance& I, int j0, int tj, float2* tile) {
+    const FTileGeom g = ftile_geom(I, j0, tj);
+    const double* raw = reinterpret_cast<const double*>(tile);
+    for (int q = threadIdx.x; q < g.items; q += kBlock) {
+        const double v = raw[q];
+        tile[q] = split_f64(v);
+    }
+}
+
+__device__ __forceinline__ void batch_tile_compute(const BatchInstance& I, float* Fout, int j0, int tj,
+                                                   const float2* tile) {
+    const FTileGeom g = ftile_geom(I, j0, tj);
+    const int n1 = g.n1, n2 = g.n2, n1q = (n1 + 3) & ~3, per_sp = g.per_sp;
+    const uint32_t m_n1 = div_magic((uint32_t)n1);
+    const int total = g.lines * n1;
     for (int q = threadIdx.x; q < total; q += kBlock) {
         const int jl = div_by(q, m_n1), i = q - jl * n1;
         const int j = j0 + jl;
@@ -1641,26 +1660,45 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_batch(BatchTables B, TcShape s
     __shared__ int s_item;
     const uint32_t tmem_cols = sh.tmem_cols;
     CtaRes R = cta_begin(smem_raw, sh, B.err);
-    // phase 1: F of every instance.  The tile's instance record is copied to shared memory
-    // once: read through a global reference, its fields (sizes, table pointers, reaction
-    // parameters) are reloaded after every store of the tile loops, which may alias it.
-    float2* tile = reinterpret_cast<float2*>(R.P.mat_slots);
-    __shared__ __align__(16) BatchInstance s_inst;
-    __shared__ int2 s_tile;
+    // phase 1: F of every instance, two tiles in flight: while the CTA computes one tile, the raw
+    // values of the next arrive by asynchronous copies into the other buffer.  Each tile's instance
+    // record is copied to shared memory once: read through a global reference, its fields (sizes,
+    // table pointers, reaction parameters) are reloaded after every store of the tile loops, which
+    // may alias it.
+    float2* tbuf0 = reinterpret_cast<float2*>(R.P.mat_slots);
+    float2* tbuf1 = tbuf0 + B.tile_f2;
+    __shared__ __align__(16) BatchInstance s_inst[2];
+    __shared__ int2 s_tile[2];
     constexpr int kInstWords = (int)(sizeof(BatchInstance) / sizeof(int));
     static_assert(sizeof(BatchInstance) % sizeof(int) == 0, "instance record copied as words");
-    for (;;) {
+    // claims the next tile into slot b (false when none is left); uniform across the CTA
+    auto fetch = [&](int b) -> bool {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(B.counter + 2, 1);
-            s_tile = it < B.n_ftiles ? B.ftiles[it] : make_int2(-1, 0);
+            s_tile[b] = it < B.n_ftiles ? B.ftiles[it] : make_int2(-1, 0);
         }
         __syncthreads();
-        const int2 t = s_tile;
-        if (t.x < 0) break;
-        const int* src = reinterpret_cast<const int*>(B.inst + t.x);
-        for (int q = threadIdx.x; q < kInstWords; q += kBlock) reinterpret_cast<int*>(&s_inst)[q] = src[q];
+        if (s_tile[b].x < 0) return false;
+        const int* src = reinterpret_cast<const int*>(B.inst + s_tile[b].x);
+        for (int q = threadIdx.x; q < kInstWords; q += kBlock) reinterpret_cast<int*>(&s_inst[b])[q] = src[q];
         __syncthreads();
-        batch_stencil_tile(s_inst, B.W_in + s_inst.w_off, B.F + s_inst.f_off, t.y, B.tj, tile);
+        return true;
+    };
+    int cb = 0;
+    bool have = fetch(0);
+    if (have) batch_tile_issue(s_inst[0], B.W_in + s_inst[0].w_off, s_tile[0].y, B.tj, reinterpret_cast<double*>(tbuf0));
+    while (have) {
+        float2* cur = cb ? tbuf1 : tbuf0;
+        cp_async_wait<0>();
+        batch_tile_convert(s_inst[cb], s_tile[cb].y, B.tj, cur);
+        __syncthreads();
+        const bool next = fetch(cb ^ 1);
+        if (next)
+            batch_tile_issue(s_inst[cb ^ 1], B.W_in + s_inst[cb ^ 1].w_off, s_tile[cb ^ 1].y, B.tj,
+                             reinterpret_cast<double*>(cb ? tbuf0 : tbuf1));
+        batch_tile_compute(s_inst[cb], B.F + s_inst[cb].f_off, s_tile[cb].y, B.tj, cur);
+        have = next;
+        cb ^= 1;
     }
     grid_barrier(B.counter + 1, gridDim.x, B.err);
     // phase 2: the chains
@@ -2049,7 +2087,8 @@ int tc_batch_shapes(int max_n1, int max_n2, uint32_t tmem_cols, int max_tj, TcSh
     const uint32_t slack = 128 + kHeaderBytes;
     const uint32_t n1p = round_up(max_n1, 16);
     const uint32_t epi = kRows * (n1p + 1) * 4u;
-    const uint32_t tile = (uint32_t)(max_tj + 2) * (uint32_t)max_n1 * 2u * (uint32_t)sizeof(float2);
+    // two phase-1 tile buffers (the next tile's copies land while the current one is computed)
+    const uint32_t tile = 2u * (uint32_t)(max_tj + 2) * (uint32_t)max_n1 * 2u * (uint32_t)sizeof(float2);
     int n = 0;
     for (uint32_t nd = 2; nd <= (uint32_t)kMaxData; ++nd)
         for (uint32_t nm = 2; nm <= nd && nm <= (uint32_t)kMaxMat; ++nm) {

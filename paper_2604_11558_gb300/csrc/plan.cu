@@ -1113,6 +1113,7 @@ sexpe_status build_batch(sexpe_plan* p, int count, const sexpe_grid* grids, cons
     // plan's own buffers (a zero state; the arithmetic is data-independent) and keep the fastest.
     TcShape shapes[16];
     const int max_tj = *std::max_element(kBatchTileLines.begin(), kBatchTileLines.end());
+    p->btab.tile_f2 = (max_tj + 2) * max_n1 * 2;
     const int nsh = tc_batch_shapes(max_n1, max_n2, tmem_cols, max_tj, shapes, 16);
     if (nsh < 1 || shapes[0].tmem_cols > 512) return SEXPE_EUNSUPPORTED;
     uint32_t smem_max = 0;

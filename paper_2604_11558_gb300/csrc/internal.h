@@ -126,6 +126,7 @@ struct SplitTables {
     Image Pphi[kMaxSpecies];       // phi_1(tau d_s A_phi) as B operand, N-tiled: tile t (rows
                                    // [t phi_nt, (t + 1) phi_nt)) at ptr + t * k_chunks * chunk_floats
     int phi_nt;                    // output phi rows per CTA of the phi product
+    int phi_ks;                    // CTAs (one cluster) sharing the K range of one phi output tile
     float* Y2;                     // phi product output, layout of Y
     const float* had_sph;          // phi_1(tau d_s sin^-2 phi_j lambda_theta'), [s][j][n1q]
     Image Qsph;                    // Q_theta as B operand of the second theta product, N-tiled by th_nt rows

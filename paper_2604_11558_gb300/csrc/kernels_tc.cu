@@ -1316,17 +1316,26 @@ __global__ void __launch_bounds__(kBlock, 2)
 // phi direction (plain): Y2[s][j'][i] = sum_j phi_1(tau d_s A_phi)[j'][j] Y[s][j][i].
 // CTA = 128 consecutive theta points (rows) x phi_nt output phi rows (the B
 // operand's N-tile blockIdx.y) of species blockIdx.z; K runs over all phi.
+// With phi_ks > 1 the K range (phi) of each output tile is split over a cluster of phi_ks CTAs
+// (consecutive blockIdx.z = z phi_ks + cluster rank): each accumulates its 1/phi_ks of the
+// K-chunks and stages its partial product in its shared memory; after a cluster barrier each CTA
+// adds the phi_ks partials of its share of the output columns, in rank order (a fixed order), from
+// the cluster's shared memory, and a second cluster barrier keeps every partial in place until the
+// peers have read it.
 __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcShape sh) {
     extern __shared__ char smem_raw[];
     const uint32_t tmem_cols = sh.tmem_cols;
     CtaRes R = cta_begin(smem_raw, sh, T.err);
-    const bool second = (int)blockIdx.z >= T.S;            // phi_pair: the second image set into Y3
-    const int s = second ? blockIdx.z - T.S : blockIdx.z, nt = blockIdx.y;
+    const int ks = T.phi_ks > 1 ? T.phi_ks : 1;
+    const int kz = ks > 1 ? (int)cluster_ctarank() : 0, zz = (int)blockIdx.z / ks;
+    const bool second = zz >= T.S;                         // phi_pair: the second image set into Y3
+    const int s = second ? zz - T.S : zz, nt = blockIdx.y;
     const int n1 = T.n1, n2 = T.n2, n1q = T.n1q, NT = T.phi_nt;
     const int i0 = blockIdx.x * kRows;
     Image mat = second ? T.Pphi2[s] : T.Pphi[s];
-    mat.ptr += (long long)nt * mat.k_chunks * mat.chunk_floats;
-    GemmSpec gs[1] = {{mat, 0, kRows, 1, NT, mat.k_chunks, R.tmem}};
+    const int kc = mat.k_chunks / ks, kc0 = kz * kc;       // this CTA's K-chunks
+    mat.ptr += (long long)nt * mat.k_chunks * mat.chunk_floats + (long long)kc0 * mat.chunk_floats;
+    GemmSpec gs[1] = {{mat, 0, kRows, 1, NT, kc, R.tmem}};
     if (threadIdx.x >= kThreads + 32) {
         pdl_trigger();
         mma_issuer<1>(R.P, gs);
@@ -1344,18 +1353,50 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_sphere_phi(SplitTables T, TcSh
         const float* Yi = T.Y + (long long)s * T.ys + i;
         run_gemm(
             R.P, gs[0],
-            [&](int c, Pre8& p) { load8_strided(p, Yi, n1q, c * 16 + h * 8, n2, valid); },
+            [&](int c, Pre8& p) { load8_strided(p, Yi, n1q, (kc0 + c) * 16 + h * 8, n2, valid); },
             [&](int, char* hi, char* lo, const Pre8& p) { store_row8(hi, lo, r, h, p.v); });
-        float* Yo = (second ? T.Y3 : T.Y2) + (long long)s * T.ys + i;
-        for (int c = 0; c < NT / 16; ++c) {
-            float v[8];
-            tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+        if (ks == 1) {
+            float* Yo = (second ? T.Y3 : T.Y2) + (long long)s * T.ys + i;
+            for (int c = 0; c < NT / 16; ++c) {
+                float v[8];
+                tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = nt * NT + c * 16 + h * 8 + q;
-                if (valid && j < n2) Yo[(long long)j * n1q] = v[q];
+                for (int q = 0; q < 8; ++q) {
+                    const int j = nt * NT + c * 16 + h * 8 + q;
+                    if (valid && j < n2) Yo[(long long)j * n1q] = v[q];
+                }
+            }
+        } else {
+            // the partial product, [column][row], in the rings (free: the product completed)
+            float* Pm = reinterpret_cast<float*>(R.P.mat_slots);
+            for (int c = 0; c < NT / 16; ++c) {
+                float v[8];
+                tmem_ld8(R.tmem + lane_base + (uint32_t)(c * 16 + h * 8), v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) Pm[(c * 16 + h * 8 + q) * kRows + r] = v[q];
             }
         }
+    }
+    if (ks > 1) {
+        __syncwarp();
+        cluster_sync_all();                              // every CTA's partial is staged
+        if (threadIdx.x < kThreads) {
+            const int r = threadIdx.x & (kRows - 1), g = threadIdx.x >> 7;
+            const int cw = NT / ks;                      // this CTA's output columns: [kz cw, (kz + 1) cw)
+            const uint32_t base = smem_u32(R.P.mat_slots);
+            const int i = i0 + r;
+            float* Yo = (second ? T.Y3 : T.Y2) + (long long)s * T.ys + i;
+            for (int cc = g; cc < cw; cc += 2) {
+                const int col = kz * cw + cc;
+                const uint32_t off = base + (uint32_t)(col * kRows + r) * 4u;
+                float acc = ld_dsmem(dsmem_addr(off, 0));
+                for (int k = 1; k < ks; ++k) acc += ld_dsmem(dsmem_addr(off, (uint32_t)k));
+                const int j = nt * NT + col;
+                if (i < n1 && j < n2) Yo[(long long)j * n1q] = acc;
+            }
+        }
+        __syncwarp();
+        cluster_sync_all();                              // the peers have read this CTA's partial
     }
     cta_end(R, tmem_cols);
 }
@@ -1868,8 +1909,24 @@ cudaError_t tc_prepare_sphere(uint32_t smem_phi, uint32_t smem_theta) {
 
 cudaError_t launch_tc_sphere_phi(const SplitTables& T, const TcShape& sh, cudaStream_t st) {
     const int n2p = (T.n2 + 15) & ~15;
-    dim3 grid((T.n1 + kRows - 1) / kRows, (n2p + T.phi_nt - 1) / T.phi_nt, T.phi_pair ? 2 * T.S : T.S);
-    return launch_pdl(k_tc_sphere_phi, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
+    const int ks = T.phi_ks > 1 ? T.phi_ks : 1;
+    dim3 grid((T.n1 + kRows - 1) / kRows, (n2p + T.phi_nt - 1) / T.phi_nt, (T.phi_pair ? 2 * T.S : T.S) * ks);
+    if (ks == 1) return launch_pdl(k_tc_sphere_phi, grid, dim3(kBlock), sh.smem_bytes, st, T, sh);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = sh.smem_bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 1;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = (unsigned)ks;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, k_tc_sphere_phi, T, sh);
 }
 
 cudaError_t launch_tc_sphere_theta(const SplitTables& T, const TcShape& sh, cudaStream_t st) {

@@ -391,6 +391,59 @@ static sexpe_status tune_stencil(sexpe_plan* p, cudaStream_t st) {
     return rc;
 }
 
+// Measured K-split of the sphere's phi product: one output tile's product runs over all n_phi / 16
+// K-chunks in one CTA, and with few tiles (16 CTAs on the 256 x 512 sphere) that serial chain sets
+// the kernel's time.  Split over a cluster of ks CTAs, each runs 1/ks of the chunks and the
+// partials are added through distributed shared memory.  Every ks in {1, 2, 4, 8} that divides
+// the chunk count (at least two chunks per CTA) and the tile's columns, and whose partial tile
+// fits in the rings, is timed like the theta splits (a configuration the device cannot launch is
+// skipped), and the fastest is kept.
+static sexpe_status tune_sphere_phi(sexpe_plan* p, cudaStream_t st) {
+    SplitTables& T = p->tabs;
+    T.phi_ks = 1;
+    const int kc = rup16(p->n[1]) / kKC;
+    const uint32_t rings_bytes = p->sh3.nm * p->sh3.mat_bytes + p->sh3.nd * p->sh3.data_bytes;
+    std::vector<int> cands{1};
+    for (int ks = 2; ks <= 8; ks *= 2)
+        if (kc % ks == 0 && kc / ks >= 2 && T.phi_nt % ks == 0 &&
+            (uint32_t)T.phi_nt * 128u * sizeof(float) <= rings_bytes)   // 128-row partial tile
+            cands.push_back(ks);
+    if (cands.size() == 1) return SEXPE_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sexpe_status rc = SEXPE_OK;
+    float best_ms = 1e30f;
+    int best = 1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = SEXPE_ECUDA;
+    } else {
+        SplitTables Tt = T;
+        for (size_t c = 0; c < cands.size() && rc == SEXPE_OK; ++c) {
+            Tt.phi_ks = cands[c];
+            if (launch_tc_sphere_phi(Tt, p->sh3, st) != cudaSuccess) {   // e.g. no room for the cluster
+                cudaGetLastError();
+                if (cands[c] == 1) rc = SEXPE_ECUDA;
+                continue;
+            }
+            bool ok = cudaEventRecord(e0, st) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_tc_sphere_phi(Tt, p->sh3, st) == cudaSuccess;
+            float ms = 0.f;
+            ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            if (!ok) rc = SEXPE_ECUDA;
+            else if (ms < best_ms) {
+                best_ms = ms;
+                best = cands[c];
+            }
+        }
+    }
+    if (rc != SEXPE_OK) cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    T.phi_ks = best;
+    return rc;
+}
+
 // Times the theta kernel of the sphere at every column split (one warm-up launch,
 // then three, CUDA events) on a zeroed scratch state and keeps the fastest.
 static sexpe_status tune_sphere_theta(sexpe_plan* p, const std::vector<int>& splits, const std::vector<Image>& qimg,
@@ -525,6 +578,7 @@ sexpe_status build_split_sphere(sexpe_plan* p, cudaStream_t st) {
     SX_CUDA(tc_prepare_sphere(p->sh3.smem_bytes, smem_max));
     p->kernels_per_step = 3;
     SX_TRY(tune_sphere_theta(p, splits, qimg, st));
+    SX_TRY(tune_sphere_phi(p, st));
     return tune_stencil(p, st);
 }
 

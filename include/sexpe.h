@@ -259,7 +259,11 @@ sexpe_status sexpe_step_noalloc(sexpe_plan* plan, double* state_dev, int64_t n_s
  * sexpe_step_noalloc (SEXPE_EINVAL).  Step with sexpe_step / sexpe_step_host;
  * destroy with sexpe_destroy.  Other errors as sexpe_setup.  sexpe_plan_info
  * reports n_species = 4, npts of the bulk grid, the bulk grid's tile choices
- * and the device bytes of both sub-plans. */
+ * and the device bytes of both sub-plans.  A SEXPE_SPLIT_TF32 plan owns a
+ * second (non-blocking) CUDA stream: each step forks the surface grid's
+ * kernels onto it from the caller's stream with an event and joins them back
+ * with events, so the step stays ordered on the caller's stream (graph
+ * capture included) while the two grids' chains overlap on the GPU. */
 typedef enum { SEXPE_COUPLING_SCHNAKENBERG_BALL = 0, SEXPE_COUPLING_DIB_CYLINDER = 1 } sexpe_coupling_kind;
 typedef struct {
     int32_t kind;            /* sexpe_coupling_kind                                       */

@@ -1,6 +1,7 @@
 """Host logic of bench.py on CPU: the max-over-ranks reduction used for the
 timed region, with two gloo ranks (replicas only: no collective on the data
-path), and the algorithmic-work table used for the roofline."""
+path), the algorithmic-work table used for the roofline, and the JSON line of the
+reference arm (the oracle on the host cores)."""
 import os
 import socket
 
@@ -49,3 +50,24 @@ def test_kernel_work_table():
     # split-TF32 flops per DOF of the whole chain: 3 passes x 2 x (2 n_phi + 2 n_theta + n_rho)
     total = sum(v["flops"] for v in wk.values()) / dof
     assert total == 3 * 2 * (2 * 100 + 2 * 100 + 100)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores, one timed step) prints one JSON
+    line with the contract's keys, the workload of our own arm and a reference-arm e2e entry."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, cwd=root, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    import bench
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
